@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the Year Loss Table hot path (Varghese & Barker, arXiv 1412.4556).
+
+One step = one pass of the whole path over the paper-scale workload
+(catalog 2,000,000 events; one layer over 16 ELTs of 20,000 events;
+1,000,000 trials of Poisson(1000) events, about 1e9 occurrences):
+
+    ara_define_layer  (per-layer ELT fold pre-pass on the device)
+    ara_layer_ylt     (per-trial gather + exact sum + aggregate terms)
+    ara_pml_tvar      (PML and TVaR at return periods 100 / 250 / 500)
+
+The YET and the ELT pool are resident in HBM when the timed region starts
+(the paper's pre-processing stage); the 4 GB id stream is larger than L2, so
+every step reads it from HBM.  ``e2e`` repeats the step through the same C
+ABI with host buffers: the YET, the ELTs and the layer go host->device and
+the YLT, PML and TVaR come back, inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+
+Under torchrun (N > 1) every rank prices its own shard of 1,000,000 trials
+(weak scaling); the shards' YLTs are all-gathered for the portfolio-wide
+PML/TVaR.  ``--impl reference`` times the FP64 CPU oracle (the only reference
+this path has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import ara_synth as S  # noqa: E402
+
+METRIC = "YLT trial-events/s & HBM GB/s vs roofline; layer-request p50/p99 latency"
+UNIT = "trial-events/s"
+PAPER_1GPU_TRIAL_EVENTS_PER_S = 1e9 / 19.93  # Tesla M2050, Section IV-C (context only)
+WORKLOAD = ("paper-scale plain ARA, FP64: catalog 2,000,000 events; 1 layer over 16 ELTs x 20,000 "
+            "events (lognormal(12,1.5) losses, D~U[5e3,5e4], Lim~U[1e6,1e7]); 1,000,000 trials x "
+            "Poisson(1000) events; OccR 1e5, OccL 2e7, AggR 5e5, AggL 1e8; RP 100/250/500")
+
+
+# ------------------------------------------------------------ distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def shard_seed(seed: int, rank: int) -> int:
+    """Each rank prices its own independent block of trials."""
+    return S.sub_seed(seed, "rank", rank) if rank else seed
+
+
+def merge_shard_ylts(parts):
+    """Portfolio-wide YLT from the ranks' shards (rank order)."""
+    return np.concatenate([np.asarray(p, dtype=np.float64) for p in parts])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- roofline
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def kernel_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ylt.cu", "ara_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1412_4556_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_launch(occurrences: int):
+    """DRAM bytes per YLT launch from the committed ncu summary, scaled to this
+    launch by occurrences; None when the kernel changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ylt_fp64_kernel_paper_scale.md")
+    try:
+        text = open(p).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_digest:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_occurrence:\s*([0-9.eE+-]+)", text)
+    if not m or not b or m.group(1) != kernel_source_digest():
+        return None
+    return float(b.group(1)) * occurrences
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(w, budget_s: float = 12.0, threads=None, max_trials=None):
+    """Time the FP64 oracle (literal Algorithm 1) on a bounded trial sample."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    layer = w.layers[0]
+    rng = np.random.default_rng(5)
+    n = w.yet.n_trials
+    probe = np.sort(rng.choice(n, min(n, max(threads * 8, 256)), replace=False))
+    t0 = time.perf_counter()
+    oracle.layer_ylt(w.yet, w.pool, layer, trials=probe, mode="literal", threads=threads)
+    dt = time.perf_counter() - t0
+    per_trial = max(dt / probe.size, 1e-7)
+    k = int(min(n, max(probe.size, budget_s / per_trial)))
+    if max_trials:
+        k = min(k, max_trials)
+    sel = np.sort(rng.choice(n, k, replace=False))
+    occ = int(np.diff(w.yet.offsets)[sel].sum())
+    t0 = time.perf_counter()
+    oracle.layer_ylt(w.yet, w.pool, layer, trials=sel, mode="literal", threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": occ / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{k} of {n} trials ({occ} trial-events), literal Algorithm 1 "
+                      f"(16 direct-access-table lookups per event), {dt:.1f} s"}
+
+
+# --------------------------------------------------------------- engine arm
+def run_engine(args):
+    import torch
+    from paper_1412_4556_b300 import ARA_TIMING_FOLD, ARA_TIMING_PML, ARA_TIMING_YLT, Engine
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    w = S.paper_scale(seed=shard_seed(S.DEFAULT_SEED, rank), n_trials=args.trials)
+    layer = w.layers[0]
+    rps = w.return_periods
+    M, N, C = w.yet.n_occurrences, w.yet.n_trials, w.yet.catalog_size
+
+    stream = torch.cuda.Stream(device=dev)
+    eng = Engine(local, stream=stream)
+    eng.load_yet_from(w.yet)
+    first = eng.load_pool(w.pool)
+    handles = [first + j for j in layer.elts]
+    ylt_dev = torch.empty(N, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    gather_buf = None
+    if world > 1:
+        gather_buf = torch.empty(N * world, dtype=torch.float64, device=dev)
+
+    def step():
+        L = eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
+        eng.layer_ylt(L, out=ylt_dev)
+        if world > 1:
+            import torch.distributed as dist
+            with torch.cuda.stream(stream):
+                dist.all_gather_into_tensor(gather_buf, ylt_dev)
+            res = eng.pml_tvar(gather_buf, rps) if rank == 0 else None
+        else:
+            res = eng.pml_tvar(ylt_dev, rps)
+        eng.release_layer(L)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    eng.set_kernel_timing(True)
+    barrier()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    n_ylt, ylt_ms = eng.kernel_timing(ARA_TIMING_YLT)
+    n_fold, fold_ms = eng.kernel_timing(ARA_TIMING_FOLD)
+    n_pml, pml_ms = eng.kernel_timing(ARA_TIMING_PML)
+    eng.set_kernel_timing(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = M * world / (ms_step / 1e3)
+
+    # Roofline of the dominant kernel (the YLT gather/sum).
+    ylt_avg_ms = ylt_ms / max(n_ylt, 1)
+    alg_bytes = 4 * M + 8 * (N + 1) + 8 * N + 8 * C
+    achieved = alg_bytes / (ylt_avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    traffic = ncu_traffic_per_launch(M)
+
+    # End to end through the C ABI with host buffers (pinned), per step.
+    e2e = run_e2e(args, w, handles_count=len(layer.elts), local=local) if rank == 0 else None
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = oracle_sample(w, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": value / PAPER_1GPU_TRIAL_EVENTS_PER_S,
+        "vs_baseline_basis": "paper's best single GPU run (Tesla M2050, 19.93 s for 1e9 trial-events, "
+                             "Section IV-C); other hardware, context only",
+        "dtype": "f64", "data": "synthetic (seeded; stands in for the paper's proprietary industry data)",
+        "config": {"workload": WORKLOAD, "n_trials_per_gpu": N, "occurrences_per_gpu": M,
+                   "catalog": C, "elts": len(layer.elts),
+                   "step": "ara_define_layer (ELT fold) + ara_layer_ylt + ara_pml_tvar",
+                   "l2": "inputs larger than L2: the 4 GB YET id stream is re-read from HBM every step",
+                   "parallelism": f"trial shards x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "ylt_fp64_kernel", "kernel_ms": ylt_avg_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "breakdown_ms_per_step": {"fold": fold_ms / max(args.steps, 1), "ylt": ylt_ms / max(args.steps, 1),
+                                  "pml_tvar": pml_ms / max(args.steps, 1)},
+        "pml": list(map(float, res[0])), "tvar": list(map(float, res[1])),
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": args.steps * (1 + 1 + 10),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, w, handles_count: int, local: int):
+    """Same step through the public C ABI with pinned host buffers: H2D of the
+    YET and the ELTs, the layer definition, the YLT and PML/TVaR back to host."""
+    import torch
+    from paper_1412_4556_b300 import Engine
+
+    layer = w.layers[0]
+    rps = w.return_periods
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_off, h_ids = pin(w.yet.offsets), pin(w.yet.ids)
+    p = w.pool
+    h_eoff, h_eids, h_eloss = pin(p.offsets), pin(p.ids), pin(p.losses)
+    h_ded, h_lim = pin(p.deductibles), pin(p.limits)
+    h_ylt = torch.empty(w.yet.n_trials, dtype=torch.float64).pin_memory()
+    eng = Engine(local)
+    N, M = w.yet.n_trials, w.yet.n_occurrences
+
+    def step():
+        eng.load_yet(w.yet.catalog_size, h_off.numpy(), h_ids.numpy())
+        first = eng.load_elts(h_eoff.numpy(), h_eids.numpy(), h_eloss.numpy(), h_ded.numpy(),
+                              h_lim.numpy())
+        L = eng.define_layer([first + j for j in layer.elts], layer.occ_ret, layer.occ_lim,
+                             layer.agg_ret, layer.agg_lim)
+        out = eng.layer_ylt(L, out=h_ylt.numpy())
+        res = eng.pml_tvar(out, rps)
+        eng.release_layer(L)
+        return res
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, args.e2e_steps))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    eng.close()
+    h2d = 8 * (N + 1) + 4 * M + 8 * (p.n_elts + 1) + 12 * p.ids.size + 16 * p.n_elts
+    d2h = 8 * N + 16 * len(rps)
+    return {"value": M / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": dt * 1e3, "steps": k,
+            "note": "pinned host buffers through ara_load_yet/ara_load_elts/ara_define_layer/"
+                    "ara_layer_ylt(host out)/ara_pml_tvar; YET ids validated on the device each step"}
+
+
+# ------------------------------------------------------------ oracle arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = S.paper_scale(n_trials=args.trials)
+    M = w.yet.n_occurrences
+    per = max(2.0, min(args.cpu_budget, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        oracle_sample(w, budget_s=per / 4)
+    vals, samples = [], []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle_sample(w, budget_s=per)
+        vals.append(r["value"])
+        samples.append(r)
+    wall = time.perf_counter() - t_all
+    value = statistics.median(vals)
+    ms_step = M / value * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+        "config": {"workload": WORKLOAD, "n_trials_per_gpu": w.yet.n_trials, "occurrences_per_gpu": M,
+                   "note": "each step times the oracle on a bounded trial sample; ms_per_step is "
+                           "extrapolated to the full workload from the measured rate"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[-1]["cores"], "kind": "oracle",
+                         "sample": samples[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "engine":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_engine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * ara.h -- C ABI of the B300 Year Loss Table engine for Aggregate Risk
+ * Analysis (Varghese & Barker, "Are Clouds Ready to Accelerate Ad hoc
+ * Financial Simulations?", arXiv 1412.4556).
+ *
+ * The calls follow the paper's problem statement (Section III):
+ *   - the Year Event Table (YET): trials of (event id, time-stamp) pairs in
+ *     ascending time-stamp order                        -> ara_load_yet
+ *   - Event Loss Tables (ELTs): (event id, loss) pairs plus financial terms
+ *     FT1 (read as a deductible and a limit)            -> ara_load_elts
+ *   - a Layer: ELTs plus occurrence terms FT2 = (OccR, OccL) and aggregate
+ *     terms FT3 = (AggR, AggL)                          -> ara_define_layer
+ *   - Algorithm 1: the Year Loss Table (one loss per trial) -> ara_layer_ylt
+ *   - PML and TVaR derived from the YLT                 -> ara_pml_tvar
+ *
+ * Conventions for every call:
+ *   - Plain pointers and sizes.  A pointer argument documented "host or
+ *     device" may point to host memory (pageable or pinned) or to device
+ *     memory of the context's GPU; the library tells them apart with
+ *     cudaPointerGetAttributes.
+ *   - The library COPIES every input; the caller keeps ownership of its
+ *     arrays and may free them when the call returns.  Outputs are
+ *     allocated by the caller.
+ *   - No call aborts the process or traps on the device.  Every failure is a
+ *     negative status; ara_last_error(ctx) holds a one-line message.  On
+ *     failure, the context's previous state (loaded YET, ELTs, layers) is
+ *     unchanged unless the description says otherwise.
+ *   - Calls on one context are not thread-safe; serialise them.
+ *   - Work runs on the context's stream (a library-owned stream, or the one
+ *     given to ara_set_stream).  Calls that write host memory return after
+ *     the data is in place; calls that only write device memory return once
+ *     the work is queued.
+ */
+#ifndef ARA_H_
+#define ARA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ARA_API __attribute__((visibility("default")))
+#else
+#define ARA_API
+#endif
+
+typedef struct ara_ctx ara_ctx;
+typedef int32_t ara_status;
+
+#define ARA_OK 0
+#define ARA_E_INVALID_ARG (-1) /* bad size, pointer, term or ordering */
+#define ARA_E_EVENT_RANGE (-2) /* an event id outside [0, catalog_size) */
+#define ARA_E_DUP_EVENT (-3)   /* an event id repeated within one ELT */
+#define ARA_E_NOMEM (-4)       /* device or host allocation failed */
+#define ARA_E_CUDA (-5)        /* a CUDA runtime call failed */
+#define ARA_E_TIMEOUT (-6)     /* a bounded wait ran out */
+#define ARA_E_NOT_FOUND (-7)   /* unknown ELT or layer handle */
+#define ARA_E_STATE (-8)       /* call order: e.g. no YET loaded yet */
+
+/* Precision of a layer's per-event table (ara_define_layer). */
+#define ARA_FP64 0        /* FP64 event losses, exact integer trial sums */
+#define ARA_FP32_TABLE 1  /* FP32 event losses, FP64 running sum */
+
+/* Timing channels for ara_kernel_timing. */
+#define ARA_TIMING_YLT 0  /* the per-trial gather/sum kernel */
+#define ARA_TIMING_FOLD 1 /* the per-layer ELT fold (pre-pass) kernel */
+#define ARA_TIMING_PML 2  /* the PML/TVaR selection kernels, summed */
+
+/* ------------------------------------------------------------------ setup */
+
+/* Create a context on CUDA device `device` with its own stream.
+ * *out receives the context (NULL on failure).  ARA_E_CUDA if the device
+ * cannot be used (for instance when no GPU is present). */
+ARA_API ara_status ara_create(ara_ctx **out, int device);
+
+/* Free every device and host resource of the context.  NULL is a no-op. */
+ARA_API void ara_destroy(ara_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  The pointer stays
+ * valid until the next call on ctx.  ctx == NULL gives the message of the
+ * last failed ara_create. */
+ARA_API const char *ara_last_error(const ara_ctx *ctx);
+
+/* Static name of a status code ("ARA_OK", "ARA_E_INVALID_ARG", ...). */
+ARA_API const char *ara_status_string(ara_status status);
+
+/* Run later work on `cuda_stream` (a cudaStream_t of the context's device);
+ * NULL restores the context's own stream.  The caller keeps ownership of
+ * the stream and must keep it alive while the context uses it. */
+ARA_API ara_status ara_set_stream(ara_ctx *ctx, void *cuda_stream);
+
+/* ------------------------------------------------ Year Event Table (YET) */
+
+/* Load the YET (Section III: trials T_i = {(E_ik, t_ik)} in ascending
+ * time-stamp order; "about one million trials of about one thousand
+ * events") as CSR arrays, replacing any YET loaded before.
+ *   catalog_size  number of catalog events; ids must lie in [0, catalog_size)
+ *   n_trials      number of trials N >= 0
+ *   trial_offsets int64[N+1], host or device: trial t owns positions
+ *                 [trial_offsets[t], trial_offsets[t+1]); [0] == 0 and the
+ *                 sequence is nondecreasing; M = trial_offsets[N] occurrences
+ *   event_ids     int32[M], host or device, in stored (time-stamp) order;
+ *                 may be NULL when M == 0.  A trial may repeat an event.
+ *   timestamps    float32[M], host or device, or NULL.  When given they must
+ *                 be finite and nondecreasing within each trial; they are
+ *                 kept on the device but the trial loss does not read them
+ *                 (the stored order already is the time order).
+ * Errors: ARA_E_INVALID_ARG (sizes, offsets, time-stamp order),
+ * ARA_E_EVENT_RANGE (an id outside the catalog, or an already loaded ELT
+ * holding an id outside the new catalog), ARA_E_NOMEM, ARA_E_CUDA.  Errors
+ * found in the sizes, the offsets or the ELT check leave the previous YET
+ * loaded; once the copy has started (it replaces the previous YET in place,
+ * since it can be several GB), a failure leaves the context with no YET.
+ * Layers already defined are re-folded against the new YET on their next
+ * use. */
+ARA_API ara_status ara_load_yet(ara_ctx *ctx, int32_t catalog_size, int64_t n_trials,
+                        const int64_t *trial_offsets, const int32_t *event_ids,
+                        const float *timestamps);
+
+/* ------------------------------------------------- Event Loss Tables (ELT) */
+
+/* Append n_elts ELTs to the context's pool (Section III: ELT = {(E_i, l_i)}
+ * plus financial terms FT1; "tens of thousands of event losses").  All
+ * arrays are host pointers.
+ *   elt_offsets int64[n_elts+1]: ELT j owns positions [off[j], off[j+1]);
+ *               off[0] == 0, nondecreasing (an empty ELT is allowed)
+ *   event_ids   int32[off[n_elts]]: distinct within one ELT, each in
+ *               [0, catalog_size) of the loaded YET
+ *   losses      double[off[n_elts]]: finite and >= 0
+ *   deductibles double[n_elts]: finite and >= 0
+ *   limits      double[n_elts]: >= 0; +inf means "no limit"
+ *   first_elt_handle (out): handle of the first new ELT; the others follow
+ *               contiguously.  Handles stay valid until ara_destroy.
+ * Requires a loaded YET (ARA_E_STATE otherwise).  Errors:
+ * ARA_E_INVALID_ARG, ARA_E_EVENT_RANGE, ARA_E_DUP_EVENT, ARA_E_NOMEM,
+ * ARA_E_CUDA; on error no ELT of the call is added. */
+ARA_API ara_status ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int64_t *elt_offsets,
+                         const int32_t *event_ids, const double *losses,
+                         const double *deductibles, const double *limits,
+                         int32_t *first_elt_handle);
+
+/* ------------------------------------------------------------------ layers */
+
+/* Define a layer (Section III: L = {E = {ELT_1..ELT_j}, FT2, FT3}).
+ *   n_elts, elt_handles  the layer's ELTs; their order is the order in
+ *                        which the per-ELT net losses are summed.  An ELT
+ *                        may not appear twice.  n_elts >= 1.
+ *   occ_ret, occ_lim     FT2: occurrence retention and limit, applied to
+ *                        each event's loss combined across the ELTs
+ *   agg_ret, agg_lim     FT3: aggregate retention and limit, applied to the
+ *                        cumulative sum of occurrence-net losses of a trial
+ *   precision            ARA_FP64 or ARA_FP32_TABLE
+ *   layer_out (out)      the layer handle
+ * Retentions must be finite and >= 0, limits >= 0 (+inf allowed).  The
+ * per-layer pre-pass (folding the ELT terms and the occurrence terms into
+ * one per-event table) is queued on the context's stream.
+ * Errors: ARA_E_INVALID_ARG, ARA_E_NOT_FOUND, ARA_E_STATE (no YET),
+ * ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_define_layer(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_handles,
+                            double occ_ret, double occ_lim, double agg_ret, double agg_lim,
+                            int32_t precision, int32_t *layer_out);
+
+/* Free the device tables of a layer; its handle becomes invalid. */
+ARA_API ara_status ara_release_layer(ara_ctx *ctx, int32_t layer);
+
+/* The layer's per-event table as FP64: out[e] = FT2(sum_j FT1(DAT_j[e]))
+ * for every catalog event e (the occurrence-net loss of one occurrence of
+ * e).  out: double[catalog_size], host or device.  Bit-identical to a
+ * sequential FP64 loop over the layer's ELTs in layer order. */
+ARA_API ara_status ara_layer_event_table(ara_ctx *ctx, int32_t layer, double *out);
+
+/* Year Loss Table of one layer (Algorithm 1) over the first n_trials trials
+ * of the loaded YET (0 <= n_trials <= loaded N).
+ *   ylt_out     double[n_trials], host or device: ylt_out[t] =
+ *               min(max(S_t - AggR, 0), AggL), S_t the sum of the trial's
+ *               occurrence-net event losses (0 for an empty trial)
+ *   cuda_stream stream for this call only, or NULL for the context's stream
+ * FP64 layers sum each trial exactly in 128-bit fixed point and round once
+ * to binary64; the result is independent of launch shape and summation
+ * order.  Errors: ARA_E_INVALID_ARG, ARA_E_NOT_FOUND, ARA_E_STATE,
+ * ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_layer_ylt(ara_ctx *ctx, int32_t layer, int64_t n_trials, double *ylt_out,
+                         void *cuda_stream);
+
+/* PML and TVaR from a YLT of n trial losses (Section III names both as read
+ * from the YLT).  For each return period RP_r: k = floor(n / RP_r);
+ * PML_r = the k-th largest trial loss; TVaR_r = mean of the k largest.
+ *   ylt             double[n], host or device; finite and >= 0
+ *   return_periods  double[n_rp], host; each RP >= 1 with floor(n/RP) >= 1
+ *   pml_out, tvar_out  double[n_rp], host
+ * The k-th largest is found by an exact radix selection on the device and
+ * the tail sum is exact before one final rounding.  Errors:
+ * ARA_E_INVALID_ARG (bad RP, NaN/negative/inf loss), ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_pml_tvar(ara_ctx *ctx, const double *ylt, int64_t n,
+                        const double *return_periods, int32_t n_rp, double *pml_out,
+                        double *tvar_out);
+
+/* ------------------------------------------------------------- measurement */
+
+/* Record CUDA events around every kernel launch of the timing channels
+ * (enable != 0) or stop recording (enable == 0).  Enabling clears the
+ * totals. */
+ARA_API ara_status ara_set_kernel_timing(ara_ctx *ctx, int32_t enable);
+
+/* Launch count and summed device time (milliseconds) of one timing channel
+ * since timing was enabled.  Waits for the recorded events. */
+ARA_API ara_status ara_kernel_timing(ara_ctx *ctx, int32_t channel, int64_t *launches,
+                             double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARA_H_ */

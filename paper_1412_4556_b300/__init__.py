@@ -1,0 +1,163 @@
+"""B300 engine for the Year Loss Table of Aggregate Risk Analysis.
+
+Varghese & Barker, "Are Clouds Ready to Accelerate Ad hoc Financial
+Simulations?" (arXiv 1412.4556), Section III, Algorithm 1: for every layer and
+trial, look each event of the trial up in the layer's ELTs, apply the ELT
+terms, combine across ELTs, apply the occurrence terms, accumulate with the
+aggregate terms, and report the trial loss; PML and TVaR follow from the YLT.
+
+The computation runs in hand-written CUDA kernels behind the C ABI of
+``include/ara.h`` (``libara_b300.so``).  :mod:`._native` binds each C entry
+point under its own name; :class:`Engine` adds array marshalling for NumPy
+arrays (host memory) and torch tensors (device memory).  PyTorch is only used
+for device buffers and streams.
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _native
+from ._native import (ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_FOLD, ARA_TIMING_PML, ARA_TIMING_YLT,
+                      AraError)
+
+__all__ = ["Engine", "AraError", "ARA_FP64", "ARA_FP32_TABLE", "ARA_TIMING_YLT",
+           "ARA_TIMING_FOLD", "ARA_TIMING_PML"]
+
+
+def _is_tensor(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, dtype, name: str):
+    """(pointer, keep-alive object) for a NumPy array or a torch tensor."""
+    if a is None:
+        return 0, None
+    if _is_tensor(a):
+        import torch
+        want = {np.int64: torch.int64, np.int32: torch.int32, np.float64: torch.float64,
+                np.float32: torch.float32}[dtype]
+        if a.dtype != want:
+            raise TypeError(f"{name}: expected {want}, got {a.dtype}")
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, arr
+
+
+class Engine:
+    """One context of the CUDA engine on one GPU."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.ctx = _native.ara_create(device)
+        self.device = device
+        self.catalog_size = 0
+        self.n_trials = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -------------------------------------------------------------- lifetime
+    def close(self) -> None:
+        if self.ctx:
+            _native.ara_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream) -> None:
+        """Queue later work on a torch.cuda.Stream (or a raw cudaStream_t int)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _native.ara_set_stream(self.ctx, int(handle or 0))
+
+    # ------------------------------------------------------------------ data
+    def load_yet(self, catalog_size: int, offsets, ids, ts=None) -> None:
+        n_trials = int(offsets.shape[0]) - 1
+        p_off, k1 = _arg(offsets, np.int64, "offsets")
+        p_ids, k2 = _arg(ids, np.int32, "ids")
+        p_ts, k3 = _arg(ts, np.float32, "ts")
+        _native.ara_load_yet(self.ctx, int(catalog_size), n_trials, p_off, p_ids, p_ts)
+        self.catalog_size = int(catalog_size)
+        self.n_trials = n_trials
+
+    def load_yet_from(self, yet) -> None:
+        """Load an :class:`ara_synth.YET`-like object (catalog_size, offsets, ids, ts)."""
+        self.load_yet(yet.catalog_size, yet.offsets, yet.ids, yet.ts)
+
+    def load_elts(self, offsets, ids, losses, deductibles, limits) -> int:
+        n = int(np.asarray(offsets).shape[0]) - 1
+        p = [_arg(offsets, np.int64, "offsets"), _arg(ids, np.int32, "ids"),
+             _arg(losses, np.float64, "losses"), _arg(deductibles, np.float64, "deductibles"),
+             _arg(limits, np.float64, "limits")]
+        return _native.ara_load_elts(self.ctx, n, *[x[0] for x in p])
+
+    def load_pool(self, pool) -> int:
+        """Load an :class:`ara_synth.ELTPool`-like object; returns the first handle."""
+        return self.load_elts(pool.offsets, pool.ids, pool.losses, pool.deductibles, pool.limits)
+
+    def define_layer(self, elt_handles: Sequence[int], occ_ret: float, occ_lim: float,
+                     agg_ret: float, agg_lim: float, precision: int = ARA_FP64) -> int:
+        h = np.ascontiguousarray(elt_handles, dtype=np.int32)
+        return _native.ara_define_layer(self.ctx, int(h.shape[0]), h.ctypes.data, occ_ret, occ_lim,
+                                        agg_ret, agg_lim, precision)
+
+    def release_layer(self, layer: int) -> None:
+        _native.ara_release_layer(self.ctx, layer)
+
+    # --------------------------------------------------------------- compute
+    def layer_ylt(self, layer: int, n_trials: Optional[int] = None, out=None, stream=None):
+        """YLT of one layer over the first n_trials trials.
+
+        ``out`` may be a float64 NumPy array (host) or a CUDA torch tensor
+        (device, filled asynchronously on the engine's stream); by default a
+        new NumPy array is returned.
+        """
+        n = self.n_trials if n_trials is None else int(n_trials)
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        if int(out.shape[0]) < n:
+            raise ValueError("out is shorter than n_trials")
+        p, keep = _arg(out, np.float64, "out")
+        if keep is not out:
+            raise TypeError("out must be a contiguous float64 array or tensor")
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+        _native.ara_layer_ylt(self.ctx, layer, n, p, int(handle or 0))
+        return out
+
+    def event_table(self, layer: int, out=None):
+        """The layer's per-event occurrence-net loss (float64, one per catalog event)."""
+        if out is None:
+            out = np.empty(self.catalog_size, dtype=np.float64)
+        p, keep = _arg(out, np.float64, "out")
+        if keep is not out:
+            raise TypeError("out must be a contiguous float64 array or tensor")
+        _native.ara_layer_event_table(self.ctx, layer, p)
+        return out
+
+    def pml_tvar(self, ylt, return_periods: Sequence[float]) -> Tuple[np.ndarray, np.ndarray]:
+        p, keep = _arg(ylt, np.float64, "ylt")
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        pml = np.zeros(rps.shape[0])
+        tvar = np.zeros(rps.shape[0])
+        _native.ara_pml_tvar(self.ctx, p, int(ylt.shape[0]), rps.ctypes.data, int(rps.shape[0]),
+                             pml.ctypes.data, tvar.ctypes.data)
+        return pml, tvar
+
+    # ----------------------------------------------------------- measurement
+    def set_kernel_timing(self, enable: bool = True) -> None:
+        _native.ara_set_kernel_timing(self.ctx, enable)
+
+    def kernel_timing(self, channel: int = ARA_TIMING_YLT):
+        """(launches, total milliseconds) recorded on a timing channel."""
+        return _native.ara_kernel_timing(self.ctx, channel)

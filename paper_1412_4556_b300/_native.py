@@ -1,0 +1,148 @@
+"""ctypes binding of the C ABI in include/ara.h (libara_b300.so).
+
+Every function here has the name of the C entry point it wraps and only
+marshals arguments: pointers are passed as integers (``ndarray.ctypes.data``
+or ``tensor.data_ptr()``), and a negative status raises :class:`AraError`
+with the library's message.  All computation happens in the CUDA library;
+there is no Python or CPU fallback, and importing fails when the library has
+not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libara_b300.so")
+
+ARA_OK = 0
+ARA_FP64 = 0
+ARA_FP32_TABLE = 1
+ARA_TIMING_YLT = 0
+ARA_TIMING_FOLD = 1
+ARA_TIMING_PML = 2
+
+STATUS_NAMES = {
+    0: "ARA_OK", -1: "ARA_E_INVALID_ARG", -2: "ARA_E_EVENT_RANGE", -3: "ARA_E_DUP_EVENT",
+    -4: "ARA_E_NOMEM", -5: "ARA_E_CUDA", -6: "ARA_E_TIMEOUT", -7: "ARA_E_NOT_FOUND",
+    -8: "ARA_E_STATE",
+}
+
+# C prototypes: name -> (restype, argtypes)
+_vp, _i32, _i64, _f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+PROTOTYPES = {
+    "ara_create": (_i32, [C.POINTER(C.c_void_p), C.c_int]),
+    "ara_destroy": (None, [_vp]),
+    "ara_last_error": (C.c_char_p, [_vp]),
+    "ara_status_string": (C.c_char_p, [_i32]),
+    "ara_set_stream": (_i32, [_vp, _vp]),
+    "ara_load_yet": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
+    "ara_load_elts": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, C.POINTER(_i32)]),
+    "ara_define_layer": (_i32, [_vp, _i32, _vp, _f64, _f64, _f64, _f64, _i32, C.POINTER(_i32)]),
+    "ara_release_layer": (_i32, [_vp, _i32]),
+    "ara_layer_event_table": (_i32, [_vp, _i32, _vp]),
+    "ara_layer_ylt": (_i32, [_vp, _i32, _i64, _vp, _vp]),
+    "ara_pml_tvar": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp, _vp]),
+    "ara_set_kernel_timing": (_i32, [_vp, _i32]),
+    "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
+}
+
+
+class AraError(RuntimeError):
+    """A negative status from the C ABI."""
+
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1412_4556_b300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load_library()
+
+
+def _check(ctx, status: int) -> None:
+    if status != ARA_OK:
+        msg = lib.ara_last_error(ctx)
+        raise AraError(status, msg.decode() if msg else "")
+
+
+def ara_create(device: int = 0) -> int:
+    out = C.c_void_p()
+    _check(None, lib.ara_create(C.byref(out), int(device)))
+    return out.value
+
+
+def ara_destroy(ctx: int) -> None:
+    lib.ara_destroy(ctx)
+
+
+def ara_last_error(ctx) -> str:
+    m = lib.ara_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ara_status_string(status: int) -> str:
+    return lib.ara_status_string(int(status)).decode()
+
+
+def ara_set_stream(ctx: int, stream: int) -> None:
+    _check(ctx, lib.ara_set_stream(ctx, stream or None))
+
+
+def ara_load_yet(ctx: int, catalog_size: int, n_trials: int, offsets: int, ids: int, ts: int) -> None:
+    _check(ctx, lib.ara_load_yet(ctx, int(catalog_size), int(n_trials), offsets or None, ids or None,
+                                 ts or None))
+
+
+def ara_load_elts(ctx: int, n_elts: int, offsets: int, ids: int, losses: int, deductibles: int,
+                  limits: int) -> int:
+    first = _i32(-1)
+    _check(ctx, lib.ara_load_elts(ctx, int(n_elts), offsets or None, ids or None, losses or None,
+                                  deductibles or None, limits or None, C.byref(first)))
+    return first.value
+
+
+def ara_define_layer(ctx: int, n_elts: int, handles: int, occ_ret: float, occ_lim: float,
+                     agg_ret: float, agg_lim: float, precision: int = ARA_FP64) -> int:
+    out = _i32(-1)
+    _check(ctx, lib.ara_define_layer(ctx, int(n_elts), handles or None, float(occ_ret), float(occ_lim),
+                                     float(agg_ret), float(agg_lim), int(precision), C.byref(out)))
+    return out.value
+
+
+def ara_release_layer(ctx: int, layer: int) -> None:
+    _check(ctx, lib.ara_release_layer(ctx, int(layer)))
+
+
+def ara_layer_event_table(ctx: int, layer: int, out: int) -> None:
+    _check(ctx, lib.ara_layer_event_table(ctx, int(layer), out or None))
+
+
+def ara_layer_ylt(ctx: int, layer: int, n_trials: int, ylt_out: int, stream: int = 0) -> None:
+    _check(ctx, lib.ara_layer_ylt(ctx, int(layer), int(n_trials), ylt_out or None, stream or None))
+
+
+def ara_pml_tvar(ctx: int, ylt: int, n: int, return_periods: int, n_rp: int, pml_out: int,
+                 tvar_out: int) -> None:
+    _check(ctx, lib.ara_pml_tvar(ctx, ylt or None, int(n), return_periods or None, int(n_rp),
+                                 pml_out or None, tvar_out or None))
+
+
+def ara_set_kernel_timing(ctx: int, enable: bool) -> None:
+    _check(ctx, lib.ara_set_kernel_timing(ctx, 1 if enable else 0))
+
+
+def ara_kernel_timing(ctx: int, channel: int):
+    n, ms = _i64(0), _f64(0.0)
+    _check(ctx, lib.ara_kernel_timing(ctx, int(channel), C.byref(n), C.byref(ms)))
+    return n.value, ms.value

@@ -1,0 +1,758 @@
+// Host side of the C ABI in include/ara.h: argument validation, device
+// buffers owned by the context, and the launch sequence of each call.
+//
+// Device memory layout of a context (all buffers library-owned):
+//   YET       offsets int64[N+1]; ids int32[M + 16] (zero tail so 16-byte
+//             loads past the last trial stay in bounds); ts float32[M] or none
+//   ELT pool  one block per ara_load_elts call: ids int32 (sorted by id per
+//             ELT), losses f64 (same order), fold bucket index int32
+//   layer     EltDesc[J]; fixed-point table 16 B x catalog; zero-skip bitmap
+//   scratch   YLT staging for host outputs, PML/TVaR workspace, error words
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ara.h"
+#include "ara_internal.cuh"
+
+using namespace ara;
+
+namespace {
+
+struct EltMeta {
+  int32_t count = 0;
+  double deductible = 0.0;
+  double limit = 0.0;
+  double max_loss = 0.0;
+  int32_t max_id = -1;
+  const int32_t *d_ids = nullptr;
+  const double *d_losses = nullptr;
+  const int32_t *d_bucket = nullptr;
+  int32_t nb = 0;
+};
+
+struct LayerRec {
+  bool live = false;
+  std::vector<int32_t> elts;
+  double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
+  int32_t precision = ARA_FP64;
+  EltDesc *d_desc = nullptr;
+  ulonglong2 *d_table = nullptr;
+  uint32_t *d_bitmap = nullptr;
+  int32_t table_catalog = 0;
+  BitmapLayout bm{0u, 0, 0};
+  int q = 0;
+  int64_t folded_version = -1;
+  double upper = 0.0;  // upper bound of any per-event table value
+};
+
+struct TimingChannel {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  int64_t launches = 0;
+  double total_ms = 0.0;
+};
+
+}  // namespace
+
+struct ara_ctx {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // YET
+  int64_t yet_version = 0;
+  bool yet_loaded = false;
+  int32_t catalog = 0;
+  int64_t n_trials = 0;
+  int64_t n_occ = 0;
+  int64_t max_trial_len = 0;
+  std::vector<int64_t> h_offsets;
+  int64_t *d_offsets = nullptr;
+  size_t cap_offsets = 0;
+  int32_t *d_ids = nullptr;
+  size_t cap_ids = 0;
+  float *d_ts = nullptr;
+  size_t cap_ts = 0;
+  bool has_ts = false;
+  // ELT pool
+  std::vector<EltMeta> elts;
+  std::vector<void *> elt_blocks;
+  // layers
+  std::vector<LayerRec> layers;
+  // scratch
+  double *d_ylt_stage = nullptr;
+  size_t cap_ylt_stage = 0;
+  double *d_sel_in = nullptr;
+  size_t cap_sel_in = 0;
+  void *d_sel_ws = nullptr;
+  double *d_sel_out = nullptr;
+  unsigned long long *d_counter = nullptr;  // validation counters
+  unsigned int *d_err = nullptr;            // PML/TVaR input check flag
+  // timing
+  bool timing = false;
+  TimingChannel chan[3];
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+ara_status fail(ara_ctx *c, ara_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+ara_status cuda_fail(ara_ctx *c, cudaError_t e, const char *what) {
+  ara_status st = (e == cudaErrorMemoryAllocation) ? ARA_E_NOMEM : ARA_E_CUDA;
+  cudaGetLastError();  // clear a sticky launch error where possible
+  return fail(c, st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define ARA_CUDA(ctx, expr, what)                   \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return cuda_fail((ctx), _e, (what)); \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t ensure(T **buf, size_t *cap, size_t count) {
+  if (*cap >= count && *buf) return cudaSuccess;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc((void **)buf, std::max<size_t>(count, 1) * sizeof(T));
+  if (e == cudaSuccess) *cap = std::max<size_t>(count, 1);
+  return e;
+}
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+bool limit_ok(double v) { return !std::isnan(v) && v >= 0.0; }
+
+// Timing helpers: record an event pair around a launch when enabled.
+struct TimedLaunch {
+  ara_ctx *c;
+  int ch;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedLaunch(ara_ctx *c_, int ch_, cudaStream_t s_) : c(c_), ch(ch_), s(s_) {
+    if (c->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, s);
+  }
+  void done() {
+    if (a && b) {
+      cudaEventRecord(b, s);
+      c->chan[ch].events.emplace_back(a, b);
+      a = b = nullptr;
+    }
+  }
+  ~TimedLaunch() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// Choose the zero-skip bitmap layout that fits the shared-memory budget of
+// the YLT kernel: one bit per event when the catalog fits, otherwise one bit
+// per event below a boundary F and one per 2^shift events above it.
+BitmapLayout plan_bitmap(int32_t catalog, size_t smem_bytes) {
+  BitmapLayout bm{0u, 0, 4};
+  const uint64_t budget = (uint64_t)(smem_bytes / 16) * 128;  // bits, whole uint4s
+  const uint64_t C = (uint64_t)std::max<int32_t>(catalog, 1);
+  uint64_t bits;
+  if (C <= budget) {
+    bits = C;
+  } else {
+    int k = 1;
+    while (((C + (1ull << k) - 1) >> k) > budget) ++k;
+    const uint64_t g = 1ull << k;
+    // largest F with F + ceil((C - F) / g) <= budget
+    uint64_t F = (budget * g > C) ? (budget * g - C) / (g - 1) : 0;
+    if (F > C) F = C;
+    while (F > 0 && F + ((C - F + g - 1) >> k) > budget) --F;
+    while (F > 0 && (C - 1) + (g - 1) * F >= (1ull << 32)) --F;  // keep e + add in 32 bits
+    bm.shift = k;
+    bm.add = (uint32_t)((g - 1) * F);
+    bits = (uint64_t)bitmap_pos((uint32_t)(C - 1), bm.add, k) + 1;
+  }
+  bm.words = (int32_t)(((bits + 127) / 128) * 4);
+  return bm;
+}
+
+size_t ylt_smem_budget(int device) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      optin <= 0) {
+    cudaGetLastError();
+    optin = 48 * 1024;
+  }
+  return (size_t)optin;
+}
+
+// Fixed-point exponent for a layer: any trial sum is at most upper * lmax;
+// keep the 128-bit integer below 2^127.
+bool choose_q(double upper, int64_t lmax, int *q) {
+  if (!(upper > 0.0) || lmax <= 0) {
+    *q = 0;
+    return true;
+  }
+  const double bound = upper * (double)lmax;
+  if (!std::isfinite(bound)) return false;
+  int e = 0;
+  std::frexp(bound, &e);  // bound < 2^e
+  *q = e + 1 - 127;
+  return true;
+}
+
+ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
+  int q = 0;
+  if (!choose_q(L.upper, std::max<int64_t>(c->max_trial_len, 1), &q))
+    return fail(c, ARA_E_INVALID_ARG,
+                "layer loss bound x longest trial overflows binary64; losses too large");
+  if (L.table_catalog != c->catalog || !L.d_table) {
+    if (L.d_table) cudaFree(L.d_table);
+    if (L.d_bitmap) cudaFree(L.d_bitmap);
+    L.d_table = nullptr;
+    L.d_bitmap = nullptr;
+    L.table_catalog = 0;
+    L.bm = plan_bitmap(c->catalog, ylt_smem_budget(c->device));
+    ARA_CUDA(c, cudaMalloc(&L.d_table, (size_t)std::max(c->catalog, 1) * sizeof(ulonglong2)),
+             "cudaMalloc(layer table)");
+    ARA_CUDA(c, cudaMalloc(&L.d_bitmap, (size_t)L.bm.words * 4), "cudaMalloc(layer bitmap)");
+    L.table_catalog = c->catalog;
+  }
+  L.q = q;
+  ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
+  TimedLaunch tl(c, ARA_TIMING_FOLD, s);
+  ARA_CUDA(c, launch_fold(L.d_desc, (int)L.elts.size(), c->catalog, L.occ_ret, L.occ_lim, q,
+                          L.d_table, L.d_bitmap, L.bm, nullptr, s),
+           "fold kernel launch");
+  tl.done();
+  L.folded_version = c->yet_version;
+  return ARA_OK;
+}
+
+void free_layer(LayerRec &L) {
+  if (L.d_desc) cudaFree(L.d_desc);
+  if (L.d_table) cudaFree(L.d_table);
+  if (L.d_bitmap) cudaFree(L.d_bitmap);
+  L = LayerRec();
+}
+
+ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out) {
+  if (layer < 0 || layer >= (int32_t)c->layers.size() || !c->layers[layer].live)
+    return fail(c, ARA_E_NOT_FOUND, "unknown layer handle %d", layer);
+  *out = &c->layers[layer];
+  return ARA_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char *ara_status_string(ara_status s) {
+  switch (s) {
+    case ARA_OK: return "ARA_OK";
+    case ARA_E_INVALID_ARG: return "ARA_E_INVALID_ARG";
+    case ARA_E_EVENT_RANGE: return "ARA_E_EVENT_RANGE";
+    case ARA_E_DUP_EVENT: return "ARA_E_DUP_EVENT";
+    case ARA_E_NOMEM: return "ARA_E_NOMEM";
+    case ARA_E_CUDA: return "ARA_E_CUDA";
+    case ARA_E_TIMEOUT: return "ARA_E_TIMEOUT";
+    case ARA_E_NOT_FOUND: return "ARA_E_NOT_FOUND";
+    case ARA_E_STATE: return "ARA_E_STATE";
+    default: return "ARA_E_UNKNOWN";
+  }
+}
+
+ara_status ara_create(ara_ctx **out, int device) {
+  if (!out) {
+    g_create_error = "ara_create: out is NULL";
+    return ARA_E_INVALID_ARG;
+  }
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    g_create_error = std::string("ara_create: no usable CUDA device (") +
+                     (e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0") + ")";
+    return ARA_E_CUDA;
+  }
+  if (device < 0 || device >= n) {
+    g_create_error = "ara_create: device index out of range";
+    return ARA_E_INVALID_ARG;
+  }
+  ara_ctx *c = new (std::nothrow) ara_ctx();
+  if (!c) {
+    g_create_error = "ara_create: out of host memory";
+    return ARA_E_NOMEM;
+  }
+  c->device = device;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_sel_ws, select_workspace_bytes(kMaxReturnPeriods));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_sel_out, 2 * kMaxReturnPeriods * sizeof(double));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("ara_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    ara_destroy(c);
+    return e == cudaErrorMemoryAllocation ? ARA_E_NOMEM : ARA_E_CUDA;
+  }
+  c->stream = c->own_stream;
+  *out = c;
+  return ARA_OK;
+}
+
+void ara_destroy(ara_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto &L : c->layers) free_layer(L);
+  for (void *p : c->elt_blocks) cudaFree(p);
+  cudaFree(c->d_offsets);
+  cudaFree(c->d_ids);
+  cudaFree(c->d_ts);
+  cudaFree(c->d_ylt_stage);
+  cudaFree(c->d_sel_in);
+  cudaFree(c->d_sel_ws);
+  cudaFree(c->d_sel_out);
+  cudaFree(c->d_counter);
+  cudaFree(c->d_err);
+  for (auto &ch : c->chan)
+    for (auto &ev : ch.events) {
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  cudaGetLastError();
+  delete c;
+}
+
+const char *ara_last_error(const ara_ctx *c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+ara_status ara_set_stream(ara_ctx *c, void *stream) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return ARA_OK;
+}
+
+ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int64_t *offsets,
+                        const int32_t *ids, const float *ts) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (catalog < 1) return fail(c, ARA_E_INVALID_ARG, "catalog_size must be >= 1 (got %d)", catalog);
+  if (n_trials < 0 || n_trials > (int64_t)1 << 40)
+    return fail(c, ARA_E_INVALID_ARG, "n_trials out of range (got %lld)", (long long)n_trials);
+  if (!offsets) return fail(c, ARA_E_INVALID_ARG, "trial_offsets is NULL");
+  cudaStream_t s = c->stream;
+  // Offsets: validated on the host (a device array is brought back first).
+  std::vector<int64_t> h((size_t)n_trials + 1);
+  ARA_CUDA(c, cudaMemcpyAsync(h.data(), offsets, h.size() * sizeof(int64_t), cudaMemcpyDefault, s),
+           "copy trial_offsets");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (h[0] != 0) return fail(c, ARA_E_INVALID_ARG, "trial_offsets[0] must be 0");
+  int64_t lmax = 0;
+  for (int64_t t = 0; t < n_trials; ++t) {
+    const int64_t d = h[t + 1] - h[t];
+    if (d < 0) return fail(c, ARA_E_INVALID_ARG, "trial_offsets decreases at trial %lld", (long long)t);
+    lmax = std::max(lmax, d);
+  }
+  const int64_t M = h[n_trials];
+  if (lmax > ((int64_t)1 << 31) - 1024)
+    return fail(c, ARA_E_INVALID_ARG, "a trial holds %lld events; at most 2^31-1024 are supported",
+                (long long)lmax);
+  if (M > 0 && !ids) return fail(c, ARA_E_INVALID_ARG, "event_ids is NULL but offsets hold %lld events", (long long)M);
+  // ELTs already loaded must still fit the new catalog.
+  for (size_t j = 0; j < c->elts.size(); ++j)
+    if (c->elts[j].max_id >= catalog)
+      return fail(c, ARA_E_EVENT_RANGE, "loaded ELT %zu holds event id %d outside the new catalog of %d",
+                  j, c->elts[j].max_id, catalog);
+  // The YET is replaced in place (it can be several GB): from here on a
+  // failure leaves the context without a YET.
+  c->yet_loaded = false;
+  c->yet_version++;
+  cudaError_t e = ensure(&c->d_offsets, &c->cap_offsets, (size_t)n_trials + 1);
+  if (e == cudaSuccess) e = ensure(&c->d_ids, &c->cap_ids, (size_t)M + 16);
+  if (e == cudaSuccess && ts) e = ensure(&c->d_ts, &c->cap_ts, (size_t)std::max<int64_t>(M, 1));
+  if (e != cudaSuccess) return cuda_fail(c, e, "allocate YET buffers");
+  e = cudaMemcpyAsync(c->d_offsets, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && M > 0)
+    e = cudaMemcpyAsync(c->d_ids, ids, (size_t)M * sizeof(int32_t), cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ids + M, 0, 16 * sizeof(int32_t), s);
+  if (e == cudaSuccess && ts && M > 0)
+    e = cudaMemcpyAsync(c->d_ts, ts, (size_t)M * sizeof(float), cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_check_ids(c->d_ids, M, catalog, c->d_counter, s);
+  if (e == cudaSuccess && ts) e = launch_check_ts(c->d_offsets, n_trials, c->d_ts, c->d_counter + 1, s);
+  unsigned long long bad[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_counter, sizeof(bad), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load YET");
+  if (bad[0]) return fail(c, ARA_E_EVENT_RANGE, "%llu event ids lie outside [0, %d)", bad[0], catalog);
+  if (bad[1])
+    return fail(c, ARA_E_INVALID_ARG,
+                "%llu time-stamps are non-finite or out of ascending order within a trial", bad[1]);
+  c->has_ts = ts != nullptr;
+  c->yet_loaded = true;
+  c->catalog = catalog;
+  c->n_trials = n_trials;
+  c->n_occ = M;
+  c->max_trial_len = lmax;
+  c->h_offsets.swap(h);
+  return ARA_OK;
+}
+
+ara_status ara_load_elts(ara_ctx *c, int32_t n_elts, const int64_t *off, const int32_t *ids,
+                         const double *losses, const double *ded, const double *lim,
+                         int32_t *first_handle) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "load the YET before ELTs (ids are checked against its catalog)");
+  if (n_elts < 1) return fail(c, ARA_E_INVALID_ARG, "n_elts must be >= 1");
+  if (!off || !ded || !lim || !first_handle) return fail(c, ARA_E_INVALID_ARG, "NULL argument");
+  if ((int64_t)c->elts.size() + n_elts > ((int64_t)1 << 30))
+    return fail(c, ARA_E_INVALID_ARG, "ELT pool is full");
+  for (const void *p : {(const void *)off, (const void *)ids, (const void *)losses, (const void *)ded,
+                        (const void *)lim})
+    if (p && is_device_ptr(p)) return fail(c, ARA_E_INVALID_ARG, "ELT arrays must be host pointers");
+  if (off[0] != 0) return fail(c, ARA_E_INVALID_ARG, "elt_offsets[0] must be 0");
+  for (int32_t j = 0; j < n_elts; ++j) {
+    if (off[j + 1] < off[j]) return fail(c, ARA_E_INVALID_ARG, "elt_offsets decreases at ELT %d", j);
+    if (off[j + 1] - off[j] > (int64_t)c->catalog)
+      return fail(c, ARA_E_DUP_EVENT, "ELT %d has more entries than catalog events", j);
+    if (!finite_nonneg(ded[j])) return fail(c, ARA_E_INVALID_ARG, "deductible of ELT %d must be finite and >= 0", j);
+    if (!limit_ok(lim[j])) return fail(c, ARA_E_INVALID_ARG, "limit of ELT %d must be >= 0 (inf allowed)", j);
+  }
+  const int64_t total = off[n_elts];
+  if (total > 0 && (!ids || !losses)) return fail(c, ARA_E_INVALID_ARG, "event_ids/losses NULL");
+  // Sort each ELT by event id, reject duplicates, build the fold buckets.
+  std::vector<int32_t> s_ids((size_t)total);
+  std::vector<double> s_loss((size_t)total);
+  std::vector<int32_t> bucket;
+  std::vector<size_t> bucket_start((size_t)n_elts);
+  std::vector<EltMeta> meta((size_t)n_elts);
+  std::vector<int64_t> perm;
+  for (int32_t j = 0; j < n_elts; ++j) {
+    const int64_t a = off[j], b = off[j + 1], n = b - a;
+    perm.resize((size_t)n);
+    std::iota(perm.begin(), perm.end(), a);
+    for (int64_t i = a; i < b; ++i) {
+      if (ids[i] < 0 || ids[i] >= c->catalog)
+        return fail(c, ARA_E_EVENT_RANGE, "ELT %d: event id %d outside [0, %d)", j, ids[i], c->catalog);
+      if (!finite_nonneg(losses[i]))
+        return fail(c, ARA_E_INVALID_ARG, "ELT %d: loss at position %lld must be finite and >= 0", j,
+                    (long long)(i - a));
+    }
+    std::sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
+    double mx = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      s_ids[(size_t)(a + i)] = ids[perm[(size_t)i]];
+      s_loss[(size_t)(a + i)] = losses[perm[(size_t)i]];
+      mx = std::max(mx, s_loss[(size_t)(a + i)]);
+      if (i > 0 && s_ids[(size_t)(a + i)] == s_ids[(size_t)(a + i - 1)])
+        return fail(c, ARA_E_DUP_EVENT, "ELT %d: event id %d appears twice", j, s_ids[(size_t)(a + i)]);
+    }
+    EltMeta &m = meta[(size_t)j];
+    m.count = (int32_t)n;
+    m.deductible = ded[j];
+    m.limit = lim[j];
+    m.max_loss = mx;
+    m.max_id = n ? s_ids[(size_t)(b - 1)] : -1;
+    m.nb = n ? m.max_id / kFoldEventsPerCta + 1 : 0;
+    bucket_start[(size_t)j] = bucket.size();
+    int64_t i = 0;
+    for (int32_t bk = 0; bk <= m.nb; ++bk) {
+      const int64_t lo = (int64_t)bk * kFoldEventsPerCta;
+      while (i < n && s_ids[(size_t)(a + i)] < lo) ++i;
+      bucket.push_back((int32_t)i);
+    }
+  }
+  // One device block: ids | losses | buckets (8-byte aligned sections).
+  const size_t n_ids_b = ((size_t)total * 4 + 7) / 8 * 8;
+  const size_t n_loss_b = (size_t)total * 8;
+  const size_t n_bk_b = bucket.size() * 4;
+  char *blk = nullptr;
+  ARA_CUDA(c, cudaMalloc(&blk, std::max<size_t>(n_ids_b + n_loss_b + n_bk_b, 8)), "cudaMalloc(ELT pool)");
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemcpyAsync(blk, s_ids.data(), (size_t)total * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(blk + n_ids_b, s_loss.data(), n_loss_b, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(blk + n_ids_b + n_loss_b, bucket.data(), n_bk_b, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return cuda_fail(c, e, "upload ELTs");
+  }
+  c->elt_blocks.push_back(blk);
+  *first_handle = (int32_t)c->elts.size();
+  for (int32_t j = 0; j < n_elts; ++j) {
+    EltMeta m = meta[(size_t)j];
+    m.d_ids = reinterpret_cast<const int32_t *>(blk) + off[j];
+    m.d_losses = reinterpret_cast<const double *>(blk + n_ids_b) + off[j];
+    m.d_bucket = reinterpret_cast<const int32_t *>(blk + n_ids_b + n_loss_b) + bucket_start[(size_t)j];
+    c->elts.push_back(m);
+  }
+  return ARA_OK;
+}
+
+ara_status ara_define_layer(ara_ctx *c, int32_t n_elts, const int32_t *handles, double occ_ret,
+                            double occ_lim, double agg_ret, double agg_lim, int32_t precision,
+                            int32_t *layer_out) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  if (!handles || !layer_out) return fail(c, ARA_E_INVALID_ARG, "NULL argument");
+  if (n_elts < 1 || n_elts > kMaxLayerElts)
+    return fail(c, ARA_E_INVALID_ARG, "a layer covers 1..%d ELTs (got %d)", kMaxLayerElts, n_elts);
+  if (precision != ARA_FP64)
+    return fail(c, ARA_E_INVALID_ARG, "precision %d is not available; use ARA_FP64", precision);
+  if (!finite_nonneg(occ_ret) || !finite_nonneg(agg_ret))
+    return fail(c, ARA_E_INVALID_ARG, "retentions must be finite and >= 0");
+  if (!limit_ok(occ_lim) || !limit_ok(agg_lim))
+    return fail(c, ARA_E_INVALID_ARG, "limits must be >= 0 (inf allowed)");
+  std::vector<int32_t> el(handles, handles + n_elts);
+  {
+    std::vector<int32_t> sorted = el;
+    std::sort(sorted.begin(), sorted.end());
+    for (size_t i = 0; i < sorted.size(); ++i) {
+      if (sorted[i] < 0 || sorted[i] >= (int32_t)c->elts.size())
+        return fail(c, ARA_E_NOT_FOUND, "unknown ELT handle %d", sorted[i]);
+      if (i && sorted[i] == sorted[i - 1])
+        return fail(c, ARA_E_INVALID_ARG, "ELT handle %d appears twice in the layer", sorted[i]);
+    }
+  }
+  LayerRec L;
+  L.live = true;
+  L.elts = el;
+  L.occ_ret = occ_ret;
+  L.occ_lim = occ_lim;
+  L.agg_ret = agg_ret;
+  L.agg_lim = agg_lim;
+  L.precision = precision;
+  // Upper bound of any per-event value: FT1 <= min(loss, limit), summed over
+  // the ELTs, capped by the occurrence limit.
+  double up = 0.0;
+  std::vector<EltDesc> desc((size_t)n_elts);
+  for (int32_t j = 0; j < n_elts; ++j) {
+    const EltMeta &m = c->elts[(size_t)el[(size_t)j]];
+    up += std::min(m.max_loss, m.limit);
+    desc[(size_t)j] = EltDesc{m.d_ids, m.d_losses, m.d_bucket, m.nb, m.count, m.deductible, m.limit};
+  }
+  L.upper = std::min(up * (1.0 + 1e-12), occ_lim);
+  ARA_CUDA(c, cudaMalloc(&L.d_desc, desc.size() * sizeof(EltDesc)), "cudaMalloc(layer ELT list)");
+  cudaError_t e = cudaMemcpyAsync(L.d_desc, desc.data(), desc.size() * sizeof(EltDesc),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_layer(L);
+    return cuda_fail(c, e, "upload layer ELT list");
+  }
+  ara_status st = fold_layer(c, L, c->stream);
+  if (st != ARA_OK) {
+    free_layer(L);
+    return st;
+  }
+  int32_t id = -1;
+  for (size_t i = 0; i < c->layers.size(); ++i)
+    if (!c->layers[i].live) {
+      id = (int32_t)i;
+      break;
+    }
+  if (id < 0) {
+    id = (int32_t)c->layers.size();
+    c->layers.emplace_back();
+  }
+  c->layers[(size_t)id] = L;
+  *layer_out = id;
+  return ARA_OK;
+}
+
+ara_status ara_release_layer(ara_ctx *c, int32_t layer) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  LayerRec *L = nullptr;
+  ara_status st = get_layer(c, layer, &L);
+  if (st) return st;
+  ARA_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  free_layer(*L);
+  return ARA_OK;
+}
+
+ara_status ara_layer_event_table(ara_ctx *c, int32_t layer, double *out) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  LayerRec *L = nullptr;
+  ara_status st = get_layer(c, layer, &L);
+  if (st) return st;
+  if (!out) return fail(c, ARA_E_INVALID_ARG, "out is NULL");
+  cudaStream_t s = c->stream;
+  const bool dev = is_device_ptr(out);
+  double *dst = out;
+  if (!dev) {
+    ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, (size_t)c->catalog), "stage buffer");
+    dst = c->d_ylt_stage;
+  }
+  ARA_CUDA(c, launch_fold(L->d_desc, (int)L->elts.size(), c->catalog, L->occ_ret, L->occ_lim, 0,
+                          nullptr, nullptr, L->bm, dst, s),
+           "fold kernel launch");
+  if (!dev) {
+    ARA_CUDA(c, cudaMemcpyAsync(out, dst, (size_t)c->catalog * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copy event table");
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
+  return ARA_OK;
+}
+
+ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *ylt_out,
+                         void *cuda_stream) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  LayerRec *L = nullptr;
+  ara_status st = get_layer(c, layer, &L);
+  if (st) return st;
+  if (n_trials < 0 || n_trials > c->n_trials)
+    return fail(c, ARA_E_INVALID_ARG, "n_trials %lld outside [0, %lld]", (long long)n_trials,
+                (long long)c->n_trials);
+  if (n_trials > 0 && !ylt_out) return fail(c, ARA_E_INVALID_ARG, "ylt_out is NULL");
+  if (n_trials == 0) return ARA_OK;
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+  if (L->folded_version != c->yet_version) {
+    st = fold_layer(c, *L, s);
+    if (st) return st;
+  }
+  const bool dev = is_device_ptr(ylt_out);
+  double *dst = ylt_out;
+  if (!dev) {
+    ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, (size_t)n_trials), "stage buffer");
+    dst = c->d_ylt_stage;
+  }
+  const double mean = (double)c->h_offsets[(size_t)n_trials] / (double)n_trials;
+  YltLaunch cfg;
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean, &cfg), "plan YLT launch");
+  TimedLaunch tl(c, ARA_TIMING_YLT, s);
+  ARA_CUDA(c, launch_ylt_fp64(c->d_offsets, c->d_ids, n_trials, L->d_table, L->d_bitmap, L->bm, L->q,
+                              L->agg_ret, L->agg_lim, dst, cfg, s),
+           "YLT kernel launch");
+  tl.done();
+  if (!dev) {
+    ARA_CUDA(c, cudaMemcpyAsync(ylt_out, dst, (size_t)n_trials * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copy YLT");
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
+  return ARA_OK;
+}
+
+ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *rps, int32_t n_rp,
+                        double *pml_out, double *tvar_out) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
+  if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps || !pml_out || !tvar_out)
+    return fail(c, ARA_E_INVALID_ARG, "need 1..%d return periods and output arrays", kMaxReturnPeriods);
+  int64_t k[kMaxReturnPeriods];
+  for (int32_t r = 0; r < n_rp; ++r) {
+    if (!(rps[r] >= 1.0)) return fail(c, ARA_E_INVALID_ARG, "return period %d must be >= 1", r);
+    const double kk = std::floor((double)n / rps[r]);
+    if (kk < 1.0) return fail(c, ARA_E_INVALID_ARG, "return period %g exceeds the %lld trials", rps[r], (long long)n);
+    k[r] = (int64_t)kk;
+  }
+  cudaStream_t s = c->stream;
+  const double *src = ylt;
+  if (!is_device_ptr(ylt)) {
+    ARA_CUDA(c, ensure(&c->d_sel_in, &c->cap_sel_in, (size_t)n), "selection input buffer");
+    ARA_CUDA(c, cudaMemcpyAsync(c->d_sel_in, ylt, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s),
+             "copy YLT");
+    src = c->d_sel_in;
+  }
+  ARA_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
+  TimedLaunch tl(c, ARA_TIMING_PML, s);
+  ARA_CUDA(c, launch_pml_tvar(src, n, k, n_rp, c->d_sel_ws, c->d_sel_out, c->d_err, c->device, s),
+           "PML/TVaR kernels");
+  tl.done();
+  double out[2 * kMaxReturnPeriods];
+  unsigned int bad = 0;
+  ARA_CUDA(c, cudaMemcpyAsync(out, c->d_sel_out, 2 * (size_t)n_rp * sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copy PML/TVaR");
+  ARA_CUDA(c, cudaMemcpyAsync(&bad, c->d_err, sizeof(bad), cudaMemcpyDeviceToHost, s), "copy flag");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (bad) return fail(c, ARA_E_INVALID_ARG, "trial losses must be finite and >= 0");
+  for (int32_t r = 0; r < n_rp; ++r) {
+    pml_out[r] = out[r];
+    tvar_out[r] = out[n_rp + r];
+  }
+  return ARA_OK;
+}
+
+ara_status ara_set_kernel_timing(ara_ctx *c, int32_t enable) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  for (auto &ch : c->chan) {
+    for (auto &ev : ch.events) {
+      cudaEventSynchronize(ev.second);
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+    ch.events.clear();
+    ch.launches = 0;
+    ch.total_ms = 0.0;
+  }
+  c->timing = enable != 0;
+  return ARA_OK;
+}
+
+ara_status ara_kernel_timing(ara_ctx *c, int32_t channel, int64_t *launches, double *total_ms) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  if (channel < 0 || channel > 2 || !launches || !total_ms)
+    return fail(c, ARA_E_INVALID_ARG, "bad timing channel or NULL output");
+  TimingChannel &ch = c->chan[channel];
+  for (auto &ev : ch.events) {
+    ARA_CUDA(c, cudaEventSynchronize(ev.second), "cudaEventSynchronize");
+    float ms = 0.f;
+    ARA_CUDA(c, cudaEventElapsedTime(&ms, ev.first, ev.second), "cudaEventElapsedTime");
+    ch.total_ms += ms;
+    ch.launches += 1;
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  ch.events.clear();
+  *launches = ch.launches;
+  *total_ms = ch.total_ms;
+  return ARA_OK;
+}
+
+}  // extern "C"

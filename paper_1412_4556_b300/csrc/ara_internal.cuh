@@ -1,0 +1,161 @@
+// Internal declarations shared by the engine's translation units: device
+// helpers for exact fixed-point accumulation, the per-ELT descriptor the fold
+// kernel reads, and the launch wrappers each kernel file exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ara {
+
+// ---------------------------------------------------------------- tuning
+constexpr int kFoldEventsPerCta = 2048;  // catalog events folded by one CTA
+constexpr int kFoldThreads = 256;
+constexpr int kFoldStage = 2048;         // ELT entries staged in smem per chunk
+constexpr int kMaxLayerElts = 1024;      // ELTs one layer may cover
+constexpr int kYltThreads = 1024;        // threads per YLT CTA (32 warps)
+constexpr int kMaxReturnPeriods = 16;
+constexpr int kSelectThreads = 512;
+
+// ------------------------------------------------------ ELT descriptor
+// One ELT of a layer, as the fold kernel sees it.  ids are sorted ascending
+// and distinct; bucket[b] is the first index whose id >= b * kFoldEventsPerCta
+// for b in [0, nb], with bucket[nb] == count.
+struct EltDesc {
+  const int32_t *ids;
+  const double *losses;
+  const int32_t *bucket;
+  int32_t nb;
+  int32_t count;
+  double deductible;
+  double limit;
+};
+
+// Zero-skip bitmap layout.  Event e maps to bit pos(e) = min(e, (e + add) >> shift):
+// events below a boundary F get one bit each, the rest share one bit per
+// 2^shift events (add = (2^shift - 1) * F).  A set bit means "some event of
+// this bit may have a nonzero loss"; a clear bit proves every event of it has
+// loss exactly zero, so skipping it leaves an exact sum unchanged.
+struct BitmapLayout {
+  uint32_t add;
+  int32_t shift;
+  int32_t words;  // 32-bit words, rounded up to a multiple of 4
+};
+
+__host__ __device__ inline uint32_t bitmap_pos(uint32_t e, uint32_t add, int shift) {
+  uint32_t c = (e + add) >> shift;
+  return e < c ? e : c;
+}
+
+// ------------------------------------------------ 128-bit fixed point
+// A non-negative value v is held as the unsigned 128-bit integer
+// round(v / 2^q); sums of such integers are exact and independent of order.
+struct U128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void add128(U128 &a, unsigned long long lo, unsigned long long hi) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(lo), "l"(hi));
+}
+
+// x: finite, >= 0.  The caller picks q so that x / 2^q < 2^127.  Values whose
+// last mantissa bit is worth at least 2^q convert exactly; smaller ones round
+// to the nearest multiple of 2^q (ties up).
+__device__ __forceinline__ U128 to_fixed(double x, int q) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int E = (int)(b >> 52);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (E == 0)
+    E = 1;  // subnormal
+  else
+    m |= 1ull << 52;
+  U128 r{0ull, 0ull};
+  if (m == 0) return r;
+  int s = E - 1075 - q;  // x = m * 2^(E-1075) = (m << s) * 2^q
+  if (s >= 64) {
+    r.hi = m << (s - 64);
+  } else if (s > 0) {
+    r.lo = m << s;
+    r.hi = m >> (64 - s);
+  } else if (s == 0) {
+    r.lo = m;
+  } else {
+    int rs = -s;
+    if (rs <= 53) r.lo = (m + (1ull << (rs - 1))) >> rs;
+  }
+  return r;
+}
+
+// Correctly rounded binary64 value of a * 2^q.
+__device__ __forceinline__ double from_fixed(U128 a, int q) {
+  if ((a.hi | a.lo) == 0ull) return 0.0;
+  int lz = a.hi ? __clzll((long long)a.hi) : 64 + __clzll((long long)a.lo);
+  unsigned long long top, rest;
+  if (lz == 0) {
+    top = a.hi;
+    rest = a.lo;
+  } else if (lz < 64) {
+    top = (a.hi << lz) | (a.lo >> (64 - lz));
+    rest = a.lo << lz;
+  } else if (lz == 64) {
+    top = a.lo;
+    rest = 0ull;
+  } else {
+    top = a.lo << (lz - 64);
+    rest = 0ull;
+  }
+  top |= (rest != 0ull) ? 1ull : 0ull;  // sticky bit keeps round-to-nearest-even exact
+  double d = __ull2double_rn(top);
+  return ldexp(d, q + 64 - lz);
+}
+
+__device__ __forceinline__ U128 shfl_xor_u128(U128 v, int m) {
+  U128 r;
+  r.lo = __shfl_xor_sync(0xFFFFFFFFu, v.lo, m);
+  r.hi = __shfl_xor_sync(0xFFFFFFFFu, v.hi, m);
+  return r;
+}
+
+__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    U128 o = shfl_xor_u128(v, m);
+    add128(v, o.lo, o.hi);
+  }
+  return v;
+}
+
+// --------------------------------------------------------- launchers
+// Each returns cudaSuccess or the launch error.
+cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
+                        double occ_lim, int q, ulonglong2 *table, uint32_t *bitmap,
+                        BitmapLayout bm, double *f64_out, cudaStream_t s);
+
+struct YltLaunch {
+  int blocks;
+  int threads;
+  size_t smem;
+  int unroll;
+};
+
+cudaError_t launch_ylt_fp64(const int64_t *offsets, const int32_t *ids, int64_t n_trials,
+                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                            int q, double agg_ret, double agg_lim, double *ylt,
+                            const YltLaunch &cfg, cudaStream_t s);
+
+// Pick the launch shape of the YLT kernel for a bitmap of bm.words words.
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_trial_len, YltLaunch *out);
+
+cudaError_t launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog,
+                             unsigned long long *bad_count, cudaStream_t s);
+
+cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const float *ts,
+                            unsigned long long *bad_count, cudaStream_t s);
+
+// PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes.
+size_t select_workspace_bytes(int n_rp);
+cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp,
+                            void *ws, double *out_pml_tvar /* device, 2*n_rp */,
+                            unsigned int *err_flag, int device, cudaStream_t s);
+
+}  // namespace ara

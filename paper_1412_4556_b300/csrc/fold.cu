@@ -1,0 +1,117 @@
+// Per-layer pre-pass: fold the layer's ELT terms and occurrence terms into
+// one table over the catalog.
+//
+// Algorithm 1 (Section III), steps 1-3, depend only on the event id, so for
+// every catalog event e the occurrence-net loss
+//     o(e) = FT2( sum over the layer's ELTs j, in layer order, of FT1_j(DAT_j[e]) )
+// is computed once here instead of once per occurrence.  DAT_j[e] is the
+// ELT's loss for e, or 0 when e is absent (Section IV-B, direct access
+// tables); an absent ELT adds FT1_j(0) = +0.0, which leaves the running sum's
+// bits unchanged, so only the present entries are added -- in layer order --
+// and the result is bit-identical to the sequential per-event ELT loop.
+//
+// One CTA owns kFoldEventsPerCta consecutive catalog events and keeps their
+// running sums in shared memory.  Each ELT is stored sorted by event id with
+// a bucket index, so the CTA finds its slice of every ELT with two loads.
+// Outputs per event: the 128-bit fixed-point table entry used by the YLT
+// kernel, one bit of the zero-skip bitmap, and (optionally) the FP64 value.
+#include "ara_internal.cuh"
+
+namespace ara {
+
+__device__ __forceinline__ double elt_terms(double loss, double deductible, double limit) {
+  // FT1 read as deductible then limit: min(max(l - D, 0), Lim)
+  return fmin(fmax(__dsub_rn(loss, deductible), 0.0), limit);
+}
+
+__global__ void __launch_bounds__(kFoldThreads)
+fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
+            double occ_lim, int q, ulonglong2 *__restrict__ table, uint32_t *__restrict__ bitmap,
+            uint32_t bm_add, int bm_shift, double *__restrict__ f64_out) {
+  __shared__ double x[kFoldEventsPerCta];
+  __shared__ int32_t seg[kMaxLayerElts + 1];    // prefix sums of slice lengths
+  __shared__ int32_t first[kMaxLayerElts];      // slice start inside ELT j
+  __shared__ uint16_t st_off[kFoldStage];
+  __shared__ double st_val[kFoldStage];
+
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const int32_t e0 = b * kFoldEventsPerCta;
+
+  for (int i = tid; i < kFoldEventsPerCta; i += kFoldThreads) x[i] = 0.0;
+  for (int j = tid; j < n_elts; j += kFoldThreads) {
+    const EltDesc d = elts[j];
+    int32_t a = d.count, z = d.count;
+    if (b < d.nb) {
+      a = d.bucket[b];
+      z = d.bucket[b + 1];
+    }
+    first[j] = a;
+    seg[j + 1] = z - a;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    seg[0] = 0;
+    for (int j = 0; j < n_elts; ++j) seg[j + 1] += seg[j];
+  }
+  __syncthreads();
+  const int32_t total = seg[n_elts];
+
+  for (int32_t base = 0; base < total; base += kFoldStage) {
+    const int32_t end = min(total, base + kFoldStage);
+    for (int32_t f = base + tid; f < end; f += kFoldThreads) {
+      int lo = 0, hi = n_elts;  // find j with seg[j] <= f < seg[j+1]
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (seg[mid] <= f) lo = mid; else hi = mid;
+      }
+      const EltDesc &d = elts[lo];
+      const int32_t i = first[lo] + (f - seg[lo]);
+      st_off[f - base] = (uint16_t)(d.ids[i] - e0);
+      st_val[f - base] = elt_terms(d.losses[i], d.deductible, d.limit);
+    }
+    __syncthreads();
+    // Apply the staged entries ELT by ELT, in layer order.  Within one ELT
+    // the event ids are distinct, so its entries touch distinct sums.
+    int j = 0;
+    while (seg[j + 1] <= base) ++j;
+    for (; j < n_elts && seg[j] < end; ++j) {
+      const int32_t lo = max(seg[j], base), hi = min(seg[j + 1], end);
+      if (lo >= hi) continue;  // uniform across the CTA
+      for (int32_t f = lo + tid; f < hi; f += kFoldThreads) {
+        const int o = st_off[f - base];
+        x[o] = __dadd_rn(x[o], st_val[f - base]);
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+
+  for (int i = tid; i < kFoldEventsPerCta; i += kFoldThreads) {
+    const int32_t e = e0 + i;
+    if (e >= catalog) break;
+    // FT2 read as occurrence retention then limit: min(max(x - OccR, 0), OccL)
+    const double o = fmin(fmax(__dsub_rn(x[i], occ_ret), 0.0), occ_lim);
+    if (f64_out) f64_out[e] = o;
+    if (table) {
+      const U128 v = to_fixed(o, q);
+      table[e] = make_ulonglong2(v.lo, v.hi);
+      if ((v.lo | v.hi) != 0ull) {
+        const uint32_t p = bitmap_pos((uint32_t)e, bm_add, bm_shift);
+        atomicOr(bitmap + (p >> 5), 1u << (p & 31));
+      }
+    }
+  }
+}
+
+cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
+                        double occ_lim, int q, ulonglong2 *table, uint32_t *bitmap,
+                        BitmapLayout bm, double *f64_out, cudaStream_t s) {
+  if (catalog <= 0) return cudaSuccess;
+  const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
+  fold_kernel<<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q, table,
+                                               bitmap, bm.add, bm.shift, f64_out);
+  return cudaGetLastError();
+}
+
+}  // namespace ara

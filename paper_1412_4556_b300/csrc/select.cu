@@ -1,0 +1,226 @@
+// PML and TVaR from a Year Loss Table (Section III: "risk metrics such as the
+// Probable Maximum Loss (PML) and the Tail Value-at-Risk (TVaR) ... can be
+// derived from the output of the analysis").
+//
+// For each return period r with k_r = floor(n / RP_r):
+//   PML_r  = the k_r-th largest trial loss
+//   TVaR_r = (sum of the k_r largest trial losses) / k_r
+//
+// Trial losses are finite and >= 0, so their binary64 bit patterns order like
+// the values.  An MSD radix selection (8 passes of 8 bits) finds the exact
+// k_r-th largest key tau_r for every r at once: each pass histograms the keys
+// that share the prefix chosen so far, and the last CTA to finish a pass
+// picks the next digit ("last block done" counter, no waiting).  A final pass
+// sums the keys above tau_r exactly in 128-bit fixed point and adds
+// (k_r - count) copies of tau_r, so ties at the threshold are handled
+// exactly; one rounding to binary64 and one division give TVaR.
+#include "ara_internal.cuh"
+
+namespace ara {
+
+struct SelState {
+  unsigned long long prefix[kMaxReturnPeriods];
+  long long k_rem[kMaxReturnPeriods];
+  long long k[kMaxReturnPeriods];
+  unsigned long long cnt_gt[kMaxReturnPeriods];
+  unsigned long long acc_lo[kMaxReturnPeriods];
+  unsigned long long acc_hi[kMaxReturnPeriods];
+  unsigned long long max_key;
+  unsigned int done_pass;
+  unsigned int done_sum;
+  unsigned int hist[kMaxReturnPeriods][256];
+};
+
+size_t select_workspace_bytes(int) { return sizeof(SelState); }
+
+struct KArgs {
+  long long k[kMaxReturnPeriods];
+};
+
+__global__ void select_init_kernel(SelState *st, KArgs ka, int n_rp) {
+  const int tid = threadIdx.x;
+  unsigned int *h = &st->hist[0][0];
+  for (int i = tid; i < kMaxReturnPeriods * 256; i += blockDim.x) h[i] = 0u;
+  if (tid < kMaxReturnPeriods) {
+    const long long k = tid < n_rp ? ka.k[tid] : 1;
+    st->prefix[tid] = 0ull;
+    st->k_rem[tid] = k;
+    st->k[tid] = k;
+    st->cnt_gt[tid] = 0ull;
+    st->acc_lo[tid] = 0ull;
+    st->acc_hi[tid] = 0ull;
+  }
+  if (tid == 0) {
+    st->max_key = 0ull;
+    st->done_pass = 0u;
+    st->done_sum = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(kSelectThreads)
+select_pass_kernel(const double *__restrict__ y, int64_t n, int n_rp, int pass, SelState *st,
+                   unsigned int *err) {
+  __shared__ unsigned int sh[kMaxReturnPeriods][256];
+  __shared__ unsigned long long s_prefix[kMaxReturnPeriods];
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n_rp * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
+  if (tid < n_rp) s_prefix[tid] = st->prefix[tid];
+  __syncthreads();
+  const int shift = 56 - 8 * pass;
+  unsigned long long local_max = 0ull;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n; i += stride) {
+    const unsigned long long key = (unsigned long long)__double_as_longlong(y[i]);
+    if (pass == 0) {
+      bad |= key >= 0x7FF0000000000000ull;  // negative, infinite or NaN
+      local_max = key > local_max ? key : local_max;
+    }
+    const unsigned int d = (unsigned int)(key >> shift) & 255u;
+    for (int r = 0; r < n_rp; ++r) {
+      const bool match = pass == 0 || ((key ^ s_prefix[r]) >> (shift + 8)) == 0ull;
+      if (match) atomicAdd(&sh[r][d], 1u);
+    }
+  }
+  if (pass == 0) {
+    for (int m = 16; m > 0; m >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, local_max, m);
+      local_max = o > local_max ? o : local_max;
+    }
+    if ((tid & 31) == 0 && local_max) atomicMax(&st->max_key, local_max);
+    if (__any_sync(0xFFFFFFFFu, bad) && (tid & 31) == 0) atomicOr(err, 1u);
+  }
+  __syncthreads();
+  for (int i = tid; i < n_rp * 256; i += blockDim.x) {
+    const unsigned int c = (&sh[0][0])[i];
+    if (c) atomicAdd(&st->hist[0][0] + i, c);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&st->done_pass, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid < n_rp) {
+    const int r = tid;
+    long long k_rem = st->k_rem[r];
+    long long cum = 0;
+    int pick = 0;
+    for (int d = 255; d >= 0; --d) {
+      const long long h = (long long)__ldcg(&st->hist[r][d]);
+      if (cum + h >= k_rem) {
+        pick = d;
+        break;
+      }
+      cum += h;
+    }
+    st->k_rem[r] = k_rem - cum;
+    st->prefix[r] = s_prefix[r] | ((unsigned long long)pick << shift);
+  }
+  __syncthreads();
+  for (int i = tid; i < n_rp * 256; i += blockDim.x) (&st->hist[0][0])[i] = 0u;
+  if (tid == 0) st->done_pass = 0u;
+}
+
+__device__ __forceinline__ int select_q(unsigned long long max_key, int64_t n) {
+  // Largest value < 2^e1; n values sum to < 2^(e1 + ceil(log2 n)); keep the
+  // fixed-point integer below 2^127.
+  const int e1 = (int)(max_key >> 52) - 1022;
+  const int lg = n > 1 ? 64 - __clzll((long long)(n - 1)) : 0;
+  return e1 + lg + 1 - 127;
+}
+
+// grid.y = return period index.
+__global__ void __launch_bounds__(kSelectThreads)
+select_sum_kernel(const double *__restrict__ y, int64_t n, int n_rp, SelState *st,
+                  double *out) {
+  __shared__ unsigned long long s_lo[kSelectThreads / 32], s_hi[kSelectThreads / 32],
+      s_cnt[kSelectThreads / 32];
+  __shared__ bool s_last;
+  const int r = blockIdx.y;
+  const int tid = threadIdx.x;
+  const unsigned long long tau = st->prefix[r];
+  const unsigned long long max_key = st->max_key;
+  const int q = select_q(max_key, n);
+  U128 acc{0ull, 0ull};
+  unsigned long long cnt = 0ull;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n; i += stride) {
+    const double v = y[i];
+    const unsigned long long key = (unsigned long long)__double_as_longlong(v);
+    if (key > tau) {
+      const U128 f = to_fixed(v, q);
+      add128(acc, f.lo, f.hi);
+      ++cnt;
+    }
+  }
+  acc = warp_sum_u128(acc);
+  for (int m = 16; m > 0; m >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, m);
+  if ((tid & 31) == 0) {
+    s_lo[tid >> 5] = acc.lo;
+    s_hi[tid >> 5] = acc.hi;
+    s_cnt[tid >> 5] = cnt;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    U128 b{0ull, 0ull};
+    unsigned long long c = 0ull;
+    for (int w = 0; w < kSelectThreads / 32; ++w) {
+      add128(b, s_lo[w], s_hi[w]);
+      c += s_cnt[w];
+    }
+    if (c) {
+      atomicAdd(&st->cnt_gt[r], c);
+      // 128-bit atomic add from two 64-bit ones: the carry out of the low
+      // word goes into the high word, so the total is exact modulo 2^128.
+      const unsigned long long old = atomicAdd(&st->acc_lo[r], b.lo);
+      const unsigned long long carry = (old + b.lo < old) ? 1ull : 0ull;
+      atomicAdd(&st->acc_hi[r], b.hi + carry);
+    }
+    __threadfence();
+    s_last = atomicAdd(&st->done_sum, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  for (int j = 0; j < n_rp; ++j) {
+    const unsigned long long tj = st->prefix[j];
+    const double tau_v = __longlong_as_double((long long)tj);
+    const unsigned long long m = (unsigned long long)(st->k[j] - (long long)__ldcg(&st->cnt_gt[j]));
+    U128 total{__ldcg(&st->acc_lo[j]), __ldcg(&st->acc_hi[j])};
+    const U128 ft = to_fixed(tau_v, q);
+    const unsigned long long plo = ft.lo * m;
+    const unsigned long long phi = __umul64hi(ft.lo, m) + ft.hi * m;
+    add128(total, plo, phi);
+    out[j] = tau_v;
+    out[n_rp + j] = __ddiv_rn(from_fixed(total, q), (double)st->k[j]);
+  }
+  st->done_sum = 0u;
+}
+
+cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp, void *ws,
+                            double *out, unsigned int *err_flag, int device, cudaStream_t s) {
+  SelState *st = reinterpret_cast<SelState *>(ws);
+  KArgs ka;
+  for (int i = 0; i < kMaxReturnPeriods; ++i) ka.k[i] = i < n_rp ? (long long)k[i] : 1;
+  select_init_kernel<<<1, 256, 0, s>>>(st, ka, n_rp);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  int64_t blocks = (n + kSelectThreads - 1) / kSelectThreads;
+  if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+  if (blocks < 1) blocks = 1;
+  for (int pass = 0; pass < 8; ++pass) {
+    select_pass_kernel<<<(int)blocks, kSelectThreads, 0, s>>>(ylt, n, n_rp, pass, st, err_flag);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  int64_t bx = (blocks + n_rp - 1) / n_rp;
+  if (bx < 1) bx = 1;
+  select_sum_kernel<<<dim3((unsigned)bx, (unsigned)n_rp), kSelectThreads, 0, s>>>(ylt, n, n_rp, st, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ara

@@ -1,0 +1,293 @@
+"""CUDA engine vs the FP64 oracle, element by element, through the C ABI."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import ara_synth as S
+import oracle
+from parity import FP64_REL_TOL, assert_fp64_parity, load_workload, r9_rel_error
+from test_oracle import hand_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def engine():
+    from paper_1412_4556_b300 import Engine
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+# ------------------------------------------------------------- exact cases
+def test_hand_worked_instance_is_exact(engine):
+    g, yet, pool, layer = hand_instance()
+    engine.load_yet_from(yet)
+    first = engine.load_pool(pool)
+    L = engine.define_layer([first + j for j in layer.elts], layer.occ_ret, layer.occ_lim,
+                            layer.agg_ret, layer.agg_lim)
+    assert engine.layer_ylt(L).tolist() == g["ylt"]
+    assert engine.event_table(L).tolist() == g["event_table"]
+    p = g["pml_tvar"]
+    pml, tvar = engine.pml_tvar(np.array(p["ylt"]), p["return_periods"])
+    assert pml.tolist() == p["pml"] and tvar.tolist() == p["tvar"]
+    _, gy, gp, gl = hand_instance(neutral=True)
+    engine.load_yet_from(gy)
+    f2 = engine.load_pool(gp)
+    L2 = engine.define_layer([f2 + j for j in gl.elts], gl.occ_ret, gl.occ_lim, gl.agg_ret, gl.agg_lim)
+    assert engine.layer_ylt(L2)[0] == g["neutral_terms"]["ylt_trial0"]
+
+
+# ----------------------------------------------------------- tiny workload
+def test_tiny_workload_parity(engine):
+    w = S.tiny()
+    layer = w.layers[0]
+    (L,) = load_workload(engine, w)
+    table = engine.event_table(L)
+    np.testing.assert_array_equal(table.view(np.uint64),
+                                  oracle.event_table(w.yet.catalog_size, w.pool, layer).view(np.uint64))
+    o, pre = oracle.layer_ylt(w.yet, w.pool, layer)
+    g = engine.layer_ylt(L)
+    assert_fp64_parity(g, o, pre)
+    # PML/TVaR: the selection is exact on a given YLT ...
+    pml_o, tvar_o = oracle.pml_tvar(o, w.return_periods)
+    pml_g, tvar_g = engine.pml_tvar(o, w.return_periods)
+    np.testing.assert_array_equal(pml_g, pml_o)
+    np.testing.assert_allclose(tvar_g, tvar_o, rtol=1e-13, atol=0)
+    # ... and 1-Lipschitz in the trial losses.
+    pml_gg, tvar_gg = engine.pml_tvar(g, w.return_periods)
+    bound = np.max(np.abs(g - o)) + FP64_REL_TOL * np.abs(tvar_o)
+    assert np.all(np.abs(pml_gg - pml_o) <= bound) and np.all(np.abs(tvar_gg - tvar_o) <= bound)
+
+
+def test_paper_shaped_workload_20k_trials(engine):
+    """Paper-scale catalog, ELTs and trial lengths; 20,000 trials (2e7 events)."""
+    w = S.paper_scale(n_trials=20_000)
+    layer = w.layers[0]
+    (L,) = load_workload(engine, w)
+    tab_g = engine.event_table(L)
+    tab_o = oracle.event_table(w.yet.catalog_size, w.pool, layer)
+    np.testing.assert_array_equal(tab_g.view(np.uint64), tab_o.view(np.uint64))
+    o, pre = oracle.layer_ylt(w.yet, w.pool, layer, mode="memo")
+    g = engine.layer_ylt(L)
+    assert_fp64_parity(g, o, pre)
+    pml_o, tvar_o = oracle.pml_tvar(o, w.return_periods[:2])
+    pml_g, tvar_g = engine.pml_tvar(o, w.return_periods[:2])
+    np.testing.assert_array_equal(pml_g, pml_o)
+    np.testing.assert_allclose(tvar_g, tvar_o, rtol=1e-13, atol=0)
+
+
+# -------------------------------------------------------------- edge cases
+def _custom_yet(catalog, lengths, seed, hot=()):
+    rng = np.random.default_rng(seed)
+    off = np.zeros(len(lengths) + 1, np.int64)
+    off[1:] = np.cumsum(lengths)
+    ids = rng.integers(0, catalog, int(off[-1])).astype(np.int32)
+    hot = list(hot)
+    if hot and ids.size:
+        pos = rng.integers(0, ids.size, min(ids.size, 64 * len(hot)))
+        ids[pos] = np.array(hot, np.int32)[rng.integers(0, len(hot), pos.size)]
+    return S.YET(catalog, off, ids)
+
+
+def _custom_pool(catalog, sizes, seed, ded=None, lim=None):
+    rng = np.random.default_rng(seed + 1)
+    off = np.zeros(len(sizes) + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    ids, losses = [], []
+    for s in sizes:
+        ids.append(rng.choice(catalog, s, replace=False))
+        losses.append(rng.lognormal(10, 2.0, s))
+    n = len(sizes)
+    ded = rng.uniform(0, 2e4, n) if ded is None else np.asarray(ded, float)
+    lim = rng.uniform(1e5, 1e7, n) if lim is None else np.asarray(lim, float)
+    return S.ELTPool(off, np.concatenate(ids).astype(np.int32) if ids else np.zeros(0, np.int32),
+                     np.concatenate(losses) if losses else np.zeros(0), ded, lim)
+
+
+LENGTHS = [0, 1, 2, 3, 4, 5, 31, 32, 33, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1023, 1024,
+           1025, 1500, 4099, 0, 0, 7, 2049, 8191]
+
+
+@pytest.mark.parametrize("catalog", [3, 2_049, 1_000_003, 2_000_000, 5_000_000])
+def test_ragged_trials_and_catalog_sizes(engine, catalog):
+    """Trial lengths around every tile edge, catalogs below and above the
+    shared-memory bitmap (exact and mixed-resolution layouts)."""
+    sizes = [min(catalog, s) for s in (1, 300, 200_000, 7)]
+    pool = _custom_pool(catalog, sizes, 3)
+    hot = [0, catalog - 1, catalog // 2] + [int(x) for x in pool.ids[:50]]
+    yet = _custom_yet(catalog, LENGTHS * 12, catalog, hot)
+    engine.load_yet_from(yet)
+    first = engine.load_pool(pool)
+    layers = [S.Layer([0, 1, 2, 3], 1e3, 5e6, 1e4, 1e8),
+              S.Layer([2, 0], 0.0, math.inf, 0.0, math.inf),
+              S.Layer([3, 2, 1], 5e5, 1e6, 2e6, 3e6),
+              S.Layer([1], 0.0, 0.0, 0.0, 1e9)]
+    for lay in layers:
+        L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret,
+                                lay.agg_lim)
+        np.testing.assert_array_equal(engine.event_table(L).view(np.uint64),
+                                      oracle.event_table(catalog, pool, lay).view(np.uint64))
+        o, pre = oracle.layer_ylt(yet, pool, lay, mode="memo")
+        assert_fp64_parity(engine.layer_ylt(L), o, pre)
+        # a prefix of the YET
+        n = 57
+        assert_fp64_parity(engine.layer_ylt(L, n_trials=n), o[:n], pre[:n])
+
+
+def test_empty_and_degenerate_inputs(engine):
+    # a YET with trials but no events: every trial loss is 0
+    yet = S.YET(10, np.zeros(6, np.int64), np.zeros(0, np.int32))
+    engine.load_yet_from(yet)
+    first = engine.load_pool(_custom_pool(10, [3, 0], 5))
+    L = engine.define_layer([first, first + 1], 0, math.inf, 0, math.inf)
+    assert engine.layer_ylt(L).tolist() == [0.0] * 5
+    assert engine.layer_ylt(L, n_trials=0).shape == (0,)
+    # a YET with no trials
+    engine.load_yet_from(S.YET(10, np.zeros(1, np.int64), np.zeros(0, np.int32)))
+    assert engine.layer_ylt(L).shape == (0,)
+    # PML/TVaR: one trial, k = n, ties, all zeros
+    pml, tvar = engine.pml_tvar(np.array([5.0]), [1.0])
+    assert pml.tolist() == [5.0] and tvar.tolist() == [5.0]
+    y = np.array([3.0, 3.0, 3.0, 1.0, 0.0, 0.0])
+    pml, tvar = engine.pml_tvar(y, [1.0, 2.0, 6.0])
+    assert pml.tolist() == [0.0, 3.0, 3.0] and tvar.tolist() == [10.0 / 6.0, 3.0, 3.0]
+    pml, tvar = engine.pml_tvar(np.zeros(1000), [10.0, 1000.0])
+    assert pml.tolist() == [0.0, 0.0] and tvar.tolist() == [0.0, 0.0]
+
+
+def test_pml_tvar_many_return_periods_wide_range(engine):
+    rng = np.random.default_rng(9)
+    y = np.concatenate([rng.lognormal(12, 3.0, 200_000), np.zeros(5000), np.full(3000, 7.25e8)])
+    rng.shuffle(y)
+    rps = [1.0, 1.5, 2.0, 3.0, 10.0, 33.3, 100.0, 250.0, 500.0, 1000.0, 2500.0, 10_000.0, 50_000.0,
+           100_000.0, 208_000.0, 7.0]
+    pml_o, tvar_o = oracle.pml_tvar(y, rps)
+    pml_g, tvar_g = engine.pml_tvar(y, rps)
+    np.testing.assert_array_equal(pml_g, pml_o)
+    np.testing.assert_allclose(tvar_g, tvar_o, rtol=1e-12, atol=0)
+
+
+def test_result_independent_of_launch_shape(engine, monkeypatch):
+    w = S.paper_scale(n_trials=3_000, catalog_size=300_000)
+    (L,) = load_workload(engine, w)
+    ref = None
+    for u in ("1", "2", "4", "8"):
+        monkeypatch.setenv("ARA_YLT_UNROLL", u)
+        g = engine.layer_ylt(L)
+        if ref is None:
+            ref = g.copy()
+        np.testing.assert_array_equal(g.view(np.uint64), ref.view(np.uint64))
+
+
+def test_device_buffers_and_streams(engine):
+    import torch
+    w = S.tiny()
+    layer = w.layers[0]
+    dev = torch.device("cuda", 0)
+    off = torch.from_numpy(w.yet.offsets).to(dev)
+    ids = torch.from_numpy(w.yet.ids).to(dev)
+    ts = torch.from_numpy(w.yet.ts).to(dev)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    engine.set_stream(s)
+    engine.load_yet(w.yet.catalog_size, off, ids, ts)
+    first = engine.load_pool(w.pool)
+    L = engine.define_layer([first + j for j in layer.elts], layer.occ_ret, layer.occ_lim,
+                            layer.agg_ret, layer.agg_lim)
+    out = torch.empty(w.yet.n_trials, dtype=torch.float64, device=dev)
+    engine.layer_ylt(L, out=out)
+    s.synchronize()
+    o, pre = oracle.layer_ylt(w.yet, w.pool, layer)
+    assert_fp64_parity(out.cpu().numpy(), o, pre)
+    pml, tvar = engine.pml_tvar(out, w.return_periods)
+    pml_h, tvar_h = engine.pml_tvar(out.cpu().numpy(), w.return_periods)
+    np.testing.assert_array_equal(pml, pml_h)
+    np.testing.assert_array_equal(tvar, tvar_h)
+
+
+def test_layer_reuse_after_yet_reload(engine):
+    w = S.tiny()
+    layer = w.layers[0]
+    (L,) = load_workload(engine, w)
+    w2 = S.tiny(seed=77, n_trials=1500)
+    engine.load_yet_from(w2.yet)       # same catalog, new trials: the layer is re-folded
+    o, pre = oracle.layer_ylt(w2.yet, w.pool, layer)
+    assert_fp64_parity(engine.layer_ylt(L), o, pre)
+
+
+# ------------------------------------------------------------ error paths
+def test_invalid_inputs_are_rejected_with_status(engine):
+    from paper_1412_4556_b300 import AraError
+    def status(fn):
+        with pytest.raises(AraError) as ei:
+            fn()
+        return ei.value.name
+
+    bad = S.YET(10, np.array([0, 2, 3], np.int64), np.array([1, 10, 2], np.int32))
+    assert status(lambda: engine.load_yet_from(bad)) == "ARA_E_EVENT_RANGE"
+    assert status(lambda: engine.load_yet(10, np.array([0, 2, 1], np.int64),
+                                          np.array([1, 2], np.int32))) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.load_yet(10, np.array([0, 3], np.int64), np.array([1, 2, 3], np.int32),
+                                          np.array([1.0, 0.5, 2.0], np.float32))) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.load_pool(_custom_pool(10, [2], 1))) == "ARA_E_STATE"
+    engine.load_yet_from(S.YET(10, np.array([0, 3], np.int64), np.array([1, 2, 3], np.int32),
+                               np.array([0.5, 0.5, 2.0], np.float32)))
+    dup = S.ELTPool(np.array([0, 2], np.int64), np.array([4, 4], np.int32), np.array([1.0, 2.0]),
+                    np.array([0.0]), np.array([1.0]))
+    assert status(lambda: engine.load_pool(dup)) == "ARA_E_DUP_EVENT"
+    nan = S.ELTPool(np.array([0, 1], np.int64), np.array([4], np.int32), np.array([np.nan]),
+                    np.array([0.0]), np.array([1.0]))
+    assert status(lambda: engine.load_pool(nan)) == "ARA_E_INVALID_ARG"
+    first = engine.load_pool(_custom_pool(10, [3], 2))
+    assert status(lambda: engine.define_layer([first + 5], 0, 1, 0, 1)) == "ARA_E_NOT_FOUND"
+    assert status(lambda: engine.define_layer([first, first], 0, 1, 0, 1)) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.define_layer([first], -1.0, 1, 0, 1)) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.define_layer([first], 0, float("nan"), 0, 1)) == "ARA_E_INVALID_ARG"
+    L = engine.define_layer([first], 0, 1e9, 0, 1e9)
+    assert status(lambda: engine.layer_ylt(L, n_trials=2)) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.layer_ylt(L + 7)) == "ARA_E_NOT_FOUND"
+    assert status(lambda: engine.pml_tvar(np.ones(10), [11.0])) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.pml_tvar(np.array([1.0, -2.0]), [1.0])) == "ARA_E_INVALID_ARG"
+    assert status(lambda: engine.pml_tvar(np.array([1.0, np.inf]), [1.0])) == "ARA_E_INVALID_ARG"
+    engine.release_layer(L)
+    assert status(lambda: engine.layer_ylt(L)) == "ARA_E_NOT_FOUND"
+    # the context still works after every error
+    L = engine.define_layer([first], 0, 1e9, 0, 1e9)
+    assert engine.layer_ylt(L).shape == (1,)
+
+
+# ------------------------------------------------- full paper-scale workload
+@pytest.fixture(scope="module")
+def paper_full():
+    return S.paper_scale()
+
+
+def test_paper_scale_full_size_sampled(paper_full):
+    """1,000,000 trials x Poisson(1000) events (~1e9 occurrences), 16 ELTs, in
+    the launch configuration the benchmark times; the oracle checks a sample
+    of trials one by one, plus properties that hold at any size."""
+    from paper_1412_4556_b300 import Engine
+    w = paper_full
+    layer = w.layers[0]
+    with Engine(0) as e:
+        (L,) = load_workload(e, w)
+        g = e.layer_ylt(L)
+        pml_g, tvar_g = e.pml_tvar(g, w.return_periods)
+    assert g.shape == (1_000_000,)
+    assert np.all(g >= 0) and np.all(g <= layer.agg_lim)
+    counts = np.diff(w.yet.offsets)
+    rng = np.random.default_rng(1)
+    sel = np.unique(np.concatenate([rng.choice(g.size, 1500, replace=False),
+                                    [0, g.size - 1, int(np.argmax(counts)), int(np.argmin(counts))],
+                                    np.argsort(g)[-50:]]))
+    o, pre = oracle.layer_ylt(w.yet, w.pool, layer, trials=sel, mode="memo")
+    assert_fp64_parity(g[sel], o, pre)
+    # PML/TVaR of the engine's YLT are the order statistics of that YLT
+    s = np.sort(g)[::-1]
+    for r, p, t in zip(w.return_periods, pml_g, tvar_g):
+        k = int(math.floor(g.size / r))
+        assert p == s[k - 1]
+        assert t == pytest.approx(math.fsum(s[:k]) / k, rel=1e-13)
