@@ -80,7 +80,8 @@ ARA_API void ara_destroy(ara_ctx *ctx);
 
 /* Message of the last failed call on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx.  ctx == NULL gives the message of the
- * last failed ara_create. */
+ * last failed call that takes no context (ara_create,
+ * ara_pml_tvar_noalloc) on the calling thread. */
 ARA_API const char *ara_last_error(const ara_ctx *ctx);
 
 /* Static name of a status code ("ARA_OK", "ARA_E_INVALID_ARG", ...). */
@@ -196,6 +197,29 @@ ARA_API ara_status ara_layer_ylt(ara_ctx *ctx, int32_t layer, int64_t n_trials, 
 ARA_API ara_status ara_pml_tvar(ara_ctx *ctx, const double *ylt, int64_t n,
                         const double *return_periods, int32_t n_rp, double *pml_out,
                         double *tvar_out);
+
+/* Allocation-free variant of ara_pml_tvar.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- a service whose
+ * pooling allocator already owns the device memory it may use, or a
+ * latency-critical request path that forbids allocation after start-up
+ * because cudaMalloc/cudaFree can stall the whole device.  It needs no
+ * context (creating one allocates) and allocates nothing: its selection
+ * workspace is a fixed static device array of about 33 KB that every GPU
+ * loading the library keeps until the process exits.
+ *   ylt             double[n], DEVICE memory of the current device; finite, >= 0
+ *   return_periods  double[n_rp], host; 1 <= n_rp <= 16 (the array's limit;
+ *                   more is rejected with ARA_E_INVALID_ARG)
+ *   pml_out, tvar_out  double[n_rp], host or device
+ *   cuda_stream     stream to run on (NULL = the legacy default stream)
+ * Same definitions and results as ara_pml_tvar.  Returns after the outputs
+ * are written.  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture.  Every call
+ * shares the one array: calls whose work overlaps on the GPU (other threads
+ * or streams) race and must be serialised by the caller.  Errors as
+ * ara_pml_tvar; the message is read with ara_last_error(NULL). */
+ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const double *return_periods,
+                                        int32_t n_rp, double *pml_out, double *tvar_out,
+                                        void *cuda_stream);
 
 /* ------------------------------------------------------------- measurement */
 

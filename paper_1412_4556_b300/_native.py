@@ -42,6 +42,7 @@ PROTOTYPES = {
     "ara_layer_event_table": (_i32, [_vp, _i32, _vp]),
     "ara_layer_ylt": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "ara_pml_tvar": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp, _vp]),
+    "ara_pml_tvar_noalloc": (_i32, [_vp, _i64, _vp, _i32, _vp, _vp, _vp]),
     "ara_set_kernel_timing": (_i32, [_vp, _i32]),
     "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
 }
@@ -58,7 +59,7 @@ class AraError(RuntimeError):
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
-        raise ImportError(f"{path} is missing: build it with `python -m paper_1412_4556_b300.build`")
+        raise ImportError(f"{path} is missing: build it with `python paper_1412_4556_b300/build.py`")
     lib = C.CDLL(path)
     for name, (res, args) in PROTOTYPES.items():
         fn = getattr(lib, name)
@@ -136,6 +137,13 @@ def ara_pml_tvar(ctx: int, ylt: int, n: int, return_periods: int, n_rp: int, pml
                  tvar_out: int) -> None:
     _check(ctx, lib.ara_pml_tvar(ctx, ylt or None, int(n), return_periods or None, int(n_rp),
                                  pml_out or None, tvar_out or None))
+
+
+def ara_pml_tvar_noalloc(ylt: int, n: int, return_periods: int, n_rp: int, pml_out: int,
+                         tvar_out: int, stream: int = 0) -> None:
+    """Context-free PML/TVaR that allocates no device memory (ylt on the device)."""
+    _check(None, lib.ara_pml_tvar_noalloc(ylt or None, int(n), return_periods or None, int(n_rp),
+                                          pml_out or None, tvar_out or None, stream or None))
 
 
 def ara_set_kernel_timing(ctx: int, enable: bool) -> None:

@@ -1,7 +1,8 @@
 """Build the engine's shared library (libara_b300.so) in-tree with nvcc for sm_103a.
 
-Usage: ``python -m paper_1412_4556_b300.build`` (or ``build()`` from Python).
-The library exports the C ABI declared in ``include/ara.h``.
+Usage: ``python paper_1412_4556_b300/build.py [--force] [-v]``.  This file is
+run (or loaded by path) without importing the package, whose import needs the
+built library.  The library exports the C ABI declared in ``include/ara.h``.
 """
 from __future__ import annotations
 
@@ -14,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libara_b300.so")
-SOURCES = ["ara_api.cu", "fold.cu", "ylt.cu", "select.cu", "validate.cu"]
+SOURCES = ["ara_api.cu", "fold.cu", "ylt.cu", "select.cu", "validate.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
@@ -47,6 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                            "-lpthread", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
+
 
 
 if __name__ == "__main__":

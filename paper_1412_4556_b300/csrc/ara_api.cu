@@ -269,6 +269,8 @@ ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out) {
 
 }  // namespace
 
+void ara::set_context_free_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
 // ======================================================================= ABI
 extern "C" {
 

@@ -154,6 +154,11 @@ cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const floa
 
 // PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes.
 size_t select_workspace_bytes(int n_rp);
+// Upper bound of select_workspace_bytes() for any n_rp <= kMaxReturnPeriods.
+constexpr size_t kSelectWorkspaceMax = 32 * 1024;
+// Record the message of a failed call that has no context (read back with
+// ara_last_error(NULL)).
+void set_context_free_error(const char *msg);
 cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp,
                             void *ws, double *out_pml_tvar /* device, 2*n_rp */,
                             unsigned int *err_flag, int device, cudaStream_t s);

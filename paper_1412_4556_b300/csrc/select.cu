@@ -32,6 +32,7 @@ struct SelState {
 };
 
 size_t select_workspace_bytes(int) { return sizeof(SelState); }
+static_assert(sizeof(SelState) <= kSelectWorkspaceMax, "selection workspace outgrew its bound");
 
 struct KArgs {
   long long k[kMaxReturnPeriods];

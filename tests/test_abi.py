@@ -18,8 +18,12 @@ def declared_symbols():
 
 @pytest.fixture(scope="module")
 def lib_path():
-    from paper_1412_4556_b300 import build
-    return build.build()
+    import importlib.util
+    path = os.path.join(ROOT, "paper_1412_4556_b300", "build.py")
+    spec = importlib.util.spec_from_file_location("ara_engine_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
 
 
 def test_header_declares_the_paper_boundary():
