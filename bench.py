@@ -77,7 +77,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []            # (monotonic time, csv line)
+        self.window = (0.0, float("inf"))
 
     def __enter__(self):
         try:
@@ -93,7 +94,15 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def wait_first_sample(self, timeout_s: float = 5.0):
+        t0 = time.monotonic()
+        while self.proc and not self.lines and time.monotonic() - t0 < timeout_s:
+            time.sleep(0.05)
+
+    def mark(self, start: float, end: float):
+        self.window = (start, end)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -106,7 +115,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo, hi = self.window
+        for ts, ln in self.lines:
+            if not (lo <= ts <= hi):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -166,14 +178,21 @@ def oracle_sample(w, budget_s: float = 12.0, threads=None, max_trials=None):
     layer = w.layers[0]
     rng = np.random.default_rng(5)
     n = w.yet.n_trials
-    probe = np.sort(rng.choice(n, min(n, max(threads * 8, 256)), replace=False))
-    t0 = time.perf_counter()
-    oracle.layer_ylt(w.yet, w.pool, layer, trials=probe, mode="literal", threads=threads)
-    dt = time.perf_counter() - t0
-    per_trial = max(dt / probe.size, 1e-7)
-    k = int(min(n, max(probe.size, budget_s / per_trial)))
-    if max_trials:
-        k = min(k, max_trials)
+    # Two probes separate the fixed cost (building the direct access tables)
+    # from the per-trial cost; the sample is then sized to the time budget.
+    sizes = [min(n, 512), min(n, 2048)]
+    times = []
+    for m in sizes:
+        probe = np.sort(rng.choice(n, m, replace=False))
+        t0 = time.perf_counter()
+        oracle.layer_ylt(w.yet, w.pool, layer, trials=probe, mode="literal", threads=threads)
+        times.append(time.perf_counter() - t0)
+    if sizes[1] > sizes[0]:
+        per_trial = max((times[1] - times[0]) / (sizes[1] - sizes[0]), 1e-7)
+        fixed = max(times[0] - sizes[0] * per_trial, 0.0)
+    else:
+        per_trial, fixed = max(times[1] / max(sizes[1], 1), 1e-7), 0.0
+    k = int(min(n, max(sizes[1], (budget_s - fixed) / per_trial)))
     sel = np.sort(rng.choice(n, k, replace=False))
     occ = int(np.diff(w.yet.offsets)[sel].sum())
     t0 = time.perf_counter()
@@ -181,7 +200,8 @@ def oracle_sample(w, budget_s: float = 12.0, threads=None, max_trials=None):
     dt = time.perf_counter() - t0
     return {"value": occ / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{k} of {n} trials ({occ} trial-events), literal Algorithm 1 "
-                      f"(16 direct-access-table lookups per event), {dt:.1f} s"}
+                      f"(16 direct-access-table lookups per event), {dt:.1f} s including the "
+                      f"table build"}
 
 
 # --------------------------------------------------------------- engine arm
@@ -227,10 +247,6 @@ def run_engine(args):
         eng.release_layer(L)
         return res
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
@@ -239,14 +255,21 @@ def run_engine(args):
 
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    eng.set_kernel_timing(True)
-    barrier()
     with ClockSampler(local) as clocks:
+        clocks.wait_first_sample()
+        for _ in range(args.warmup):
+            step()
+        eng.set_kernel_timing(True)
+        barrier()
+        t_start = time.monotonic()
         ev0.record(stream)
         for _ in range(args.steps):
             res = step()
         ev1.record(stream)
         barrier()
+        t_end = time.monotonic()
+        time.sleep(0.3)
+        clocks.mark(t_start, t_end)
     ms_total = ev0.elapsed_time(ev1)
     n_ylt, ylt_ms = eng.kernel_timing(ARA_TIMING_YLT)
     n_fold, fold_ms = eng.kernel_timing(ARA_TIMING_FOLD)
@@ -394,12 +417,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "engine":

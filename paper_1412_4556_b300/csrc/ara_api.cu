@@ -2,8 +2,10 @@
 // buffers owned by the context, and the launch sequence of each call.
 //
 // Device memory layout of a context (all buffers library-owned):
-//   YET       offsets int64[N+1]; ids int32[M + 16] (zero tail so 16-byte
-//             loads past the last trial stay in bounds); ts float32[M] or none
+//   YET       raw offsets int64[N+1]; padded offsets int64[N+1]; padded ids
+//             int32[Mp + 16]: trial t at [poff[t], poff[t+1]), a multiple of
+//             4 positions, gaps and tail filled with the sentinel id (the
+//             catalog size); ts float32[M] or none; staging for host ids
 //   ELT pool  one block per ara_load_elts call: ids int32 (sorted by id per
 //             ELT), losses f64 (same order), fold bucket index int32
 //   layer     EltDesc[J]; fixed-point table 16 B x catalog; zero-skip bitmap
@@ -47,8 +49,9 @@ struct LayerRec {
   ulonglong2 *d_table = nullptr;
   uint32_t *d_bitmap = nullptr;
   int32_t table_catalog = 0;
-  BitmapLayout bm{0u, 0, 0};
+  BitmapLayout bm{0u, 0};
   int q = 0;
+  AggFixed agg_fx{{0ull, 0ull}, {0ull, 0ull}, 0};
   int64_t folded_version = -1;
   double upper = 0.0;  // upper bound of any per-event table value
 };
@@ -73,11 +76,16 @@ struct ara_ctx {
   int64_t n_trials = 0;
   int64_t n_occ = 0;
   int64_t max_trial_len = 0;
-  std::vector<int64_t> h_offsets;
-  int64_t *d_offsets = nullptr;
+  std::vector<int64_t> h_offsets;   // raw CSR offsets
+  std::vector<int64_t> h_poff;      // padded offsets (multiples of 4)
+  int64_t *d_offsets = nullptr;     // raw offsets
   size_t cap_offsets = 0;
-  int32_t *d_ids = nullptr;
+  int64_t *d_poff = nullptr;        // padded offsets
+  size_t cap_poff = 0;
+  int32_t *d_ids = nullptr;         // padded ids + 16-entry sentinel tail
   size_t cap_ids = 0;
+  int32_t *d_raw = nullptr;         // staging for ids copied from the host
+  size_t cap_raw = 0;
   float *d_ts = nullptr;
   size_t cap_ts = 0;
   bool has_ts = false;
@@ -174,29 +182,20 @@ struct TimedLaunch {
 };
 
 // Choose the zero-skip bitmap layout that fits the shared-memory budget of
-// the YLT kernel: one bit per event when the catalog fits, otherwise one bit
-// per event below a boundary F and one per 2^shift events above it.
-BitmapLayout plan_bitmap(int32_t catalog, size_t smem_bytes) {
-  BitmapLayout bm{0u, 0, 4};
-  const uint64_t budget = (uint64_t)(smem_bytes / 16) * 128;  // bits, whole uint4s
-  const uint64_t C = (uint64_t)std::max<int32_t>(catalog, 1);
-  uint64_t bits;
-  if (C <= budget) {
-    bits = C;
+// the YLT kernel: one bit per event when the catalog fits, otherwise the
+// events spread evenly over every word of the budget (see BitmapLayout).
+BitmapLayout plan_bitmap(int32_t events, size_t smem_bytes) {
+  const uint64_t max_words = (uint64_t)(smem_bytes / 16) * 4;  // whole uint4s
+  const uint64_t E = (uint64_t)std::max<int32_t>(events, 1);
+  BitmapLayout bm;
+  const uint64_t exact_words = (E + 31) / 32;
+  if (exact_words <= max_words) {
+    bm.mul = 1u << 27;  // word e >> 5
+    bm.words = (int32_t)((exact_words + 3) / 4 * 4);
   } else {
-    int k = 1;
-    while (((C + (1ull << k) - 1) >> k) > budget) ++k;
-    const uint64_t g = 1ull << k;
-    // largest F with F + ceil((C - F) / g) <= budget
-    uint64_t F = (budget * g > C) ? (budget * g - C) / (g - 1) : 0;
-    if (F > C) F = C;
-    while (F > 0 && F + ((C - F + g - 1) >> k) > budget) --F;
-    while (F > 0 && (C - 1) + (g - 1) * F >= (1ull << 32)) --F;  // keep e + add in 32 bits
-    bm.shift = k;
-    bm.add = (uint32_t)((g - 1) * F);
-    bits = (uint64_t)bitmap_pos((uint32_t)(C - 1), bm.add, k) + 1;
+    bm.words = (int32_t)max_words;
+    bm.mul = (uint32_t)(((uint64_t)max_words << 32) / E);  // word(E-1) < max_words
   }
-  bm.words = (int32_t)(((bits + 127) / 128) * 4);
   return bm;
 }
 
@@ -225,6 +224,44 @@ bool choose_q(double upper, int64_t lmax, int *q) {
   return true;
 }
 
+// v (finite, >= 0) as the integer v / 2^q, when that is exact and below
+// 2^127; false otherwise.
+bool to_fixed_exact(double v, int q, U128 *out) {
+  *out = U128{0ull, 0ull};
+  if (v == 0.0) return true;
+  int e = 0;
+  const double m = std::frexp(v, &e);                     // v = m * 2^e, m in [0.5, 1)
+  const uint64_t mi = (uint64_t)std::ldexp(m, 53);         // v = mi * 2^(e - 53)
+  const int sh = e - 53 - q;                               // v / 2^q = mi * 2^sh
+  if (sh < 0) {
+    if (-sh >= 64 || (mi & ((1ull << -sh) - 1)) != 0ull) return false;
+    out->lo = mi >> -sh;
+    return true;
+  }
+  if (sh + 53 > 127) return false;
+  if (sh >= 64) {
+    out->hi = mi << (sh - 64);
+  } else if (sh > 0) {
+    out->lo = mi << sh;
+    out->hi = mi >> (64 - sh);
+  } else {
+    out->lo = mi;
+  }
+  return true;
+}
+
+// The layer's aggregate terms on its fixed-point grid (see AggFixed).
+AggFixed agg_terms_fixed(double agg_ret, double agg_lim, int q) {
+  AggFixed af{{0ull, 0ull}, {~0ull, ~0ull}, 0};
+  const bool ret_ok = to_fixed_exact(agg_ret, q, &af.ret);
+  bool lim_ok = true;
+  if (std::isfinite(agg_lim) && agg_lim < std::ldexp(1.0, 127 + q)) {
+    lim_ok = to_fixed_exact(agg_lim, q, &af.lim);
+  }  // else: no trial sum reaches AggL, the clamp never binds
+  af.exact = (ret_ok && lim_ok) ? 1 : 0;
+  return af;
+}
+
 ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
   int q = 0;
   if (!choose_q(L.upper, std::max<int64_t>(c->max_trial_len, 1), &q))
@@ -236,13 +273,17 @@ ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
     L.d_table = nullptr;
     L.d_bitmap = nullptr;
     L.table_catalog = 0;
-    L.bm = plan_bitmap(c->catalog, ylt_smem_budget(c->device));
-    ARA_CUDA(c, cudaMalloc(&L.d_table, (size_t)std::max(c->catalog, 1) * sizeof(ulonglong2)),
+    // One extra entry for the sentinel id (= catalog) that pads trials; it
+    // stays zero because the fold only writes entries below the catalog size.
+    L.bm = plan_bitmap(c->catalog + 1, ylt_smem_budget(c->device));
+    ARA_CUDA(c, cudaMalloc(&L.d_table, ((size_t)c->catalog + 1) * sizeof(ulonglong2)),
              "cudaMalloc(layer table)");
     ARA_CUDA(c, cudaMalloc(&L.d_bitmap, (size_t)L.bm.words * 4), "cudaMalloc(layer bitmap)");
+    ARA_CUDA(c, cudaMemsetAsync(L.d_table + c->catalog, 0, sizeof(ulonglong2), s), "cudaMemsetAsync(table)");
     L.table_catalog = c->catalog;
   }
   L.q = q;
+  L.agg_fx = agg_terms_fixed(L.agg_ret, L.agg_lim, q);
   ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
   TimedLaunch tl(c, ARA_TIMING_FOLD, s);
   ARA_CUDA(c, launch_fold(L.d_desc, (int)L.elts.size(), c->catalog, L.occ_ret, L.occ_lim, q,
@@ -337,7 +378,9 @@ void ara_destroy(ara_ctx *c) {
   for (auto &L : c->layers) free_layer(L);
   for (void *p : c->elt_blocks) cudaFree(p);
   cudaFree(c->d_offsets);
+  cudaFree(c->d_poff);
   cudaFree(c->d_ids);
+  cudaFree(c->d_raw);
   cudaFree(c->d_ts);
   cudaFree(c->d_ylt_stage);
   cudaFree(c->d_sel_in);
@@ -397,22 +440,35 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
     if (c->elts[j].max_id >= catalog)
       return fail(c, ARA_E_EVENT_RANGE, "loaded ELT %zu holds event id %d outside the new catalog of %d",
                   j, c->elts[j].max_id, catalog);
+  // Padded layout: every trial rounded up to a multiple of 4 positions.
+  std::vector<int64_t> hp((size_t)n_trials + 1);
+  hp[0] = 0;
+  for (int64_t t = 0; t < n_trials; ++t) hp[(size_t)t + 1] = hp[(size_t)t] + ((h[(size_t)t + 1] - h[(size_t)t] + 3) & ~(int64_t)3);
+  const int64_t Mp = hp[(size_t)n_trials];
   // The YET is replaced in place (it can be several GB): from here on a
   // failure leaves the context without a YET.
   c->yet_loaded = false;
   c->yet_version++;
+  const bool dev_ids = M > 0 && is_device_ptr(ids);
   cudaError_t e = ensure(&c->d_offsets, &c->cap_offsets, (size_t)n_trials + 1);
-  if (e == cudaSuccess) e = ensure(&c->d_ids, &c->cap_ids, (size_t)M + 16);
+  if (e == cudaSuccess) e = ensure(&c->d_poff, &c->cap_poff, (size_t)n_trials + 1);
+  if (e == cudaSuccess) e = ensure(&c->d_ids, &c->cap_ids, (size_t)Mp + 16);
+  if (e == cudaSuccess && M > 0 && !dev_ids) e = ensure(&c->d_raw, &c->cap_raw, (size_t)M);
   if (e == cudaSuccess && ts) e = ensure(&c->d_ts, &c->cap_ts, (size_t)std::max<int64_t>(M, 1));
   if (e != cudaSuccess) return cuda_fail(c, e, "allocate YET buffers");
   e = cudaMemcpyAsync(c->d_offsets, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && M > 0)
-    e = cudaMemcpyAsync(c->d_ids, ids, (size_t)M * sizeof(int32_t), cudaMemcpyDefault, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ids + M, 0, 16 * sizeof(int32_t), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_poff, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  const int32_t *src = ids;
+  if (e == cudaSuccess && M > 0 && !dev_ids) {
+    e = cudaMemcpyAsync(c->d_raw, ids, (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    src = c->d_raw;
+  }
   if (e == cudaSuccess && ts && M > 0)
     e = cudaMemcpyAsync(c->d_ts, ts, (size_t)M * sizeof(float), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, 2 * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = launch_check_ids(c->d_ids, M, catalog, c->d_counter, s);
+  if (e == cudaSuccess)
+    e = launch_pad_ids(src, c->d_offsets, c->d_poff, n_trials, c->d_ids, catalog, c->d_counter, s);
   if (e == cudaSuccess && ts) e = launch_check_ts(c->d_offsets, n_trials, c->d_ts, c->d_counter + 1, s);
   unsigned long long bad[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_counter, sizeof(bad), cudaMemcpyDeviceToHost, s);
@@ -429,6 +485,7 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
   c->n_occ = M;
   c->max_trial_len = lmax;
   c->h_offsets.swap(h);
+  c->h_poff.swap(hp);
   return ARA_OK;
 }
 
@@ -661,12 +718,12 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
     ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, (size_t)n_trials), "stage buffer");
     dst = c->d_ylt_stage;
   }
-  const double mean = (double)c->h_offsets[(size_t)n_trials] / (double)n_trials;
+  const double mean_chunks = (double)(c->h_poff[(size_t)n_trials] / 4) / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean, &cfg), "plan YLT launch");
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, &cfg), "plan YLT launch");
   TimedLaunch tl(c, ARA_TIMING_YLT, s);
-  ARA_CUDA(c, launch_ylt_fp64(c->d_offsets, c->d_ids, n_trials, L->d_table, L->d_bitmap, L->bm, L->q,
-                              L->agg_ret, L->agg_lim, dst, cfg, s),
+  ARA_CUDA(c, launch_ylt_fp64(c->d_poff, c->d_ids, n_trials, L->d_table, L->d_bitmap, L->bm,
+                              c->catalog, L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst, cfg, s),
            "YLT kernel launch");
   tl.done();
   if (!dev) {

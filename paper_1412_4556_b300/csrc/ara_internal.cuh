@@ -31,20 +31,26 @@ struct EltDesc {
   double limit;
 };
 
-// Zero-skip bitmap layout.  Event e maps to bit pos(e) = min(e, (e + add) >> shift):
-// events below a boundary F get one bit each, the rest share one bit per
-// 2^shift events (add = (2^shift - 1) * F).  A set bit means "some event of
-// this bit may have a nonzero loss"; a clear bit proves every event of it has
-// loss exactly zero, so skipping it leaves an exact sum unchanged.
+// Zero-skip bitmap layout.  Event e maps to bit (e & 31) of word
+// umulhi(e, mul) = floor(e * mul / 2^32).  With mul = 2^27 that is one bit
+// per event (word e >> 5).  When the catalog has more events than the shared
+// memory budget has bits, mul = floor(2^32 * words / events) spreads the
+// events evenly over the words, and the few events of a word whose low five
+// bits coincide share a bit.  A set bit means "some event of this bit may
+// have a nonzero loss"; a clear bit proves every event of it has loss exactly
+// zero, so skipping it leaves an exact sum unchanged.  The word index is one
+// multiply-high (FMA pipe) and the bit index needs no arithmetic.
 struct BitmapLayout {
-  uint32_t add;
-  int32_t shift;
-  int32_t words;  // 32-bit words, rounded up to a multiple of 4
+  uint32_t mul;
+  int32_t words;  // 32-bit words, a multiple of 4
 };
 
-__host__ __device__ inline uint32_t bitmap_pos(uint32_t e, uint32_t add, int shift) {
-  uint32_t c = (e + add) >> shift;
-  return e < c ? e : c;
+__host__ __device__ inline uint32_t bitmap_word(uint32_t e, uint32_t mul) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(e, mul);
+#else
+  return (uint32_t)(((uint64_t)e * mul) >> 32);
+#endif
 }
 
 // ------------------------------------------------ 128-bit fixed point
@@ -109,6 +115,77 @@ __device__ __forceinline__ double from_fixed(U128 a, int q) {
   return ldexp(d, q + 64 - lz);
 }
 
+// The same value computed with integer instructions only (B300 issues FP64
+// at a small fraction of its integer rate): round the 128-bit integer to 53
+// significant bits, nearest-even, and assemble the binary64 bit pattern.
+// Results that would be subnormal or overflow take the FP64 path above.
+__device__ __forceinline__ double from_fixed_int(U128 a, int q) {
+  if ((a.hi | a.lo) == 0ull) return 0.0;
+  const int lz = a.hi ? __clzll((long long)a.hi) : 64 + __clzll((long long)a.lo);
+  unsigned long long top, rest;
+  if (lz == 0) {
+    top = a.hi;
+    rest = a.lo;
+  } else if (lz < 64) {
+    top = (a.hi << lz) | (a.lo >> (64 - lz));
+    rest = a.lo << lz;
+  } else if (lz == 64) {
+    top = a.lo;
+    rest = 0ull;
+  } else {
+    top = a.lo << (lz - 64);
+    rest = 0ull;
+  }
+  unsigned long long mant = top >> 11;           // 53 bits, bit 52 set
+  const unsigned long long low = top & 0x7FFull;  // the 11 bits below
+  const bool half = low == 0x400ull && rest == 0ull;
+  const bool up = low > 0x400ull || (low == 0x400ull && rest != 0ull) || (half && (mant & 1ull));
+  mant += up ? 1ull : 0ull;
+  int e2 = 127 - lz + q;  // value in [2^e2, 2^(e2+1)) before rounding
+  if (mant == (1ull << 53)) {
+    mant >>= 1;
+    ++e2;
+  }
+  const int biased = e2 + 1023;
+  if (biased <= 0 || biased >= 2047) return from_fixed(a, q);
+  return __longlong_as_double((long long)(((unsigned long long)biased << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// a >= b for 128-bit unsigned integers.
+__device__ __forceinline__ bool ge128(U128 a, U128 b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);
+}
+
+__device__ __forceinline__ U128 sub128(U128 a, U128 b) {
+  U128 r = a;
+  asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(r.lo), "+l"(r.hi) : "l"(b.lo), "l"(b.hi));
+  return r;
+}
+
+// Aggregate terms of a layer on the 128-bit fixed-point grid of its table.
+// exact = 1 when AggR and AggL lie exactly on that grid (or AggL is beyond
+// any trial sum), so min(max(S - AggR, 0), AggL) is computed exactly in
+// integers and rounded once; otherwise the FP64 clamp is used.
+struct AggFixed {
+  U128 ret;
+  U128 lim;
+  int exact;
+};
+
+// Trial loss from the exact trial sum S (Section III step 4).
+__device__ __forceinline__ double trial_loss(U128 S, int q, const AggFixed &af, double agg_ret,
+                                             double agg_lim) {
+  if (af.exact) {
+    U128 d{0ull, 0ull};
+    if (ge128(S, af.ret)) d = sub128(S, af.ret);
+    if (ge128(d, af.lim)) d = af.lim;
+    return from_fixed_int(d, q);
+  }
+  const double Sv = from_fixed(S, q);
+  return fmin(fmax(__dsub_rn(Sv, agg_ret), 0.0), agg_lim);
+}
+
 __device__ __forceinline__ U128 shfl_xor_u128(U128 v, int m) {
   U128 r;
   r.lo = __shfl_xor_sync(0xFFFFFFFFu, v.lo, m);
@@ -138,16 +215,20 @@ struct YltLaunch {
   int unroll;
 };
 
-cudaError_t launch_ylt_fp64(const int64_t *offsets, const int32_t *ids, int64_t n_trials,
+// poff/pids: the padded YET layout written by launch_pad_ids; sentinel =
+// catalog size (its table entry is zero).
+cudaError_t launch_ylt_fp64(const int64_t *poff, const int32_t *pids, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int q, double agg_ret, double agg_lim, double *ylt,
-                            const YltLaunch &cfg, cudaStream_t s);
+                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
+                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s);
 
-// Pick the launch shape of the YLT kernel for a bitmap of bm.words words.
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_trial_len, YltLaunch *out);
+// Pick the launch shape of the YLT kernel for a bitmap of bm.words words and
+// trials of mean_chunks 16-byte chunks.
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, YltLaunch *out);
 
-cudaError_t launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog,
-                             unsigned long long *bad_count, cudaStream_t s);
+cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *poff,
+                           int64_t n_trials, int32_t *dst, int32_t catalog,
+                           unsigned long long *bad_count, cudaStream_t s);
 
 cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const float *ts,
                             unsigned long long *bad_count, cudaStream_t s);

@@ -27,7 +27,7 @@ __device__ __forceinline__ double elt_terms(double loss, double deductible, doub
 __global__ void __launch_bounds__(kFoldThreads)
 fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
             double occ_lim, int q, ulonglong2 *__restrict__ table, uint32_t *__restrict__ bitmap,
-            uint32_t bm_add, int bm_shift, double *__restrict__ f64_out) {
+            uint32_t bm_mul, double *__restrict__ f64_out) {
   __shared__ double x[kFoldEventsPerCta];
   __shared__ int32_t seg[kMaxLayerElts + 1];    // prefix sums of slice lengths
   __shared__ int32_t first[kMaxLayerElts];      // slice start inside ELT j
@@ -97,8 +97,7 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
       const U128 v = to_fixed(o, q);
       table[e] = make_ulonglong2(v.lo, v.hi);
       if ((v.lo | v.hi) != 0ull) {
-        const uint32_t p = bitmap_pos((uint32_t)e, bm_add, bm_shift);
-        atomicOr(bitmap + (p >> 5), 1u << (p & 31));
+        atomicOr(bitmap + bitmap_word((uint32_t)e, bm_mul), 1u << (e & 31));
       }
     }
   }
@@ -110,7 +109,7 @@ cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, doub
   if (catalog <= 0) return cudaSuccess;
   const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
   fold_kernel<<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q, table,
-                                               bitmap, bm.add, bm.shift, f64_out);
+                                               bitmap, bm.mul, f64_out);
   return cudaGetLastError();
 }
 

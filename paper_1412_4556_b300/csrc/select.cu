@@ -103,23 +103,30 @@ select_pass_kernel(const double *__restrict__ y, int64_t n, int n_rp, int pass, 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (tid < n_rp) {
-    const int r = tid;
-    long long k_rem = st->k_rem[r];
-    long long cum = 0;
-    int pick = 0;
-    for (int d = 255; d >= 0; --d) {
-      const long long h = (long long)__ldcg(&st->hist[r][d]);
-      if (cum + h >= k_rem) {
-        pick = d;
-        break;
-      }
-      cum += h;
+  // Pick the next digit of every return period in parallel: thread i holds
+  // the count of digit 255 - i (descending), a block-wide inclusive scan
+  // gives the counts of keys above each digit, and the one thread whose
+  // range contains rank k_rem records the digit.
+  __shared__ long long s_warp[kSelectThreads / 32];
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int r = 0; r < n_rp; ++r) {
+    const long long k_rem = st->k_rem[r];
+    const long long h = tid < 256 ? (long long)__ldcg(&st->hist[r][255 - tid]) : 0;
+    long long incl = h;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
     }
-    st->k_rem[r] = k_rem - cum;
-    st->prefix[r] = s_prefix[r] | ((unsigned long long)pick << shift);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    for (int w = 0; w < wid; ++w) incl += s_warp[w];
+    const long long excl = incl - h;
+    if (tid < 256 && excl < k_rem && k_rem <= incl) {
+      st->k_rem[r] = k_rem - excl;
+      st->prefix[r] = s_prefix[r] | ((unsigned long long)(255 - tid) << shift);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = tid; i < n_rp * 256; i += blockDim.x) (&st->hist[0][0])[i] = 0u;
   if (tid == 0) st->done_pass = 0u;
 }

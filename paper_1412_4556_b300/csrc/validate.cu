@@ -1,4 +1,4 @@
-// Device-side checks of a freshly copied YET: every event id must lie in the
+// Device-side ingest of a freshly copied YET: every event id must lie in the
 // catalog (Section III: ids are drawn from the catalogue of events), and
 // time-stamps, when given, must be finite and ascending within each trial
 // (Section III: each trial is ordered by ascending time-stamp).  Violations
@@ -7,18 +7,6 @@
 #include "ara_internal.cuh"
 
 namespace ara {
-
-__global__ void check_ids_kernel(const int32_t *__restrict__ ids, int64_t n, int32_t catalog,
-                                 unsigned long long *bad) {
-  unsigned long long local = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int32_t v = ids[i];
-    local += (v < 0 || v >= catalog) ? 1ull : 0ull;
-  }
-  for (int m = 16; m > 0; m >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, m);
-  if ((threadIdx.x & 31) == 0 && local) atomicAdd(bad, local);
-}
 
 // One warp per trial: position i of trial t is checked against i + 1.
 __global__ void check_ts_kernel(const int64_t *__restrict__ offsets, int64_t n_trials,
@@ -40,12 +28,48 @@ __global__ void check_ts_kernel(const int64_t *__restrict__ offsets, int64_t n_t
   if (lane == 0 && local) atomicAdd(bad, local);
 }
 
-cudaError_t launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog,
-                             unsigned long long *bad_count, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  int64_t blocks = (n + 255) / 256;
+// Copy the YET ids into the engine's padded layout: trial t occupies
+// dst[poff[t] .. poff[t+1]), a multiple of 4 positions, so every 16-byte
+// chunk of dst belongs to exactly one trial; the gap after the trial's
+// events and the 16 positions after the last trial hold the sentinel id
+// (= catalog size, whose table entry is zero).  Ids outside the catalog are
+// counted (and replaced by the sentinel, so no later kernel indexes with
+// them).  One warp per trial.
+__global__ void pad_ids_kernel(const int32_t *__restrict__ src, const int64_t *__restrict__ off,
+                               const int64_t *__restrict__ poff, int64_t n_trials,
+                               int32_t *__restrict__ dst, int32_t catalog,
+                               unsigned long long *bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned long long local = 0;
+  for (int64_t t = w0; t < n_trials; t += warps) {
+    const int64_t s = off[t], n = off[t + 1] - s;
+    const int64_t d = poff[t], dn = poff[t + 1] - d;
+    for (int64_t i = lane; i < dn; i += 32) {
+      int32_t v = catalog;
+      if (i < n) {
+        v = src[s + i];
+        if (v < 0 || v >= catalog) {
+          ++local;
+          v = catalog;
+        }
+      }
+      dst[d + i] = v;
+    }
+  }
+  if (w0 == 0 && lane < 16) dst[poff[n_trials] + lane] = catalog;
+  for (int m = 16; m > 0; m >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, m);
+  if (lane == 0 && local) atomicAdd(bad, local);
+}
+
+cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *poff,
+                           int64_t n_trials, int32_t *dst, int32_t catalog,
+                           unsigned long long *bad_count, cudaStream_t s) {
+  int64_t blocks = (n_trials + 7) / 8;
   if (blocks > 148 * 16) blocks = 148 * 16;
-  check_ids_kernel<<<(int)blocks, 256, 0, s>>>(ids, n, catalog, bad_count);
+  if (blocks < 1) blocks = 1;
+  pad_ids_kernel<<<(int)blocks, 256, 0, s>>>(src, off, poff, n_trials, dst, catalog, bad_count);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,7 @@
 // The Year Loss Table kernel: Algorithm 1 (Section III), steps 1-4, for every
 // trial of the YET, with steps 1-3 already folded into the per-event table.
 //
-// For trial t with occurrences k = offsets[t] .. offsets[t+1]-1:
+// For trial t with occurrences id_k (the trial's events in stored order):
 //     S_t   = sum_k o(id_k)                  (occurrence-net losses, step 3)
 //     YLT_t = min(max(S_t - AggR, 0), AggL)  (aggregate terms, step 4)
 // The aggregate clamp applied to the running sum after every event ends at
@@ -11,7 +11,10 @@
 // B300 design:
 //  * One warp per trial; each warp owns a contiguous run of trials, so the
 //    YET id stream is read once, in 16-byte coalesced loads, U loads in flight
-//    per lane, with an evict-first L2 policy.
+//    per lane, with an evict-first L2 policy.  The engine stores every trial
+//    padded to a multiple of 4 ids with a sentinel event whose table entry is
+//    zero, so each 16-byte chunk belongs to one trial and no per-event bounds
+//    test is needed.
 //  * The layer's zero-skip bitmap sits in shared memory.  Only occurrences
 //    whose bit is set fetch their table entry (a random 16-byte gather served
 //    by L2, evict-last); the rest add an exact zero and are skipped.
@@ -41,8 +44,7 @@ __device__ __forceinline__ unsigned long long policy_evict_last() {
 
 __device__ __forceinline__ int4 ld_ids(const int4 *p, unsigned long long pol) {
   int4 v;
-  asm volatile(
-      "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
       : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
       : "l"(p), "l"(pol));
   return v;
@@ -50,18 +52,38 @@ __device__ __forceinline__ int4 ld_ids(const int4 *p, unsigned long long pol) {
 
 __device__ __forceinline__ ulonglong2 ld_entry(const ulonglong2 *p, unsigned long long pol) {
   ulonglong2 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
                : "=l"(v.x), "=l"(v.y)
                : "l"(p), "l"(pol));
   return v;
 }
 
+// Table entry of `id` if `hit`, else zero: a predicated 16-byte gather, so
+// occurrences whose bitmap bit is clear cost no memory request.
+__device__ __forceinline__ ulonglong2 gather_if(const ulonglong2 *p, uint32_t hit,
+                                                unsigned long long pol) {
+  ulonglong2 v = make_ulonglong2(0ull, 0ull);
+  asm("{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
+      : "+l"(v.x), "+l"(v.y)
+      : "r"(hit), "l"(p), "l"(pol));
+  return v;
+}
+
+// One bulk copy-engine request pulls a whole trial's ids (a contiguous,
+// 16-byte aligned run) into L2, so the warp's own loads of that trial hit L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int U>
 __global__ void __launch_bounds__(kYltThreads, 1)
-ylt_fp64_kernel(const int64_t *__restrict__ offsets, const int32_t *__restrict__ ids,
+ylt_fp64_kernel(const int64_t *__restrict__ poff, const int4 *__restrict__ pids4,
                 int64_t n_trials, const ulonglong2 *__restrict__ table,
-                const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_add, int bm_shift,
-                int q, double agg_ret, double agg_lim, double *__restrict__ ylt) {
+                const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
+                int32_t sentinel, int q, AggFixed af, double agg_ret, double agg_lim,
+                double *__restrict__ ylt) {
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
   __syncthreads();
@@ -74,91 +96,99 @@ ylt_fp64_kernel(const int64_t *__restrict__ offsets, const int32_t *__restrict__
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t t_begin = n_trials * w / n_warps;
   const int64_t t_end = n_trials * (w + 1) / n_warps;
-  const int4 *ids4 = reinterpret_cast<const int4 *>(ids);
+  const int4 sent4 = make_int4(sentinel, sentinel, sentinel, sentinel);
 
+  int64_t p_next = t_begin < t_end ? poff[t_begin] : 0;
+  if (lane == 0 && t_begin < t_end) {
+    const int64_t b = poff[t_begin + 1];
+    if (b > p_next) prefetch_l2(pids4 + (p_next >> 2), (uint32_t)((b - p_next) * 4));
+  }
   for (int64_t t = t_begin; t < t_end; ++t) {
-    const int64_t s = offsets[t];
-    const int64_t e = offsets[t + 1];
-    const int64_t base = s & ~3ll;              // 16-byte aligned start
-    const int32_t lo_r = (int32_t)(s - base);   // first valid position (0..3)
-    const int32_t hi_r = (int32_t)(e - base);   // one past the last valid position
+    const int64_t p0 = p_next;
+    p_next = poff[t + 1];
+    // While this trial is summed, its successor's ids travel to L2.
+    if (lane == 0 && t + 1 < t_end) {
+      const int64_t b = poff[t + 2];
+      if (b > p_next) prefetch_l2(pids4 + (p_next >> 2), (uint32_t)((b - p_next) * 4));
+    }
+    const int4 *tp = pids4 + (p0 >> 2);
+    const int nk = (int)((p_next - p0) >> 2);  // 16-byte chunks of this trial
     U128 acc{0ull, 0ull};
-    for (int32_t c = 4 * lane; c < hi_r; c += 128 * U) {
+    for (int base = 0; base < nk; base += 32 * U) {
       int4 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int32_t r = c + 128 * u;
-        v[u] = (r < hi_r) ? ld_ids(ids4 + ((base + r) >> 2), pol_ids) : make_int4(0, 0, 0, 0);
+        v[u] = sent4;
+        const int j = base + 32 * u + lane;
+        if (base + 32 * u < nk && j < nk) v[u] = ld_ids(tp + j, pol_ids);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int32_t r = c + 128 * u;
-        const int32_t idv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        if (base + 32 * u >= nk) break;  // warp-uniform: the rest of this step is empty
+        const uint32_t idv[4] = {(uint32_t)v[u].x, (uint32_t)v[u].y, (uint32_t)v[u].z,
+                                 (uint32_t)v[u].w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const uint32_t id = (uint32_t)idv[i];
-          const uint32_t pos = bitmap_pos(id, bm_add, bm_shift);
-          const uint32_t word = s_bm[pos >> 5];
-          const bool in_trial = (r + i >= lo_r) && (r + i < hi_r);
-          if (in_trial && ((word >> (pos & 31)) & 1u)) {
-            const ulonglong2 x = ld_entry(table + id, pol_tab);
-            add128(acc, x.x, x.y);
-          }
+          const uint32_t id = idv[i];
+          const uint32_t word = s_bm[bitmap_word(id, bm_mul)];
+          const uint32_t hit = __funnelshift_r(word, word, id) & 1u;  // bit id & 31
+          const ulonglong2 x = gather_if(table + id, hit, pol_tab);
+          add128(acc, x.x, x.y);
         }
       }
     }
     acc = warp_sum_u128(acc);
-    if (lane == 0) {
-      const double S = from_fixed(acc, q);
-      ylt[t] = fmin(fmax(__dsub_rn(S, agg_ret), 0.0), agg_lim);
-    }
+    if (lane == 0) ylt[t] = trial_loss(acc, q, af, agg_ret, agg_lim);
   }
 }
 
 template <int U>
-static cudaError_t launch_u(const int64_t *offsets, const int32_t *ids, int64_t n_trials,
+static cudaError_t launch_u(const int64_t *poff, const int32_t *pids, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int q, double agg_ret, double agg_lim, double *ylt,
-                            const YltLaunch &cfg, cudaStream_t s) {
+                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
+                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
   cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.smem);
   if (err != cudaSuccess) return err;
   ylt_fp64_kernel<U><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
-      offsets, ids, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4,
-      bm.add, bm.shift, q, agg_ret, agg_lim, ylt);
+      poff, reinterpret_cast<const int4 *>(pids), n_trials, table,
+      reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sentinel, q, af, agg_ret,
+      agg_lim, ylt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ylt_fp64(const int64_t *offsets, const int32_t *ids, int64_t n_trials,
+cudaError_t launch_ylt_fp64(const int64_t *poff, const int32_t *pids, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int q, double agg_ret, double agg_lim, double *ylt,
-                            const YltLaunch &cfg, cudaStream_t s) {
+                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
+                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
   switch (cfg.unroll) {
-    case 1: return launch_u<1>(offsets, ids, n_trials, table, bitmap, bm, q, agg_ret, agg_lim, ylt, cfg, s);
-    case 2: return launch_u<2>(offsets, ids, n_trials, table, bitmap, bm, q, agg_ret, agg_lim, ylt, cfg, s);
-    case 4: return launch_u<4>(offsets, ids, n_trials, table, bitmap, bm, q, agg_ret, agg_lim, ylt, cfg, s);
-    default: return launch_u<8>(offsets, ids, n_trials, table, bitmap, bm, q, agg_ret, agg_lim, ylt, cfg, s);
+    case 1: return launch_u<1>(poff, pids, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+    case 2: return launch_u<2>(poff, pids, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+    default: return launch_u<4>(poff, pids, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
   }
 }
 
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_trial_len, YltLaunch *out) {
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, YltLaunch *out) {
   int sms = 0;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
-  int unroll = mean_trial_len >= 768.0 ? 8 : mean_trial_len >= 384.0 ? 4 : mean_trial_len >= 160.0 ? 2 : 1;
+  // Chunks per lane of a typical trial.  Measured on B300 with ~8 chunks per
+  // lane (1000-event trials): U = 2 beats 4 and 8 (fewer wasted slots in the
+  // last step of a trial, more warps' worth of registers free).
+  const double per_lane = mean_chunks / 32.0;
+  int unroll = per_lane > 1.5 ? 2 : 1;
   if (const char *env = std::getenv("ARA_YLT_UNROLL")) {
     int u = std::atoi(env);
-    if (u == 1 || u == 2 || u == 4 || u == 8) unroll = u;
+    if (u == 1 || u == 2 || u == 4) unroll = u;
   }
   out->threads = kYltThreads;
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
   const void *fn = unroll == 1 ? (const void *)ylt_fp64_kernel<1>
                  : unroll == 2 ? (const void *)ylt_fp64_kernel<2>
-                 : unroll == 4 ? (const void *)ylt_fp64_kernel<4>
-                               : (const void *)ylt_fp64_kernel<8>;
+                               : (const void *)ylt_fp64_kernel<4>;
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;

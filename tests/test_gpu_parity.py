@@ -124,7 +124,9 @@ def test_ragged_trials_and_catalog_sizes(engine, catalog):
     layers = [S.Layer([0, 1, 2, 3], 1e3, 5e6, 1e4, 1e8),
               S.Layer([2, 0], 0.0, math.inf, 0.0, math.inf),
               S.Layer([3, 2, 1], 5e5, 1e6, 2e6, 3e6),
-              S.Layer([1], 0.0, 0.0, 0.0, 1e9)]
+              S.Layer([1], 0.0, 0.0, 0.0, 1e9),
+              # aggregate terms off the fixed-point grid: the FP64 clamp path
+              S.Layer([0, 2], 250.0, 2e7, 1.2345e-30, 7.77e-29 + 3e6)]
     for lay in layers:
         L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret,
                                 lay.agg_lim)
