@@ -163,7 +163,9 @@ ARA_API ara_status ara_define_layer(ara_ctx *ctx, int32_t n_elts, const int32_t 
                             double occ_ret, double occ_lim, double agg_ret, double agg_lim,
                             int32_t precision, int32_t *layer_out);
 
-/* Free the device tables of a layer; its handle becomes invalid. */
+/* Release a layer; its handle becomes invalid.  Its device buffers are kept
+ * for reuse by later layers, ordered by the context's stream: work queued on
+ * other streams that reads the layer must be complete before this call. */
 ARA_API ara_status ara_release_layer(ara_ctx *ctx, int32_t layer);
 
 /* The layer's per-event table as FP64: out[e] = FT2(sum_j FT1(DAT_j[e]))

@@ -2,10 +2,11 @@
 // buffers owned by the context, and the launch sequence of each call.
 //
 // Device memory layout of a context (all buffers library-owned):
-//   YET       raw offsets int64[N+1]; padded offsets int64[N+1]; padded ids
-//             int32[Mp + 16]: trial t at [poff[t], poff[t+1]), a multiple of
-//             4 positions, gaps and tail filled with the sentinel id (the
-//             catalog size); ts float32[M] or none; staging for host ids
+//   YET       raw offsets int64[N+1]; chunk offsets int64[N+1]; id chunks
+//             int4[Mc + kChunkTail]: trial t at chunks [coff[t], coff[t+1]),
+//             6 ids of 21 bits per chunk when the catalog fits (else 4 plain
+//             ids), gaps and tail filled with the sentinel id (the catalog
+//             size); ts float32[M] or none; staging for host ids
 //   ELT pool  one block per ara_load_elts call: ids int32 (sorted by id per
 //             ELT), losses f64 (same order), fold bucket index int32
 //   layer     EltDesc[J]; fixed-point table 16 B x catalog; zero-skip bitmap
@@ -46,6 +47,7 @@ struct LayerRec {
   double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
   int32_t precision = ARA_FP64;
   EltDesc *d_desc = nullptr;
+  int32_t desc_cap = 0;
   ulonglong2 *d_table = nullptr;
   uint32_t *d_bitmap = nullptr;
   int32_t table_catalog = 0;
@@ -55,6 +57,20 @@ struct LayerRec {
   int64_t folded_version = -1;
   double upper = 0.0;  // upper bound of any per-event table value
 };
+
+// Device buffers of a released layer, kept for the next layer (defining and
+// releasing layers then needs no cudaMalloc/cudaFree, which would stall the
+// device).  Reuse is ordered by the context's stream.
+struct LayerBuffers {
+  EltDesc *d_desc = nullptr;
+  int32_t desc_cap = 0;
+  ulonglong2 *d_table = nullptr;
+  uint32_t *d_bitmap = nullptr;
+  int32_t table_catalog = 0;
+  BitmapLayout bm{0u, 0};
+};
+
+constexpr size_t kLayerPoolMax = 64;
 
 struct TimingChannel {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -77,13 +93,14 @@ struct ara_ctx {
   int64_t n_occ = 0;
   int64_t max_trial_len = 0;
   std::vector<int64_t> h_offsets;   // raw CSR offsets
-  std::vector<int64_t> h_poff;      // padded offsets (multiples of 4)
+  std::vector<int64_t> h_coff;      // chunk offsets
   int64_t *d_offsets = nullptr;     // raw offsets
   size_t cap_offsets = 0;
-  int64_t *d_poff = nullptr;        // padded offsets
-  size_t cap_poff = 0;
-  int32_t *d_ids = nullptr;         // padded ids + 16-entry sentinel tail
-  size_t cap_ids = 0;
+  int64_t *d_coff = nullptr;        // chunk offsets
+  size_t cap_coff = 0;
+  int4 *d_chunks = nullptr;         // id chunks + sentinel tail
+  size_t cap_chunks = 0;
+  bool packed = false;              // 6 ids of 21 bits per chunk
   int32_t *d_raw = nullptr;         // staging for ids copied from the host
   size_t cap_raw = 0;
   float *d_ts = nullptr;
@@ -94,6 +111,7 @@ struct ara_ctx {
   std::vector<void *> elt_blocks;
   // layers
   std::vector<LayerRec> layers;
+  std::vector<LayerBuffers> pool;
   // scratch
   double *d_ylt_stage = nullptr;
   size_t cap_ylt_stage = 0;
@@ -301,6 +319,49 @@ void free_layer(LayerRec &L) {
   L = LayerRec();
 }
 
+void free_buffers(LayerBuffers &B) {
+  if (B.d_desc) cudaFree(B.d_desc);
+  if (B.d_table) cudaFree(B.d_table);
+  if (B.d_bitmap) cudaFree(B.d_bitmap);
+  B = LayerBuffers();
+}
+
+// Hand a layer's buffers to the pool (or free them when the pool is full).
+void recycle_layer(ara_ctx *c, LayerRec &L) {
+  LayerBuffers B;
+  B.d_desc = L.d_desc;
+  B.desc_cap = L.desc_cap;
+  B.d_table = L.d_table;
+  B.d_bitmap = L.d_bitmap;
+  B.table_catalog = L.table_catalog;
+  B.bm = L.bm;
+  L = LayerRec();
+  if (c->pool.size() < kLayerPoolMax) {
+    c->pool.push_back(B);
+  } else {
+    cudaStreamSynchronize(c->stream);
+    free_buffers(B);
+  }
+}
+
+// Take pooled buffers that fit (descriptor capacity and catalog size).
+bool take_pooled(ara_ctx *c, int32_t n_elts, LayerRec &L) {
+  for (size_t i = c->pool.size(); i-- > 0;) {
+    LayerBuffers &B = c->pool[i];
+    if (B.desc_cap >= n_elts && B.table_catalog == c->catalog && B.d_table) {
+      L.d_desc = B.d_desc;
+      L.desc_cap = B.desc_cap;
+      L.d_table = B.d_table;
+      L.d_bitmap = B.d_bitmap;
+      L.table_catalog = B.table_catalog;
+      L.bm = B.bm;
+      c->pool.erase(c->pool.begin() + (long)i);
+      return true;
+    }
+  }
+  return false;
+}
+
 ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out) {
   if (layer < 0 || layer >= (int32_t)c->layers.size() || !c->layers[layer].live)
     return fail(c, ARA_E_NOT_FOUND, "unknown layer handle %d", layer);
@@ -376,10 +437,11 @@ void ara_destroy(ara_ctx *c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &L : c->layers) free_layer(L);
+  for (auto &B : c->pool) free_buffers(B);
   for (void *p : c->elt_blocks) cudaFree(p);
   cudaFree(c->d_offsets);
-  cudaFree(c->d_poff);
-  cudaFree(c->d_ids);
+  cudaFree(c->d_coff);
+  cudaFree(c->d_chunks);
   cudaFree(c->d_raw);
   cudaFree(c->d_ts);
   cudaFree(c->d_ylt_stage);
@@ -440,25 +502,28 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
     if (c->elts[j].max_id >= catalog)
       return fail(c, ARA_E_EVENT_RANGE, "loaded ELT %zu holds event id %d outside the new catalog of %d",
                   j, c->elts[j].max_id, catalog);
-  // Padded layout: every trial rounded up to a multiple of 4 positions.
+  // Chunked layout: every trial rounded up to whole 16-byte chunks.
+  const bool packed = catalog <= kPackedIdLimit;
+  const int64_t ipc = packed ? 6 : 4;
   std::vector<int64_t> hp((size_t)n_trials + 1);
   hp[0] = 0;
-  for (int64_t t = 0; t < n_trials; ++t) hp[(size_t)t + 1] = hp[(size_t)t] + ((h[(size_t)t + 1] - h[(size_t)t] + 3) & ~(int64_t)3);
-  const int64_t Mp = hp[(size_t)n_trials];
+  for (int64_t t = 0; t < n_trials; ++t)
+    hp[(size_t)t + 1] = hp[(size_t)t] + (h[(size_t)t + 1] - h[(size_t)t] + ipc - 1) / ipc;
+  const int64_t Mc = hp[(size_t)n_trials];
   // The YET is replaced in place (it can be several GB): from here on a
   // failure leaves the context without a YET.
   c->yet_loaded = false;
   c->yet_version++;
   const bool dev_ids = M > 0 && is_device_ptr(ids);
   cudaError_t e = ensure(&c->d_offsets, &c->cap_offsets, (size_t)n_trials + 1);
-  if (e == cudaSuccess) e = ensure(&c->d_poff, &c->cap_poff, (size_t)n_trials + 1);
-  if (e == cudaSuccess) e = ensure(&c->d_ids, &c->cap_ids, (size_t)Mp + 16);
+  if (e == cudaSuccess) e = ensure(&c->d_coff, &c->cap_coff, (size_t)n_trials + 1);
+  if (e == cudaSuccess) e = ensure(&c->d_chunks, &c->cap_chunks, (size_t)Mc + kChunkTail);
   if (e == cudaSuccess && M > 0 && !dev_ids) e = ensure(&c->d_raw, &c->cap_raw, (size_t)M);
   if (e == cudaSuccess && ts) e = ensure(&c->d_ts, &c->cap_ts, (size_t)std::max<int64_t>(M, 1));
   if (e != cudaSuccess) return cuda_fail(c, e, "allocate YET buffers");
   e = cudaMemcpyAsync(c->d_offsets, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->d_poff, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(c->d_coff, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
   const int32_t *src = ids;
   if (e == cudaSuccess && M > 0 && !dev_ids) {
     e = cudaMemcpyAsync(c->d_raw, ids, (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice, s);
@@ -468,7 +533,8 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
     e = cudaMemcpyAsync(c->d_ts, ts, (size_t)M * sizeof(float), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, 2 * sizeof(unsigned long long), s);
   if (e == cudaSuccess)
-    e = launch_pad_ids(src, c->d_offsets, c->d_poff, n_trials, c->d_ids, catalog, c->d_counter, s);
+    e = launch_pad_ids(src, c->d_offsets, c->d_coff, n_trials, c->d_chunks, catalog, packed,
+                       c->d_counter, s);
   if (e == cudaSuccess && ts) e = launch_check_ts(c->d_offsets, n_trials, c->d_ts, c->d_counter + 1, s);
   unsigned long long bad[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_counter, sizeof(bad), cudaMemcpyDeviceToHost, s);
@@ -485,7 +551,8 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
   c->n_occ = M;
   c->max_trial_len = lmax;
   c->h_offsets.swap(h);
-  c->h_poff.swap(hp);
+  c->h_coff.swap(hp);
+  c->packed = packed;
   return ARA_OK;
 }
 
@@ -628,10 +695,14 @@ ara_status ara_define_layer(ara_ctx *c, int32_t n_elts, const int32_t *handles, 
     desc[(size_t)j] = EltDesc{m.d_ids, m.d_losses, m.d_bucket, m.nb, m.count, m.deductible, m.limit};
   }
   L.upper = std::min(up * (1.0 + 1e-12), occ_lim);
-  ARA_CUDA(c, cudaMalloc(&L.d_desc, desc.size() * sizeof(EltDesc)), "cudaMalloc(layer ELT list)");
+  if (!take_pooled(c, n_elts, L)) {
+    L.desc_cap = std::max<int32_t>(n_elts, 64);
+    ARA_CUDA(c, cudaMalloc(&L.d_desc, (size_t)L.desc_cap * sizeof(EltDesc)), "cudaMalloc(layer ELT list)");
+  }
+  // A copy from pageable memory returns once the data is staged, so `desc`
+  // may go out of scope; the stream orders it after earlier users of d_desc.
   cudaError_t e = cudaMemcpyAsync(L.d_desc, desc.data(), desc.size() * sizeof(EltDesc),
                                   cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_layer(L);
     return cuda_fail(c, e, "upload layer ELT list");
@@ -662,8 +733,7 @@ ara_status ara_release_layer(ara_ctx *c, int32_t layer) {
   LayerRec *L = nullptr;
   ara_status st = get_layer(c, layer, &L);
   if (st) return st;
-  ARA_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  free_layer(*L);
+  recycle_layer(c, *L);
   return ARA_OK;
 }
 
@@ -718,12 +788,12 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
     ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, (size_t)n_trials), "stage buffer");
     dst = c->d_ylt_stage;
   }
-  const double mean_chunks = (double)(c->h_poff[(size_t)n_trials] / 4) / (double)n_trials;
+  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, &cfg), "plan YLT launch");
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, &cfg), "plan YLT launch");
   TimedLaunch tl(c, ARA_TIMING_YLT, s);
-  ARA_CUDA(c, launch_ylt_fp64(c->d_poff, c->d_ids, n_trials, L->d_table, L->d_bitmap, L->bm,
-                              c->catalog, L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst, cfg, s),
+  ARA_CUDA(c, launch_ylt_fp64(c->d_coff, c->d_chunks, c->packed, n_trials, L->d_table, L->d_bitmap,
+                              L->bm, c->catalog, L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst, cfg, s),
            "YLT kernel launch");
   tl.done();
   if (!dev) {

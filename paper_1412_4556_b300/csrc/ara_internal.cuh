@@ -15,6 +15,20 @@ constexpr int kFoldStage = 2048;         // ELT entries staged in smem per chunk
 constexpr int kMaxLayerElts = 1024;      // ELTs one layer may cover
 constexpr int kYltThreads = 1024;        // threads per YLT CTA (32 warps)
 constexpr int kMaxReturnPeriods = 16;
+constexpr int kChunkTail = 4;            // sentinel chunks after the last trial
+constexpr int32_t kPackedIdLimit = (1 << 21) - 1;  // catalog sizes whose ids pack in 21 bits
+
+// Six ids of at most 21 bits in one 16-byte chunk (three per 64-bit half).
+__host__ __device__ inline int4 pack6(const int32_t *v) {
+  const unsigned long long lo = (unsigned long long)(uint32_t)v[0] |
+                                ((unsigned long long)(uint32_t)v[1] << 21) |
+                                ((unsigned long long)(uint32_t)v[2] << 42);
+  const unsigned long long hi = (unsigned long long)(uint32_t)v[3] |
+                                ((unsigned long long)(uint32_t)v[4] << 21) |
+                                ((unsigned long long)(uint32_t)v[5] << 42);
+  return make_int4((int)(uint32_t)lo, (int)(uint32_t)(lo >> 32), (int)(uint32_t)hi,
+                   (int)(uint32_t)(hi >> 32));
+}
 constexpr int kSelectThreads = 512;
 
 // ------------------------------------------------------ ELT descriptor
@@ -215,19 +229,21 @@ struct YltLaunch {
   int unroll;
 };
 
-// poff/pids: the padded YET layout written by launch_pad_ids; sentinel =
-// catalog size (its table entry is zero).
-cudaError_t launch_ylt_fp64(const int64_t *poff, const int32_t *pids, int64_t n_trials,
+// coff/chunks: the chunked YET layout written by launch_pad_ids (packed: 6
+// ids of 21 bits per chunk, else 4 plain ids); sentinel = catalog size (its
+// table entry is zero).
+cudaError_t launch_ylt_fp64(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
                             int32_t sentinel, int q, const AggFixed &af, double agg_ret,
                             double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s);
 
 // Pick the launch shape of the YLT kernel for a bitmap of bm.words words and
 // trials of mean_chunks 16-byte chunks.
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, YltLaunch *out);
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed,
+                     YltLaunch *out);
 
-cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *poff,
-                           int64_t n_trials, int32_t *dst, int32_t catalog,
+cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *coff,
+                           int64_t n_trials, int4 *dst, int32_t catalog, bool packed,
                            unsigned long long *bad_count, cudaStream_t s);
 
 cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const float *ts,

@@ -11,10 +11,12 @@
 // B300 design:
 //  * One warp per trial; each warp owns a contiguous run of trials, so the
 //    YET id stream is read once, in 16-byte coalesced loads, U loads in flight
-//    per lane, with an evict-first L2 policy.  The engine stores every trial
-//    padded to a multiple of 4 ids with a sentinel event whose table entry is
-//    zero, so each 16-byte chunk belongs to one trial and no per-event bounds
-//    test is needed.
+//    per lane, with an evict-first L2 policy; one lane bulk-prefetches the
+//    next trial into L2.  The engine stores every trial as whole 16-byte
+//    chunks (4 plain ids, or 6 ids of 21 bits when the catalog allows, which
+//    cuts the id stream by a third), padded with a sentinel event whose table
+//    entry is zero, so each chunk belongs to one trial and no per-event
+//    bounds test is needed.
 //  * The layer's zero-skip bitmap sits in shared memory.  Only occurrences
 //    whose bit is set fetch their table entry (a random 16-byte gather served
 //    by L2, evict-last); the rest add an exact zero and are skipped.
@@ -77,12 +79,32 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <int U>
+// The ids of one 16-byte chunk: four plain 32-bit ids, or six 21-bit ids
+// packed three to a 64-bit half (see pack6).
+template <bool PACKED>
+__device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]) {
+  if constexpr (PACKED) {
+    constexpr uint32_t M = 0x1FFFFFu;
+    id[0] = (uint32_t)c.x & M;
+    id[1] = __funnelshift_r((uint32_t)c.x, (uint32_t)c.y, 21) & M;
+    id[2] = ((uint32_t)c.y >> 10) & M;
+    id[3] = (uint32_t)c.z & M;
+    id[4] = __funnelshift_r((uint32_t)c.z, (uint32_t)c.w, 21) & M;
+    id[5] = ((uint32_t)c.w >> 10) & M;
+  } else {
+    id[0] = (uint32_t)c.x;
+    id[1] = (uint32_t)c.y;
+    id[2] = (uint32_t)c.z;
+    id[3] = (uint32_t)c.w;
+  }
+}
+
+template <int U, bool PACKED>
 __global__ void __launch_bounds__(kYltThreads, 1)
-ylt_fp64_kernel(const int64_t *__restrict__ poff, const int4 *__restrict__ pids4,
+ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
                 int64_t n_trials, const ulonglong2 *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
-                int32_t sentinel, int q, AggFixed af, double agg_ret, double agg_lim,
+                int4 sent4, int q, AggFixed af, double agg_ret, double agg_lim,
                 double *__restrict__ ylt) {
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
@@ -96,23 +118,22 @@ ylt_fp64_kernel(const int64_t *__restrict__ poff, const int4 *__restrict__ pids4
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t t_begin = n_trials * w / n_warps;
   const int64_t t_end = n_trials * (w + 1) / n_warps;
-  const int4 sent4 = make_int4(sentinel, sentinel, sentinel, sentinel);
 
-  int64_t p_next = t_begin < t_end ? poff[t_begin] : 0;
+  int64_t p_next = t_begin < t_end ? coff[t_begin] : 0;
   if (lane == 0 && t_begin < t_end) {
-    const int64_t b = poff[t_begin + 1];
-    if (b > p_next) prefetch_l2(pids4 + (p_next >> 2), (uint32_t)((b - p_next) * 4));
+    const int64_t b = coff[t_begin + 1];
+    if (b > p_next) prefetch_l2(chunks + p_next, (uint32_t)((b - p_next) * 16));
   }
   for (int64_t t = t_begin; t < t_end; ++t) {
     const int64_t p0 = p_next;
-    p_next = poff[t + 1];
+    p_next = coff[t + 1];
     // While this trial is summed, its successor's ids travel to L2.
     if (lane == 0 && t + 1 < t_end) {
-      const int64_t b = poff[t + 2];
-      if (b > p_next) prefetch_l2(pids4 + (p_next >> 2), (uint32_t)((b - p_next) * 4));
+      const int64_t b = coff[t + 2];
+      if (b > p_next) prefetch_l2(chunks + p_next, (uint32_t)((b - p_next) * 16));
     }
-    const int4 *tp = pids4 + (p0 >> 2);
-    const int nk = (int)((p_next - p0) >> 2);  // 16-byte chunks of this trial
+    const int4 *tp = chunks + p0;
+    const int nk = (int)(p_next - p0);  // 16-byte chunks of this trial
     U128 acc{0ull, 0ull};
     for (int base = 0; base < nk; base += 32 * U) {
       int4 v[U];
@@ -125,10 +146,10 @@ ylt_fp64_kernel(const int64_t *__restrict__ poff, const int4 *__restrict__ pids4
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (base + 32 * u >= nk) break;  // warp-uniform: the rest of this step is empty
-        const uint32_t idv[4] = {(uint32_t)v[u].x, (uint32_t)v[u].y, (uint32_t)v[u].z,
-                                 (uint32_t)v[u].w};
+        uint32_t idv[PACKED ? 6 : 4];
+        chunk_ids<PACKED>(v[u], idv);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < (PACKED ? 6 : 4); ++i) {
           const uint32_t id = idv[i];
           const uint32_t word = s_bm[bitmap_word(id, bm_mul)];
           const uint32_t hit = __funnelshift_r(word, word, id) & 1u;  // bit id & 31
@@ -142,35 +163,47 @@ ylt_fp64_kernel(const int64_t *__restrict__ poff, const int4 *__restrict__ pids4
   }
 }
 
-template <int U>
-static cudaError_t launch_u(const int64_t *poff, const int32_t *pids, int64_t n_trials,
+template <int U, bool PACKED>
+static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
                             int32_t sentinel, int q, const AggFixed &af, double agg_ret,
                             double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U>,
+  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.smem);
   if (err != cudaSuccess) return err;
-  ylt_fp64_kernel<U><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
-      poff, reinterpret_cast<const int4 *>(pids), n_trials, table,
-      reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sentinel, q, af, agg_ret,
-      agg_lim, ylt);
+  int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
+  const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
+  ylt_fp64_kernel<U, PACKED><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
+      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul,
+      sent4, q, af, agg_ret, agg_lim, ylt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ylt_fp64(const int64_t *poff, const int32_t *pids, int64_t n_trials,
+template <bool PACKED>
+static cudaError_t launch_p(const int64_t *coff, const int4 *chunks, int64_t n_trials,
+                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
+                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
+  switch (cfg.unroll) {
+    case 1: return launch_u<1, PACKED>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+    case 2: return launch_u<2, PACKED>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+    default: return launch_u<4, PACKED>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+  }
+}
+
+cudaError_t launch_ylt_fp64(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
                             int32_t sentinel, int q, const AggFixed &af, double agg_ret,
                             double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
-  switch (cfg.unroll) {
-    case 1: return launch_u<1>(poff, pids, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
-    case 2: return launch_u<2>(poff, pids, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
-    default: return launch_u<4>(poff, pids, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
-  }
+  if (packed)
+    return launch_p<true>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+  return launch_p<false>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
 }
 
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, YltLaunch *out) {
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed,
+                     YltLaunch *out) {
   int sms = 0;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
@@ -186,9 +219,12 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, Ylt
   out->threads = kYltThreads;
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
-  const void *fn = unroll == 1 ? (const void *)ylt_fp64_kernel<1>
-                 : unroll == 2 ? (const void *)ylt_fp64_kernel<2>
-                               : (const void *)ylt_fp64_kernel<4>;
+  const void *fn = packed ? (unroll == 1 ? (const void *)ylt_fp64_kernel<1, true>
+                             : unroll == 2 ? (const void *)ylt_fp64_kernel<2, true>
+                                           : (const void *)ylt_fp64_kernel<4, true>)
+                          : (unroll == 1 ? (const void *)ylt_fp64_kernel<1, false>
+                             : unroll == 2 ? (const void *)ylt_fp64_kernel<2, false>
+                                           : (const void *)ylt_fp64_kernel<4, false>);
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
