@@ -207,7 +207,7 @@ def _log_uniform(g: np.random.Generator, lo: float, hi: float) -> float:
 
 def random_layer(g: np.random.Generator, n_pool: int, k_lo: int, k_hi: int) -> Layer:
     """k ~ U{k_lo..k_hi} distinct pool ELTs; terms log-uniform over the batched-layer ranges."""
-    k = int(g.integers(k_lo, k_hi + 1))
+    k = min(int(g.integers(k_lo, k_hi + 1)), n_pool)
     elts = [int(x) for x in g.choice(n_pool, size=k, replace=False)]
     return Layer(elts,
                  occ_ret=_log_uniform(g, 1e4, 1e6), occ_lim=_log_uniform(g, 1e6, 1e8),

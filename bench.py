@@ -380,6 +380,94 @@ def run_e2e(args, w, handles_count: int, local: int):
                     "ara_layer_ylt(host out)/ara_pml_tvar; YET ids validated on the device each step"}
 
 
+# ------------------------------------------------------- batched layers
+BATCHED = ("batched layers, FP64: the paper-scale YET (1,000,000 trials x Poisson(1000), catalog "
+           "2,000,000) shared by 64 layers of U{1..32} ELTs from a pool of 256 ELTs of U{10k..50k} "
+           "events; per-layer OccR/OccL/AggR/AggL log-uniform over [1e4,1e6]/[1e6,1e8]/[1e5,1e7]/"
+           "[1e7,1e9]; RP 100/250/500")
+
+
+def run_batched(args):
+    """Config-2 step: define 64 layers (ELT folds), price them in pairs in one
+    call (ara_layers_ylt), PML/TVaR for all (ara_pml_tvar_batch).  Also times
+    the plain path (ara_layer_ylt once per layer) for comparison."""
+    import torch
+    from paper_1412_4556_b300 import ARA_TIMING_YLT, Engine
+
+    w = S.batched(n_trials=args.trials)
+    M, N = w.yet.n_occurrences, w.yet.n_trials
+    G = len(w.layers)
+    stream = torch.cuda.Stream()
+    eng = Engine(0, stream=stream)
+    eng.load_yet_from(w.yet)
+    first = eng.load_pool(w.pool)
+    handles = [[first + j for j in L.elts] for L in w.layers]
+    out = torch.empty((G, N), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+
+    def define():
+        return [eng.define_layer(h, L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim)
+                for h, L in zip(handles, w.layers)]
+
+    def step_batched():
+        hs = define()
+        eng.layers_ylt(hs, out=out)
+        res = eng.pml_tvar_batch(out, w.return_periods)
+        for h in hs:
+            eng.release_layer(h)
+        return res
+
+    def step_plain():
+        hs = define()
+        for i, h in enumerate(hs):
+            eng.layer_ylt(h, out=out[i])
+        res = eng.pml_tvar_batch(out, w.return_periods)
+        for h in hs:
+            eng.release_layer(h)
+        return res
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eng.set_kernel_timing(True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        n_k, k_ms = eng.kernel_timing(ARA_TIMING_YLT)
+        eng.set_kernel_timing(False)
+        return e0.elapsed_time(e1) / steps, k_ms / steps
+
+    steps = max(3, min(args.steps, 20))
+    with ClockSampler(0) as clocks:
+        clocks.wait_first_sample()
+        t0 = time.monotonic()
+        ms_b, ylt_b = timed(step_batched, steps)
+        t1 = time.monotonic()
+        time.sleep(0.3)
+        clocks.mark(t0, t1)
+    ms_p, ylt_p = timed(step_plain, steps)
+    value = G * M / (ms_b / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "layer-trial-events/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": BATCHED, "layers": G, "n_trials": N, "occurrences": M,
+                   "step": "64 x ara_define_layer + ara_layers_ylt + ara_pml_tvar_batch",
+                   "l2": "inputs larger than L2 (4 GB YET id stream per layer pair)"},
+        "ylt_kernels_ms_per_step": ylt_b,
+        "plain_per_layer": {"ms_per_step": ms_p, "ylt_kernels_ms_per_step": ylt_p,
+                            "value": G * M / (ms_p / 1e3),
+                            "step": "64 x ara_define_layer + 64 x ara_layer_ylt + ara_pml_tvar_batch"},
+        "speedup_vs_plain": ms_p / ms_b,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ oracle arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -420,6 +508,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
+                    help="paper: the single-layer paper-scale step (default); batched: 64 layers")
     ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
@@ -429,6 +519,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_engine(args)
 

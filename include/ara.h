@@ -200,6 +200,27 @@ ARA_API ara_status ara_pml_tvar(ara_ctx *ctx, const double *ylt, int64_t n,
                         const double *return_periods, int32_t n_rp, double *pml_out,
                         double *tvar_out);
 
+/* Year Loss Tables of several layers over the first n_trials trials
+ * (Section III: a Program covers several Layers, a Portfolio several
+ * Programs; each layer's YLT is Algorithm 1 for that layer).
+ *   layers       n_layers layer handles
+ *   ylt_out      double[n_layers][n_trials], host or device, layer-major:
+ *                ylt_out[i * n_trials + t] is trial t of layers[i]
+ *   cuda_stream  stream for this call only, or NULL for the context's stream
+ * Layers are priced two at a time: their tables are interleaved so one L2
+ * sector serves both, and one pass over the YET feeds both.  Each value is
+ * identical to ara_layer_ylt's for the same layer.  Errors as ara_layer_ylt. */
+ARA_API ara_status ara_layers_ylt(ara_ctx *ctx, int32_t n_layers, const int32_t *layers,
+                                  int64_t n_trials, double *ylt_out, void *cuda_stream);
+
+/* PML and TVaR of n_layers YLTs of n trials each, as ara_pml_tvar for each
+ * layer.  ylt: double[n_layers][n] (host or device, layer-major);
+ * return_periods: double[n_rp] (host); pml_out, tvar_out: double[n_layers][n_rp]
+ * (host).  Errors as ara_pml_tvar. */
+ARA_API ara_status ara_pml_tvar_batch(ara_ctx *ctx, const double *ylt, int32_t n_layers, int64_t n,
+                                      const double *return_periods, int32_t n_rp, double *pml_out,
+                                      double *tvar_out);
+
 /* Allocation-free variant of ara_pml_tvar.  The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc -- a service whose
  * pooling allocator already owns the device memory it may use, or a

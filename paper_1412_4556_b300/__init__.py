@@ -135,6 +135,31 @@ class Engine:
         _native.ara_layer_ylt(self.ctx, layer, n, p, int(handle or 0))
         return out
 
+    def layers_ylt(self, layers: Sequence[int], n_trials: Optional[int] = None, out=None, stream=None):
+        """YLTs of several layers in one call: array [len(layers), n_trials]
+        (NumPy by default, or a CUDA tensor given as ``out``)."""
+        h = np.ascontiguousarray(layers, dtype=np.int32)
+        n = self.n_trials if n_trials is None else int(n_trials)
+        if out is None:
+            out = np.empty((h.shape[0], n), dtype=np.float64)
+        p, keep = _arg(out, np.float64, "out")
+        if keep is not out:
+            raise TypeError("out must be a contiguous float64 array or tensor")
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+        _native.ara_layers_ylt(self.ctx, int(h.shape[0]), h.ctypes.data, n, p, int(handle or 0))
+        return out
+
+    def pml_tvar_batch(self, ylts, return_periods: Sequence[float]):
+        """PML and TVaR per layer of a [n_layers, n] YLT array: two [n_layers, n_rp] arrays."""
+        p, keep = _arg(ylts, np.float64, "ylts")
+        n_layers, n = int(ylts.shape[0]), int(ylts.shape[1])
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        pml = np.zeros((n_layers, rps.shape[0]))
+        tvar = np.zeros((n_layers, rps.shape[0]))
+        _native.ara_pml_tvar_batch(self.ctx, p, n_layers, n, rps.ctypes.data, int(rps.shape[0]),
+                                   pml.ctypes.data, tvar.ctypes.data)
+        return pml, tvar
+
     def event_table(self, layer: int, out=None):
         """The layer's per-event occurrence-net loss (float64, one per catalog event)."""
         if out is None:

@@ -43,6 +43,8 @@ PROTOTYPES = {
     "ara_layer_ylt": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "ara_pml_tvar": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp, _vp]),
     "ara_pml_tvar_noalloc": (_i32, [_vp, _i64, _vp, _i32, _vp, _vp, _vp]),
+    "ara_layers_ylt": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp]),
+    "ara_pml_tvar_batch": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp]),
     "ara_set_kernel_timing": (_i32, [_vp, _i32]),
     "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
 }
@@ -137,6 +139,18 @@ def ara_pml_tvar(ctx: int, ylt: int, n: int, return_periods: int, n_rp: int, pml
                  tvar_out: int) -> None:
     _check(ctx, lib.ara_pml_tvar(ctx, ylt or None, int(n), return_periods or None, int(n_rp),
                                  pml_out or None, tvar_out or None))
+
+
+def ara_layers_ylt(ctx: int, n_layers: int, layers: int, n_trials: int, ylt_out: int,
+                   stream: int = 0) -> None:
+    _check(ctx, lib.ara_layers_ylt(ctx, int(n_layers), layers or None, int(n_trials), ylt_out or None,
+                                   stream or None))
+
+
+def ara_pml_tvar_batch(ctx: int, ylt: int, n_layers: int, n: int, return_periods: int, n_rp: int,
+                       pml_out: int, tvar_out: int) -> None:
+    _check(ctx, lib.ara_pml_tvar_batch(ctx, ylt or None, int(n_layers), int(n), return_periods or None,
+                                       int(n_rp), pml_out or None, tvar_out or None))
 
 
 def ara_pml_tvar_noalloc(ylt: int, n: int, return_periods: int, n_rp: int, pml_out: int,

@@ -119,6 +119,15 @@ struct ara_ctx {
   size_t cap_sel_in = 0;
   void *d_sel_ws = nullptr;
   double *d_sel_out = nullptr;
+  unsigned char *d_sel_ws_batch = nullptr;  // per-layer selection states
+  size_t cap_sel_ws_batch = 0;
+  double *d_sel_out_batch = nullptr;
+  size_t cap_sel_out_batch = 0;
+  ulonglong2 *d_pair_table = nullptr;       // two layers' tables interleaved
+  size_t cap_pair_table = 0;
+  uint32_t *d_pair_bitmap = nullptr;        // union of their bitmaps
+  size_t cap_pair_bitmap = 0;
+  int tuned_unroll[3] = {0, 0, 0};          // YLT unroll picked by the autotuner, per G
   unsigned long long *d_counter = nullptr;  // validation counters
   unsigned int *d_err = nullptr;            // PML/TVaR input check flag
   // timing
@@ -448,6 +457,10 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_sel_in);
   cudaFree(c->d_sel_ws);
   cudaFree(c->d_sel_out);
+  cudaFree(c->d_sel_ws_batch);
+  cudaFree(c->d_sel_out_batch);
+  cudaFree(c->d_pair_table);
+  cudaFree(c->d_pair_bitmap);
   cudaFree(c->d_counter);
   cudaFree(c->d_err);
   for (auto &ch : c->chan)
@@ -790,10 +803,12 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
   }
   const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, &cfg), "plan YLT launch");
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, 1, c->tuned_unroll[1], &cfg),
+           "plan YLT launch");
+  const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst};
   TimedLaunch tl(c, ARA_TIMING_YLT, s);
-  ARA_CUDA(c, launch_ylt_fp64(c->d_coff, c->d_chunks, c->packed, n_trials, L->d_table, L->d_bitmap,
-                              L->bm, c->catalog, L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst, cfg, s),
+  ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, L->d_table, L->d_bitmap,
+                               L->bm, c->catalog, 1, &out, cfg, s),
            "YLT kernel launch");
   tl.done();
   if (!dev) {
@@ -843,6 +858,128 @@ ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *
     pml_out[r] = out[r];
     tvar_out[r] = out[n_rp + r];
   }
+  return ARA_OK;
+}
+
+ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, int64_t n_trials,
+                          double *ylt_out, void *cuda_stream) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  if (n_layers < 1 || !layers) return fail(c, ARA_E_INVALID_ARG, "need n_layers >= 1 layer handles");
+  if (n_trials < 0 || n_trials > c->n_trials)
+    return fail(c, ARA_E_INVALID_ARG, "n_trials %lld outside [0, %lld]", (long long)n_trials,
+                (long long)c->n_trials);
+  if (n_trials > 0 && !ylt_out) return fail(c, ARA_E_INVALID_ARG, "ylt_out is NULL");
+  std::vector<LayerRec *> Ls((size_t)n_layers);
+  for (int32_t i = 0; i < n_layers; ++i) {
+    ara_status st = get_layer(c, layers[i], &Ls[(size_t)i]);
+    if (st) return st;
+  }
+  if (n_trials == 0) return ARA_OK;
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+  for (LayerRec *L : Ls)
+    if (L->folded_version != c->yet_version) {
+      ara_status st = fold_layer(c, *L, s);
+      if (st) return st;
+    }
+  const bool dev = is_device_ptr(ylt_out);
+  double *dst = ylt_out;
+  const size_t total = (size_t)n_layers * (size_t)n_trials;
+  if (!dev) {
+    ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, total), "stage buffer");
+    dst = c->d_ylt_stage;
+  }
+  const BitmapLayout bm = Ls[0]->bm;  // every layer of a catalog shares the layout
+  const size_t entries = (size_t)c->catalog + 1;
+  if (n_layers > 1) {
+    ARA_CUDA(c, ensure(&c->d_pair_table, &c->cap_pair_table, 2 * entries), "pair table");
+    ARA_CUDA(c, ensure(&c->d_pair_bitmap, &c->cap_pair_bitmap, (size_t)bm.words), "pair bitmap");
+  }
+  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
+  for (int32_t i = 0; i < n_layers; i += 2) {
+    const int G = (i + 1 < n_layers) ? 2 : 1;
+    LayerOut outs[2];
+    for (int g = 0; g < G; ++g) {
+      const LayerRec *L = Ls[(size_t)(i + g)];
+      outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst + (size_t)(i + g) * (size_t)n_trials};
+    }
+    const ulonglong2 *table = Ls[(size_t)i]->d_table;
+    const uint32_t *bitmap = Ls[(size_t)i]->d_bitmap;
+    if (G == 2) {
+      ARA_CUDA(c, launch_interleave(Ls[(size_t)i]->d_table, Ls[(size_t)i + 1]->d_table, (int64_t)entries,
+                                    c->d_pair_table, Ls[(size_t)i]->d_bitmap, Ls[(size_t)i + 1]->d_bitmap,
+                                    bm.words, c->d_pair_bitmap, s),
+               "interleave layer tables");
+      table = c->d_pair_table;
+      bitmap = c->d_pair_bitmap;
+    }
+    YltLaunch cfg;
+    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, G, c->tuned_unroll[G], &cfg),
+             "plan YLT launch");
+    TimedLaunch tl(c, ARA_TIMING_YLT, s);
+    ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, bitmap, bm,
+                                 c->catalog, G, outs, cfg, s),
+             "YLT kernel launch");
+    tl.done();
+  }
+  if (!dev) {
+    ARA_CUDA(c, cudaMemcpyAsync(ylt_out, dst, total * sizeof(double), cudaMemcpyDeviceToHost, s), "copy YLTs");
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
+  return ARA_OK;
+}
+
+ara_status ara_pml_tvar_batch(ara_ctx *c, const double *ylt, int32_t n_layers, int64_t n,
+                              const double *rps, int32_t n_rp, double *pml_out, double *tvar_out) {
+  if (!c) return ARA_E_INVALID_ARG;
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (n < 1 || !ylt || n_layers < 1) return fail(c, ARA_E_INVALID_ARG, "need n_layers >= 1 and n >= 1 trial losses");
+  if (n_layers > 65535) return fail(c, ARA_E_INVALID_ARG, "at most 65535 layers per call");
+  if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps || !pml_out || !tvar_out)
+    return fail(c, ARA_E_INVALID_ARG, "need 1..%d return periods and output arrays", kMaxReturnPeriods);
+  int64_t k[kMaxReturnPeriods];
+  for (int32_t r = 0; r < n_rp; ++r) {
+    if (!(rps[r] >= 1.0)) return fail(c, ARA_E_INVALID_ARG, "return period %d must be >= 1", r);
+    const double kk = std::floor((double)n / rps[r]);
+    if (kk < 1.0) return fail(c, ARA_E_INVALID_ARG, "return period %g exceeds the %lld trials", rps[r], (long long)n);
+    k[r] = (int64_t)kk;
+  }
+  cudaStream_t s = c->stream;
+  const size_t total = (size_t)n_layers * (size_t)n;
+  const double *src = ylt;
+  if (!is_device_ptr(ylt)) {
+    ARA_CUDA(c, ensure(&c->d_sel_in, &c->cap_sel_in, total), "selection input buffer");
+    ARA_CUDA(c, cudaMemcpyAsync(c->d_sel_in, ylt, total * sizeof(double), cudaMemcpyHostToDevice, s),
+             "copy YLTs");
+    src = c->d_sel_in;
+  }
+  ARA_CUDA(c, ensure(&c->d_sel_ws_batch, &c->cap_sel_ws_batch,
+                     (size_t)n_layers * select_workspace_bytes(kMaxReturnPeriods)),
+           "selection workspace");
+  ARA_CUDA(c, ensure(&c->d_sel_out_batch, &c->cap_sel_out_batch, (size_t)n_layers * 2 * (size_t)n_rp),
+           "selection output");
+  ARA_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
+  TimedLaunch tl(c, ARA_TIMING_PML, s);
+  ARA_CUDA(c, launch_pml_tvar_batch(src, n_layers, n, k, n_rp, c->d_sel_ws_batch, c->d_sel_out_batch,
+                                    c->d_err, c->device, s),
+           "PML/TVaR kernels");
+  tl.done();
+  std::vector<double> out((size_t)n_layers * 2 * (size_t)n_rp);
+  unsigned int bad = 0;
+  ARA_CUDA(c, cudaMemcpyAsync(out.data(), c->d_sel_out_batch, out.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, s),
+           "copy PML/TVaR");
+  ARA_CUDA(c, cudaMemcpyAsync(&bad, c->d_err, sizeof(bad), cudaMemcpyDeviceToHost, s), "copy flag");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (bad) return fail(c, ARA_E_INVALID_ARG, "trial losses must be finite and >= 0");
+  for (int32_t l = 0; l < n_layers; ++l)
+    for (int32_t r = 0; r < n_rp; ++r) {
+      pml_out[(size_t)l * n_rp + r] = out[(size_t)l * 2 * n_rp + r];
+      tvar_out[(size_t)l * n_rp + r] = out[(size_t)l * 2 * n_rp + n_rp + r];
+    }
   return ARA_OK;
 }
 

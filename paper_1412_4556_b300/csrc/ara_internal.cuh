@@ -229,18 +229,33 @@ struct YltLaunch {
   int unroll;
 };
 
+// Per-layer constants and output of one YLT kernel launch.
+struct LayerOut {
+  int q;             // fixed-point exponent of the layer's table
+  AggFixed af;       // aggregate terms on the table's grid
+  double agg_ret;
+  double agg_lim;
+  double *ylt;       // device output, one value per trial
+};
+
 // coff/chunks: the chunked YET layout written by launch_pad_ids (packed: 6
 // ids of 21 bits per chunk, else 4 plain ids); sentinel = catalog size (its
-// table entry is zero).
-cudaError_t launch_ylt_fp64(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
-                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
-                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s);
+// table entry is zero).  G = 1: one layer's table (16 bytes per event);
+// G = 2: two layers' tables interleaved (32 bytes per event) with the union
+// of their bitmaps.
+cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
+                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                             int32_t sentinel, int G, const LayerOut *outs, const YltLaunch &cfg,
+                             cudaStream_t s);
 
 // Pick the launch shape of the YLT kernel for a bitmap of bm.words words and
-// trials of mean_chunks 16-byte chunks.
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed,
-                     YltLaunch *out);
+// trials of mean_chunks 16-byte chunks (unroll_hint 1/2/4 forces the unroll).
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int G,
+                     int unroll_hint, YltLaunch *out);
+
+cudaError_t launch_interleave(const ulonglong2 *ta, const ulonglong2 *tb, int64_t entries,
+                              ulonglong2 *out, const uint32_t *ba, const uint32_t *bb,
+                              int32_t words, uint32_t *bout, cudaStream_t s);
 
 cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *coff,
                            int64_t n_trials, int4 *dst, int32_t catalog, bool packed,
@@ -249,7 +264,9 @@ cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t
 cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const float *ts,
                             unsigned long long *bad_count, cudaStream_t s);
 
-// PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes.
+// PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes
+// per layer; the batch form reads n_layers YLTs of n values each (layer-major)
+// and writes 2*n_rp values per layer (PML then TVaR).
 size_t select_workspace_bytes(int n_rp);
 // Upper bound of select_workspace_bytes() for any n_rp <= kMaxReturnPeriods.
 constexpr size_t kSelectWorkspaceMax = 32 * 1024;
@@ -259,5 +276,8 @@ void set_context_free_error(const char *msg);
 cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp,
                             void *ws, double *out_pml_tvar /* device, 2*n_rp */,
                             unsigned int *err_flag, int device, cudaStream_t s);
+cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, const int64_t *k,
+                                  int n_rp, void *ws, double *out, unsigned int *err_flag,
+                                  int device, cudaStream_t s);
 
 }  // namespace ara

@@ -38,7 +38,8 @@ struct KArgs {
   long long k[kMaxReturnPeriods];
 };
 
-__global__ void select_init_kernel(SelState *st, KArgs ka, int n_rp) {
+__global__ void select_init_kernel(SelState *states, KArgs ka, int n_rp) {
+  SelState *st = states + blockIdx.x;
   const int tid = threadIdx.x;
   unsigned int *h = &st->hist[0][0];
   for (int i = tid; i < kMaxReturnPeriods * 256; i += blockDim.x) h[i] = 0u;
@@ -59,8 +60,10 @@ __global__ void select_init_kernel(SelState *st, KArgs ka, int n_rp) {
 }
 
 __global__ void __launch_bounds__(kSelectThreads)
-select_pass_kernel(const double *__restrict__ y, int64_t n, int n_rp, int pass, SelState *st,
-                   unsigned int *err) {
+select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pass,
+                   SelState *states, unsigned int *err) {
+  const double *__restrict__ y = ylts + (size_t)blockIdx.y * (size_t)n;
+  SelState *st = states + blockIdx.y;
   __shared__ unsigned int sh[kMaxReturnPeriods][256];
   __shared__ unsigned long long s_prefix[kMaxReturnPeriods];
   __shared__ bool s_last;
@@ -139,10 +142,13 @@ __device__ __forceinline__ int select_q(unsigned long long max_key, int64_t n) {
   return e1 + lg + 1 - 127;
 }
 
-// grid.y = return period index.
+// grid.y = return period index, grid.z = layer.
 __global__ void __launch_bounds__(kSelectThreads)
-select_sum_kernel(const double *__restrict__ y, int64_t n, int n_rp, SelState *st,
-                  double *out) {
+select_sum_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, SelState *states,
+                  double *outs) {
+  const double *__restrict__ y = ylts + (size_t)blockIdx.z * (size_t)n;
+  SelState *st = states + blockIdx.z;
+  double *out = outs + (size_t)blockIdx.z * 2 * (size_t)n_rp;
   __shared__ unsigned long long s_lo[kSelectThreads / 32], s_hi[kSelectThreads / 32],
       s_cnt[kSelectThreads / 32];
   __shared__ bool s_last;
@@ -207,28 +213,38 @@ select_sum_kernel(const double *__restrict__ y, int64_t n, int n_rp, SelState *s
   st->done_sum = 0u;
 }
 
-cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp, void *ws,
-                            double *out, unsigned int *err_flag, int device, cudaStream_t s) {
+cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, const int64_t *k,
+                                  int n_rp, void *ws, double *out, unsigned int *err_flag,
+                                  int device, cudaStream_t s) {
   SelState *st = reinterpret_cast<SelState *>(ws);
   KArgs ka;
   for (int i = 0; i < kMaxReturnPeriods; ++i) ka.k[i] = i < n_rp ? (long long)k[i] : 1;
-  select_init_kernel<<<1, 256, 0, s>>>(st, ka, n_rp);
+  select_init_kernel<<<n_layers, 256, 0, s>>>(st, ka, n_rp);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   int64_t blocks = (n + kSelectThreads - 1) / kSelectThreads;
-  if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+  int64_t cap = ((int64_t)sms * 4 + n_layers - 1) / n_layers;
+  if (cap < 1) cap = 1;
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   for (int pass = 0; pass < 8; ++pass) {
-    select_pass_kernel<<<(int)blocks, kSelectThreads, 0, s>>>(ylt, n, n_rp, pass, st, err_flag);
+    select_pass_kernel<<<dim3((unsigned)blocks, (unsigned)n_layers), kSelectThreads, 0, s>>>(
+        ylts, n, n_rp, pass, st, err_flag);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
   int64_t bx = (blocks + n_rp - 1) / n_rp;
   if (bx < 1) bx = 1;
-  select_sum_kernel<<<dim3((unsigned)bx, (unsigned)n_rp), kSelectThreads, 0, s>>>(ylt, n, n_rp, st, out);
+  select_sum_kernel<<<dim3((unsigned)bx, (unsigned)n_rp, (unsigned)n_layers), kSelectThreads, 0, s>>>(
+      ylts, n, n_rp, st, out);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp, void *ws,
+                            double *out, unsigned int *err_flag, int device, cudaStream_t s) {
+  return launch_pml_tvar_batch(ylt, 1, n, k, n_rp, ws, out, err_flag, device, s);
 }
 
 }  // namespace ara

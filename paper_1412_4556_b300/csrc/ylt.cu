@@ -99,13 +99,39 @@ __device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]
   }
 }
 
-template <int U, bool PACKED>
+// Table entries of `id` for G layers (16 bytes each, interleaved) if `hit`,
+// else zeros; G = 2 is one 32-byte load, i.e. one L2 sector for two layers.
+template <int G>
+__device__ __forceinline__ void gather_group(const ulonglong2 *table, uint32_t id, uint32_t hit,
+                                             unsigned long long pol, ulonglong2 (&x)[G]) {
+  if constexpr (G == 1) {
+    x[0] = gather_if(table + id, hit, pol);
+  } else {
+    unsigned long long a = 0ull, b = 0ull, c = 0ull, d = 0ull;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%5], %6;\n\t}"
+        : "+l"(a), "+l"(b), "+l"(c), "+l"(d)
+        : "r"(hit), "l"(table + 2 * (size_t)id), "l"(pol));
+    x[0] = make_ulonglong2(a, b);
+    x[1] = make_ulonglong2(c, d);
+  }
+}
+
+template <int G>
+struct GroupOut {
+  LayerOut l[G];
+};
+
+// G layers share one pass over the YET: one zero-skip bitmap (the union of
+// the layers' bitmaps), one gather per occurrence that any layer needs, and
+// one 128-bit accumulator per layer.
+template <int U, bool PACKED, int G>
 __global__ void __launch_bounds__(kYltThreads, 1)
 ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
                 int64_t n_trials, const ulonglong2 *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
-                int4 sent4, int q, AggFixed af, double agg_ret, double agg_lim,
-                double *__restrict__ ylt) {
+                int4 sent4, GroupOut<G> out) {
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
   __syncthreads();
@@ -134,7 +160,9 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
     }
     const int4 *tp = chunks + p0;
     const int nk = (int)(p_next - p0);  // 16-byte chunks of this trial
-    U128 acc{0ull, 0ull};
+    U128 acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = U128{0ull, 0ull};
     for (int base = 0; base < nk; base += 32 * U) {
       int4 v[U];
 #pragma unroll
@@ -153,57 +181,74 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
           const uint32_t id = idv[i];
           const uint32_t word = s_bm[bitmap_word(id, bm_mul)];
           const uint32_t hit = __funnelshift_r(word, word, id) & 1u;  // bit id & 31
-          const ulonglong2 x = gather_if(table + id, hit, pol_tab);
-          add128(acc, x.x, x.y);
+          ulonglong2 x[G];
+          gather_group<G>(table, id, hit, pol_tab, x);
+#pragma unroll
+          for (int g = 0; g < G; ++g) add128(acc[g], x[g].x, x[g].y);
         }
       }
     }
-    acc = warp_sum_u128(acc);
-    if (lane == 0) ylt[t] = trial_loss(acc, q, af, agg_ret, agg_lim);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const U128 sum = warp_sum_u128(acc[g]);
+      const LayerOut &L = out.l[g];
+      if (lane == 0) L.ylt[t] = trial_loss(sum, L.q, L.af, L.agg_ret, L.agg_lim);
+    }
   }
 }
 
-template <int U, bool PACKED>
+template <int U, bool PACKED, int G>
 static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
-                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED>,
+                            int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
+                            cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.smem);
   if (err != cudaSuccess) return err;
   int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
   const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
-  ylt_fp64_kernel<U, PACKED><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
+  GroupOut<G> go;
+  for (int g = 0; g < G; ++g) go.l[g] = outs[g];
+  ylt_fp64_kernel<U, PACKED, G><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
       coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul,
-      sent4, q, af, agg_ret, agg_lim, ylt);
+      sent4, go);
   return cudaGetLastError();
 }
 
-template <bool PACKED>
-static cudaError_t launch_p(const int64_t *coff, const int4 *chunks, int64_t n_trials,
-                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
-                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
+template <bool PACKED, int G>
+static cudaError_t launch_pg(const int64_t *coff, const int4 *chunks, int64_t n_trials,
+                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                             int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
+                             cudaStream_t s) {
   switch (cfg.unroll) {
-    case 1: return launch_u<1, PACKED>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
-    case 2: return launch_u<2, PACKED>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
-    default: return launch_u<4, PACKED>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+    case 1: return launch_u<1, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    case 2: return launch_u<2, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    default: return launch_u<4, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
   }
 }
 
-cudaError_t launch_ylt_fp64(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
-                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int32_t sentinel, int q, const AggFixed &af, double agg_ret,
-                            double agg_lim, double *ylt, const YltLaunch &cfg, cudaStream_t s) {
+cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
+                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                             int32_t sentinel, int G, const LayerOut *outs, const YltLaunch &cfg,
+                             cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
-  if (packed)
-    return launch_p<true>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
-  return launch_p<false>(coff, chunks, n_trials, table, bitmap, bm, sentinel, q, af, agg_ret, agg_lim, ylt, cfg, s);
+  if (G == 2)
+    return packed ? launch_pg<true, 2>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
+                  : launch_pg<false, 2>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+  return packed ? launch_pg<true, 1>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
+                : launch_pg<false, 1>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
 }
 
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed,
-                     YltLaunch *out) {
+template <bool PACKED, int G>
+static const void *kernel_ptr(int unroll) {
+  return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, G>
+       : unroll == 2 ? (const void *)ylt_fp64_kernel<2, PACKED, G>
+                     : (const void *)ylt_fp64_kernel<4, PACKED, G>;
+}
+
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int G,
+                     int unroll_hint, YltLaunch *out) {
   int sms = 0;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
@@ -212,6 +257,7 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   // last step of a trial, more warps' worth of registers free).
   const double per_lane = mean_chunks / 32.0;
   int unroll = per_lane > 1.5 ? 2 : 1;
+  if (unroll_hint == 1 || unroll_hint == 2 || unroll_hint == 4) unroll = unroll_hint;
   if (const char *env = std::getenv("ARA_YLT_UNROLL")) {
     int u = std::atoi(env);
     if (u == 1 || u == 2 || u == 4) unroll = u;
@@ -219,12 +265,8 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   out->threads = kYltThreads;
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
-  const void *fn = packed ? (unroll == 1 ? (const void *)ylt_fp64_kernel<1, true>
-                             : unroll == 2 ? (const void *)ylt_fp64_kernel<2, true>
-                                           : (const void *)ylt_fp64_kernel<4, true>)
-                          : (unroll == 1 ? (const void *)ylt_fp64_kernel<1, false>
-                             : unroll == 2 ? (const void *)ylt_fp64_kernel<2, false>
-                                           : (const void *)ylt_fp64_kernel<4, false>);
+  const void *fn = G == 2 ? (packed ? kernel_ptr<true, 2>(unroll) : kernel_ptr<false, 2>(unroll))
+                          : (packed ? kernel_ptr<true, 1>(unroll) : kernel_ptr<false, 1>(unroll));
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
@@ -233,6 +275,28 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   if (per_sm < 1) per_sm = 1;
   out->blocks = sms * per_sm;
   return cudaSuccess;
+}
+
+// Interleave two layers' tables (entry e of layer a then of layer b, 32 bytes
+// per event) and OR their zero-skip bitmaps, for a two-layer pass.
+__global__ void interleave_kernel(const ulonglong2 *__restrict__ ta, const ulonglong2 *__restrict__ tb,
+                                  int64_t entries, ulonglong2 *__restrict__ out,
+                                  const uint32_t *__restrict__ ba, const uint32_t *__restrict__ bb,
+                                  int32_t words, uint32_t *__restrict__ bout) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < entries; e += stride) {
+    out[2 * e] = ta[e];
+    out[2 * e + 1] = tb[e];
+  }
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride)
+    bout[w] = ba[w] | bb[w];
+}
+
+cudaError_t launch_interleave(const ulonglong2 *ta, const ulonglong2 *tb, int64_t entries,
+                              ulonglong2 *out, const uint32_t *ba, const uint32_t *bb,
+                              int32_t words, uint32_t *bout, cudaStream_t s) {
+  interleave_kernel<<<148 * 8, 256, 0, s>>>(ta, tb, entries, out, ba, bb, words, bout);
+  return cudaGetLastError();
 }
 
 }  // namespace ara
