@@ -390,9 +390,14 @@ BATCHED = ("batched layers, FP64: the paper-scale YET (1,000,000 trials x Poisso
 def run_batched(args):
     """Config-2 step: define 64 layers (ELT folds), price them in pairs in one
     call (ara_layers_ylt), PML/TVaR for all (ara_pml_tvar_batch).  Also times
-    the plain path (ara_layer_ylt once per layer) for comparison."""
+    the plain path (ara_layer_ylt once per layer) for comparison.  With
+    --workload mixed the layers use FP32 tables (config 3) and the line
+    reports their error against the FP64 path."""
     import torch
-    from paper_1412_4556_b300 import ARA_TIMING_YLT, Engine
+    from paper_1412_4556_b300 import ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_YLT, Engine
+
+    mixed = args.workload == "mixed"
+    prec = ARA_FP32_TABLE if mixed else ARA_FP64
 
     w = S.batched(n_trials=args.trials)
     M, N = w.yet.n_occurrences, w.yet.n_trials
@@ -405,8 +410,8 @@ def run_batched(args):
     out = torch.empty((G, N), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
 
-    def define():
-        return [eng.define_layer(h, L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim)
+    def define(p=prec):
+        return [eng.define_layer(h, L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim, precision=p)
                 for h, L in zip(handles, w.layers)]
 
     def step_batched():
@@ -451,6 +456,22 @@ def run_batched(args):
         clocks.mark(t0, t1)
     ms_p, ylt_p = timed(step_plain, steps)
     value = G * M / (ms_b / 1e3)
+    accuracy = None
+    if mixed:
+        # Error of the FP32-table YLTs and PML/TVaR against the FP64 path (which
+        # matches the FP64 oracle within 1e-12 per trial in the parity tests).
+        h32, h64 = define(ARA_FP32_TABLE), define(ARA_FP64)
+        y32 = eng.layers_ylt(h32)
+        y64 = eng.layers_ylt(h64)
+        p32, t32 = eng.pml_tvar_batch(y32, w.return_periods)
+        p64, t64 = eng.pml_tvar_batch(y64, w.return_periods)
+        rel = np.abs(y32 - y64) / np.maximum(np.abs(y64), 1.0)
+        accuracy = {"max_rel_trial_err_vs_fp64": float(rel.max()),
+                    "max_abs_trial_err_usd": float(np.abs(y32 - y64).max()),
+                    "max_rel_pml_err": float((np.abs(p32 - p64) / np.maximum(p64, 1.0)).max()),
+                    "max_rel_tvar_err": float((np.abs(t32 - t64) / np.maximum(t64, 1.0)).max())}
+        for h in h32 + h64:
+            eng.release_layer(h)
     line = {
         "metric": METRIC, "value": value, "unit": "layer-trial-events/s", "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
@@ -465,6 +486,10 @@ def run_batched(args):
         "speedup_vs_plain": ms_p / ms_b,
         "clocks": clocks.summary(),
     }
+    if mixed:
+        line["dtype"] = "f32 tables, exact trial sums"
+        line["config"]["workload"] = "mixed precision (FP32 tables): " + BATCHED
+        line["accuracy"] = accuracy
     print(json.dumps(line), flush=True)
 
 
@@ -508,8 +533,9 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
-    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
-                    help="paper: the single-layer paper-scale step (default); batched: 64 layers")
+    ap.add_argument("--workload", choices=["paper", "batched", "mixed"], default="paper",
+                    help="paper: the single-layer paper-scale step (default); batched: 64 layers; "
+                         "mixed: 64 FP32-table layers")
     ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
@@ -519,7 +545,7 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batched":
+    elif args.workload in ("batched", "mixed"):
         run_batched(args)
     else:
         run_engine(args)

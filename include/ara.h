@@ -61,7 +61,8 @@ typedef int32_t ara_status;
 
 /* Precision of a layer's per-event table (ara_define_layer). */
 #define ARA_FP64 0        /* FP64 event losses, exact integer trial sums */
-#define ARA_FP32_TABLE 1  /* FP32 event losses, FP64 running sum */
+#define ARA_FP32_TABLE 1  /* ELT terms, combination and occurrence terms in FP32;
+                             trial sums still exact (at least FP64) */
 
 /* Timing channels for ara_kernel_timing. */
 #define ARA_TIMING_YLT 0  /* the per-trial gather/sum kernel */
@@ -152,7 +153,11 @@ ARA_API ara_status ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int64_t *el
  *                        each event's loss combined across the ELTs
  *   agg_ret, agg_lim     FT3: aggregate retention and limit, applied to the
  *                        cumulative sum of occurrence-net losses of a trial
- *   precision            ARA_FP64 or ARA_FP32_TABLE
+ *   precision            ARA_FP64, or ARA_FP32_TABLE: losses and terms are
+ *                        rounded to binary32 and the ELT combination and
+ *                        occurrence terms run in binary32 (Section IV-B,
+ *                        "single precision when possible"); the trial sum
+ *                        and aggregate terms keep full precision
  *   layer_out (out)      the layer handle
  * Retentions must be finite and >= 0, limits >= 0 (+inf allowed).  The
  * per-layer pre-pass (folding the ELT terms and the occurrence terms into

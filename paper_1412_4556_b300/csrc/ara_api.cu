@@ -314,7 +314,7 @@ ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
   ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
   TimedLaunch tl(c, ARA_TIMING_FOLD, s);
   ARA_CUDA(c, launch_fold(L.d_desc, (int)L.elts.size(), c->catalog, L.occ_ret, L.occ_lim, q,
-                          L.d_table, L.d_bitmap, L.bm, nullptr, s),
+                          L.d_table, L.d_bitmap, L.bm, L.precision == ARA_FP32_TABLE, nullptr, s),
            "fold kernel launch");
   tl.done();
   L.folded_version = c->yet_version;
@@ -673,8 +673,8 @@ ara_status ara_define_layer(ara_ctx *c, int32_t n_elts, const int32_t *handles, 
   if (!handles || !layer_out) return fail(c, ARA_E_INVALID_ARG, "NULL argument");
   if (n_elts < 1 || n_elts > kMaxLayerElts)
     return fail(c, ARA_E_INVALID_ARG, "a layer covers 1..%d ELTs (got %d)", kMaxLayerElts, n_elts);
-  if (precision != ARA_FP64)
-    return fail(c, ARA_E_INVALID_ARG, "precision %d is not available; use ARA_FP64", precision);
+  if (precision != ARA_FP64 && precision != ARA_FP32_TABLE)
+    return fail(c, ARA_E_INVALID_ARG, "precision must be ARA_FP64 or ARA_FP32_TABLE (got %d)", precision);
   if (!finite_nonneg(occ_ret) || !finite_nonneg(agg_ret))
     return fail(c, ARA_E_INVALID_ARG, "retentions must be finite and >= 0");
   if (!limit_ok(occ_lim) || !limit_ok(agg_lim))
@@ -766,7 +766,7 @@ ara_status ara_layer_event_table(ara_ctx *c, int32_t layer, double *out) {
     dst = c->d_ylt_stage;
   }
   ARA_CUDA(c, launch_fold(L->d_desc, (int)L->elts.size(), c->catalog, L->occ_ret, L->occ_lim, 0,
-                          nullptr, nullptr, L->bm, dst, s),
+                          nullptr, nullptr, L->bm, L->precision == ARA_FP32_TABLE, dst, s),
            "fold kernel launch");
   if (!dev) {
     ARA_CUDA(c, cudaMemcpyAsync(out, dst, (size_t)c->catalog * sizeof(double), cudaMemcpyDeviceToHost, s),

@@ -220,7 +220,7 @@ __device__ __forceinline__ U128 warp_sum_u128(U128 v) {
 // Each returns cudaSuccess or the launch error.
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
                         double occ_lim, int q, ulonglong2 *table, uint32_t *bitmap,
-                        BitmapLayout bm, double *f64_out, cudaStream_t s);
+                        BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s);
 
 struct YltLaunch {
   int blocks;

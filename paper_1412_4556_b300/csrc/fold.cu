@@ -15,6 +15,12 @@
 // a bucket index, so the CTA finds its slice of every ELT with two loads.
 // Outputs per event: the 128-bit fixed-point table entry used by the YLT
 // kernel, one bit of the zero-skip bitmap, and (optionally) the FP64 value.
+// Reduced-precision layers run the same steps in binary32 (the paper's
+// "single precision when possible", Section IV-B); their values are then
+// binary32 numbers held exactly in the same fixed-point table, and each trial
+// is still summed exactly, so only the per-event values carry FP32 rounding.
+#include <type_traits>
+
 #include "ara_internal.cuh"
 
 namespace ara {
@@ -24,21 +30,32 @@ __device__ __forceinline__ double elt_terms(double loss, double deductible, doub
   return fmin(fmax(__dsub_rn(loss, deductible), 0.0), limit);
 }
 
+// FP32 variant (reduced-precision layers): losses and terms rounded to
+// binary32, the same operations in binary32.
+__device__ __forceinline__ float elt_terms32(double loss, double deductible, double limit) {
+  return fminf(fmaxf(__fsub_rn(__double2float_rn(loss), __double2float_rn(deductible)), 0.f),
+               __double2float_rn(limit));
+}
+
+// FP32 = true: combine and apply occurrence terms in binary32 (the table then
+// holds binary32 values, exactly representable in the fixed-point grid).
+template <bool FP32>
 __global__ void __launch_bounds__(kFoldThreads)
 fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
             double occ_lim, int q, ulonglong2 *__restrict__ table, uint32_t *__restrict__ bitmap,
             uint32_t bm_mul, double *__restrict__ f64_out) {
-  __shared__ double x[kFoldEventsPerCta];
+  using Real = typename std::conditional<FP32, float, double>::type;
+  __shared__ Real x[kFoldEventsPerCta];
   __shared__ int32_t seg[kMaxLayerElts + 1];    // prefix sums of slice lengths
   __shared__ int32_t first[kMaxLayerElts];      // slice start inside ELT j
   __shared__ uint16_t st_off[kFoldStage];
-  __shared__ double st_val[kFoldStage];
+  __shared__ Real st_val[kFoldStage];
 
   const int tid = threadIdx.x;
   const int b = blockIdx.x;
   const int32_t e0 = b * kFoldEventsPerCta;
 
-  for (int i = tid; i < kFoldEventsPerCta; i += kFoldThreads) x[i] = 0.0;
+  for (int i = tid; i < kFoldEventsPerCta; i += kFoldThreads) x[i] = Real(0);
   for (int j = tid; j < n_elts; j += kFoldThreads) {
     const EltDesc d = elts[j];
     int32_t a = d.count, z = d.count;
@@ -68,7 +85,10 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
       const EltDesc &d = elts[lo];
       const int32_t i = first[lo] + (f - seg[lo]);
       st_off[f - base] = (uint16_t)(d.ids[i] - e0);
-      st_val[f - base] = elt_terms(d.losses[i], d.deductible, d.limit);
+      if constexpr (FP32)
+        st_val[f - base] = elt_terms32(d.losses[i], d.deductible, d.limit);
+      else
+        st_val[f - base] = elt_terms(d.losses[i], d.deductible, d.limit);
     }
     __syncthreads();
     // Apply the staged entries ELT by ELT, in layer order.  Within one ELT
@@ -80,7 +100,10 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
       if (lo >= hi) continue;  // uniform across the CTA
       for (int32_t f = lo + tid; f < hi; f += kFoldThreads) {
         const int o = st_off[f - base];
-        x[o] = __dadd_rn(x[o], st_val[f - base]);
+        if constexpr (FP32)
+          x[o] = __fadd_rn(x[o], st_val[f - base]);
+        else
+          x[o] = __dadd_rn(x[o], st_val[f - base]);
       }
       __syncthreads();
     }
@@ -91,7 +114,12 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
     const int32_t e = e0 + i;
     if (e >= catalog) break;
     // FT2 read as occurrence retention then limit: min(max(x - OccR, 0), OccL)
-    const double o = fmin(fmax(__dsub_rn(x[i], occ_ret), 0.0), occ_lim);
+    double o;
+    if constexpr (FP32)
+      o = (double)fminf(fmaxf(__fsub_rn(x[i], __double2float_rn(occ_ret)), 0.f),
+                        __double2float_rn(occ_lim));
+    else
+      o = fmin(fmax(__dsub_rn(x[i], occ_ret), 0.0), occ_lim);
     if (f64_out) f64_out[e] = o;
     if (table) {
       const U128 v = to_fixed(o, q);
@@ -105,11 +133,15 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
 
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
                         double occ_lim, int q, ulonglong2 *table, uint32_t *bitmap,
-                        BitmapLayout bm, double *f64_out, cudaStream_t s) {
+                        BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s) {
   if (catalog <= 0) return cudaSuccess;
   const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
-  fold_kernel<<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q, table,
-                                               bitmap, bm.mul, f64_out);
+  if (fp32)
+    fold_kernel<true><<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
+                                                       table, bitmap, bm.mul, f64_out);
+  else
+    fold_kernel<false><<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
+                                                        table, bitmap, bm.mul, f64_out);
   return cudaGetLastError();
 }
 
