@@ -493,6 +493,128 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+SERVICE = ("ad hoc pricing service: paper-scale YET (catalog 2,000,000 events; 1,000,000 trials x "
+           "Poisson(1000)) and a pool of 256 ELTs (10,000-50,000 events each) resident on the device; "
+           "layer requests of 2-32 pool ELTs with batched-layer terms over a 100k/250k/1M-trial prefix, "
+           "FP32 tables with exact trial sums; PML/TVaR at RP 100/250/500")
+
+
+def run_service(args):
+    """Config-4 serving run: a seeded Poisson stream of layer-pricing requests
+    played open-loop against the pricing service (continuous batching over
+    slots, admission by device memory); reports requests/s and p50/p99
+    latency, then the same requests all at once (saturating) and at a higher
+    rate; 1% of the requests are checked against the oracle on sampled trials."""
+    from paper_1412_4556_b300 import ARA_FP32_TABLE, ARA_FP64, Engine, Service
+    import oracle
+
+    rps = (100.0, 250.0, 500.0)
+    w = S.batched(n_layers=1, n_trials=args.trials)
+    reqs = S.service_requests(n_requests=args.requests, rate_per_s=args.rate)
+    eng = Engine(0)
+    eng.load_yet_from(w.yet)
+    first = eng.load_pool(w.pool)
+    sample = list(range(0, len(reqs), 100))
+
+    def play(rate_scale, want=()):
+        svc = Service(eng, rps, slots=args.slots, max_batch=args.max_batch)
+        for rq in reqs[:max(args.warmup, 3)]:  # warm-up requests, not timed
+            L = rq.layer
+            svc.wait(svc.submit([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim,
+                                rq.n_trials, precision=ARA_FP32_TABLE))
+        tickets = []
+        t0 = time.perf_counter()
+        for i, rq in enumerate(reqs):
+            if rate_scale is not None:
+                delay = t0 + rq.arrival_s / rate_scale - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            L = rq.layer
+            tickets.append(svc.submit([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret,
+                                      L.agg_lim, rq.n_trials, precision=ARA_FP32_TABLE,
+                                      want_ylt=i in want))
+        res = [svc.wait(t) for t in tickets]
+        st = svc.stats()
+        svc.close()
+        bad = [r for r in res if not r.ok]
+        if bad:
+            raise RuntimeError(f"{len(bad)} requests failed: {bad[0].status_name} {bad[0].message}")
+        lat = np.array([r.latency for r in res]) * 1e3
+        span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+        occ = sum(int(w.yet.offsets[rq.n_trials]) for rq in reqs)
+        by_n = {}
+        for n in sorted({rq.n_trials for rq in reqs}):
+            ln = np.array([r.latency for r, rq in zip(res, reqs) if rq.n_trials == n]) * 1e3
+            by_n[str(n)] = {"count": int(ln.size), "p50_ms": float(np.percentile(ln, 50)),
+                            "p99_ms": float(np.percentile(ln, 99))}
+        return res, {
+            "offered_rate_per_s": None if rate_scale is None else args.rate * rate_scale,
+            "latency_by_trials": by_n,
+            "requests_per_s": len(res) / span, "layer_trial_events_per_s": occ / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "mean_batch": float(np.mean([r.batch_size for r in res])),
+            "max_batch": st["max_batch_seen"], "max_in_flight": st["max_in_flight"],
+            "max_slots_busy": st["max_slots_busy"], "max_device_bytes_in_flight": st["max_bytes_in_flight"],
+        }
+
+    with ClockSampler(0) as clocks:
+        clocks.wait_first_sample()
+        t0 = time.monotonic()
+        res, paced = play(1.0, want=set(sample))
+        t1 = time.monotonic()
+        time.sleep(0.3)
+        clocks.mark(t0, t1)
+    _, saturating = play(None)
+    _, fast = play(10.0)
+
+    # 1% of the requests against the FP64 oracle (memoised Algorithm 1) on
+    # sampled trials; PML/TVaR against the FP64 GPU path, which matches the
+    # oracle within 1e-12 per trial in the parity tests.
+    g = np.random.default_rng(7)
+    worst_rel, worst_bound, worst_pml, worst_tvar, oracle_s, oracle_occ = 0.0, 0.0, 0.0, 0.0, 0.0, 0
+    for i in sample:
+        rq, r = reqs[i], res[i]
+        sel = np.sort(g.choice(rq.n_trials, min(rq.n_trials, args.oracle_trials), replace=False))
+        t = time.perf_counter()
+        o, pre = oracle.layer_ylt(w.yet, w.pool, rq.layer, trials=sel, mode="memo")
+        oracle_s += time.perf_counter() - t
+        oracle_occ += int(np.sum(np.diff(w.yet.offsets)[sel]))
+        err = np.abs(r.ylt[sel] - o)
+        worst_rel = max(worst_rel, float(np.max(err / np.maximum(np.maximum(np.abs(o), pre), 1e-300))))
+        worst_bound = max(worst_bound, float(np.max(err / np.maximum(1e-5 * np.maximum(np.abs(o), pre), 1.0))))
+        L = rq.layer
+        h = eng.define_layer([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim,
+                             precision=ARA_FP64)
+        p64, t64 = eng.pml_tvar(eng.layer_ylt(h, rq.n_trials), rps)
+        eng.release_layer(h)
+        worst_pml = max(worst_pml, float(np.max(np.abs(r.pml - p64) / np.maximum(p64, 1.0))))
+        worst_tvar = max(worst_tvar, float(np.max(np.abs(r.tvar - t64) / np.maximum(t64, 1.0))))
+    eng.close()
+    import multiprocessing
+    line = {
+        "metric": METRIC, "value": saturating["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+        "steps": len(reqs), "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / saturating["requests_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 tables, exact trial sums", "data": "synthetic (seeded)",
+        "config": {"workload": SERVICE, "requests": len(reqs), "arrival_rate_per_s": args.rate,
+                   "slots": args.slots, "max_batch": args.max_batch,
+                   "step": "one request: fold + YLT + PML/TVaR, host in and out",
+                   "l2": "inputs larger than L2 (up to 4 GB of YET ids per request)"},
+        "latency_ms": {"p50": paced["p50_ms"], "p99": paced["p99_ms"], "at_rate_per_s": args.rate},
+        "paced": paced, "paced_10x": fast, "saturating": saturating,
+        "accuracy_1pct": {"requests": len(sample), "trials_per_request": args.oracle_trials,
+                          "max_rel_trial_err_vs_oracle": worst_rel,
+                          "max_err_over_bound(1e-5 rel, 1 USD)": worst_bound,
+                          "max_rel_pml_err_vs_fp64": worst_pml, "max_rel_tvar_err_vs_fp64": worst_tvar},
+        "cpu_baseline": {"value": oracle_occ / oracle_s, "unit": "layer-trial-events/s",
+                         "cores": multiprocessing.cpu_count(), "kind": "oracle",
+                         "sample": f"memoised oracle on {args.oracle_trials} sampled trials of each of "
+                                   f"{len(sample)} requests"},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ oracle arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -533,9 +655,14 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
-    ap.add_argument("--workload", choices=["paper", "batched", "mixed"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "batched", "mixed", "service"], default="paper",
                     help="paper: the single-layer paper-scale step (default); batched: 64 layers; "
-                         "mixed: 64 FP32-table layers")
+                         "mixed: 64 FP32-table layers; service: the pricing-request stream")
+    ap.add_argument("--requests", type=int, default=2000, help="service: requests in the stream")
+    ap.add_argument("--rate", type=float, default=50.0, help="service: Poisson arrival rate per s")
+    ap.add_argument("--slots", type=int, default=4, help="service: batches in flight")
+    ap.add_argument("--max-batch", type=int, default=16, help="service: requests per batch")
+    ap.add_argument("--oracle-trials", type=int, default=2000, help="service: trials checked per sample")
     ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
@@ -547,6 +674,8 @@ def main():
         run_reference(args)
     elif args.workload in ("batched", "mixed"):
         run_batched(args)
+    elif args.workload == "service":
+        run_service(args)
     else:
         run_engine(args)
 

@@ -58,6 +58,7 @@ typedef int32_t ara_status;
 #define ARA_E_TIMEOUT (-6)     /* a bounded wait ran out */
 #define ARA_E_NOT_FOUND (-7)   /* unknown ELT or layer handle */
 #define ARA_E_STATE (-8)       /* call order: e.g. no YET loaded yet */
+#define ARA_E_CANCELLED (-9)   /* a service request cancelled before it started */
 
 /* Precision of a layer's per-event table (ara_define_layer). */
 #define ARA_FP64 0        /* FP64 event losses, exact integer trial sums */
@@ -76,13 +77,15 @@ typedef int32_t ara_status;
  * cannot be used (for instance when no GPU is present). */
 ARA_API ara_status ara_create(ara_ctx **out, int device);
 
-/* Free every device and host resource of the context.  NULL is a no-op. */
+/* Free every device and host resource of the context (an attached pricing
+ * service is destroyed first).  NULL is a no-op. */
 ARA_API void ara_destroy(ara_ctx *ctx);
 
 /* Message of the last failed call on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx.  ctx == NULL gives the message of the
  * last failed call that takes no context (ara_create,
- * ara_pml_tvar_noalloc) on the calling thread. */
+ * ara_pml_tvar_noalloc, the ara_service_* calls) on the calling thread, as
+ * does a ctx that a pricing service owns. */
 ARA_API const char *ara_last_error(const ara_ctx *ctx);
 
 /* Static name of a status code ("ARA_OK", "ARA_E_INVALID_ARG", ...). */
@@ -248,6 +251,112 @@ ARA_API ara_status ara_pml_tvar_batch(ara_ctx *ctx, const double *ylt, int32_t n
 ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const double *return_periods,
                                         int32_t n_rp, double *pml_out, double *tvar_out,
                                         void *cuda_stream);
+
+/* ---------------------------------------------------------- pricing service */
+/*
+ * Ad hoc pricing (Section I: an underwriter quotes a contract while on the
+ * phone, so a layer must be priced in real time).  Each request is one Layer
+ * (Section III) over ELTs already loaded into the context, priced by
+ * Algorithm 1 over a prefix of the loaded YET, with PML and TVaR at the
+ * service's return periods.  The YET and the ELT pool stay on the device.
+ *
+ * A scheduler thread owned by the service admits queued requests in arrival
+ * order while a slot is free and the in-flight requests' device memory stays
+ * within the budget, and batches the requests that share the oldest queued
+ * request's trial count (up to max_batch) into one slot: their layers are
+ * folded, priced two per pass over the YET, and their PML/TVaR computed in
+ * one batched selection, all on the slot's own stream, so batches of
+ * different slots overlap on the device.  Requests that arrive meanwhile are
+ * queued and join the next batch that a free slot takes (continuous
+ * batching).  A request's results do not depend on the other requests of its
+ * batch: they are identical to pricing it alone.
+ *
+ * While a service is attached, the context is used by the scheduler thread
+ * alone: every other call on the context returns ARA_E_STATE (ara_destroy
+ * destroys the service first).  The service calls may be made from any
+ * thread; their error messages are read with ara_last_error(NULL) on the
+ * calling thread.  Requests use the ELTs and the YET loaded before
+ * ara_service_create.
+ */
+typedef struct ara_service ara_service;
+
+typedef struct {
+  int32_t slots;             /* batches in flight at once, 1..16; each has a stream */
+  int32_t max_batch;         /* requests per batch, 1..64 */
+  int64_t memory_budget;     /* device bytes that in-flight requests may hold
+                                (layer tables, YLTs, selection state); 0 = a
+                                quarter of the free device memory at creation */
+  int32_t n_return_periods;  /* 1..16 */
+  double return_periods[16]; /* each >= 1 */
+  int32_t fail_every;        /* fault injection for tests: when > 0, every
+                                fail_every-th admitted request ends with
+                                ARA_E_NOMEM as if its allocation had failed,
+                                and the rest of its batch proceeds; 0 = off */
+} ara_service_config;
+
+typedef struct {
+  int32_t n_elts;              /* 1..1024 */
+  const int32_t *elt_handles;  /* host; copied at submit; order = summation order */
+  double occ_ret, occ_lim, agg_ret, agg_lim;  /* as ara_define_layer */
+  int32_t precision;           /* ARA_FP64 or ARA_FP32_TABLE */
+  int64_t n_trials;            /* trials 0..n_trials-1 of the loaded YET; floor(n_trials / RP) >= 1 */
+  double deadline_s;           /* > 0: a request not started this many seconds
+                                  after submit ends with ARA_E_TIMEOUT; 0 = none */
+  double *ylt_out;             /* optional host double[n_trials] that receives
+                                  the YLT; must stay valid until the request
+                                  ends (ara_service_wait returns it or
+                                  ara_service_destroy runs); NULL = not wanted */
+} ara_request;
+
+typedef struct {
+  ara_status status;     /* ARA_OK, or why the request failed */
+  int32_t batch_size;    /* requests priced in its batch */
+  int32_t slot;          /* slot that priced it (-1 if it never started) */
+  int32_t n_return_periods;
+  double pml[16], tvar[16];
+  double t_submit, t_start, t_done;  /* seconds since the service started */
+  char message[160];     /* failure message, empty on success */
+} ara_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, cancelled, timed_out, batches;
+  int64_t queued, in_flight;         /* now */
+  int64_t max_in_flight;             /* most requests in flight at once */
+  int64_t max_batch_seen;            /* largest batch formed */
+  int64_t bytes_in_flight, max_bytes_in_flight, memory_budget;
+  int64_t max_slots_busy;            /* most slots busy at once */
+} ara_service_stats;
+
+/* Attach a service to ctx (a YET must be loaded: ARA_E_STATE otherwise) and
+ * start its scheduler thread.  Waits for the context's queued work first.
+ * Errors: ARA_E_INVALID_ARG (config), ARA_E_STATE (no YET, or a service is
+ * already attached), ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_service_create(ara_ctx *ctx, const ara_service_config *config,
+                                      ara_service **out);
+
+/* Queue one request; *ticket identifies it (> 0).  The request is checked
+ * here: ARA_E_INVALID_ARG (terms, sizes, a return period above n_trials),
+ * ARA_E_NOT_FOUND (ELT handle), ARA_E_NOMEM (its device footprint exceeds
+ * the whole budget), ARA_E_STATE (service shutting down). */
+ARA_API ara_status ara_service_submit(ara_service *svc, const ara_request *request, int64_t *ticket);
+
+/* Wait up to timeout_s seconds (>= 0) for a request to end.  ARA_OK: *out
+ * holds its result (out->status says whether it succeeded) and the ticket is
+ * retired.  ARA_E_TIMEOUT: still queued or running (the wait changed
+ * nothing).  ARA_E_NOT_FOUND: unknown or retired ticket. */
+ARA_API ara_status ara_service_wait(ara_service *svc, int64_t ticket, double timeout_s, ara_result *out);
+
+/* Cancel a queued request: it ends with ARA_E_CANCELLED.  ARA_E_STATE if it
+ * already started or ended; ARA_E_NOT_FOUND for an unknown ticket. */
+ARA_API ara_status ara_service_cancel(ara_service *svc, int64_t ticket);
+
+/* Counters since creation (host copy). */
+ARA_API ara_status ara_service_get_stats(ara_service *svc, ara_service_stats *out);
+
+/* Stop the scheduler: queued requests end with ARA_E_CANCELLED, batches on
+ * the device are waited for, the service's buffers are freed and the
+ * context is detached (usable again).  Results not collected are dropped. */
+ARA_API void ara_service_destroy(ara_service *svc);
 
 /* ------------------------------------------------------------- measurement */
 

@@ -22,8 +22,8 @@ from . import _native
 from ._native import (ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_FOLD, ARA_TIMING_PML, ARA_TIMING_YLT,
                       AraError)
 
-__all__ = ["Engine", "AraError", "ARA_FP64", "ARA_FP32_TABLE", "ARA_TIMING_YLT",
-           "ARA_TIMING_FOLD", "ARA_TIMING_PML"]
+__all__ = ["Engine", "Service", "ServiceResult", "AraError", "ARA_FP64", "ARA_FP32_TABLE",
+           "ARA_TIMING_YLT", "ARA_TIMING_FOLD", "ARA_TIMING_PML"]
 
 
 def _is_tensor(a) -> bool:
@@ -53,6 +53,7 @@ class Engine:
     def __init__(self, device: int = 0, stream=None):
         self.ctx = _native.ara_create(device)
         self.device = device
+        self._service = None
         self.catalog_size = 0
         self.n_trials = 0
         if stream is not None:
@@ -60,6 +61,8 @@ class Engine:
 
     # -------------------------------------------------------------- lifetime
     def close(self) -> None:
+        if self._service is not None:
+            self._service.close()
         if self.ctx:
             _native.ara_destroy(self.ctx)
             self.ctx = 0
@@ -186,3 +189,97 @@ class Engine:
     def kernel_timing(self, channel: int = ARA_TIMING_YLT):
         """(launches, total milliseconds) recorded on a timing channel."""
         return _native.ara_kernel_timing(self.ctx, channel)
+
+
+class ServiceResult:
+    """Outcome of one pricing request (see ara_result)."""
+
+    def __init__(self, r: "_native.Result", ylt):
+        self.status = r.status
+        self.status_name = _native.STATUS_NAMES.get(r.status, str(r.status))
+        self.message = r.message.decode(errors="replace")
+        self.batch_size = r.batch_size
+        self.slot = r.slot
+        n = r.n_return_periods
+        self.pml = np.array(r.pml[:n])
+        self.tvar = np.array(r.tvar[:n])
+        self.t_submit, self.t_start, self.t_done = r.t_submit, r.t_start, r.t_done
+        self.ylt = ylt
+
+    @property
+    def ok(self) -> bool:
+        return self.status == _native.ARA_OK
+
+    @property
+    def latency(self) -> float:
+        """Seconds from submit to the end of the request."""
+        return self.t_done - self.t_submit
+
+
+class Service:
+    """Ad hoc pricing service on an :class:`Engine` (see ``ara_service_create``).
+
+    While it runs, the engine's context belongs to the service's scheduler
+    thread; other engine calls raise ``AraError(ARA_E_STATE)``.
+    """
+
+    def __init__(self, engine: Engine, return_periods: Sequence[float] = (100.0, 250.0, 500.0),
+                 slots: int = 4, max_batch: int = 16, memory_budget: int = 0, fail_every: int = 0):
+        if engine._service is not None:
+            raise AraError(-8, "the engine already has a service")
+        cfg = _native.ServiceConfig()
+        cfg.slots, cfg.max_batch, cfg.memory_budget = int(slots), int(max_batch), int(memory_budget)
+        rps = list(return_periods)
+        if not 1 <= len(rps) <= 16:
+            raise ValueError("1..16 return periods")
+        cfg.n_return_periods = len(rps)
+        for i, r in enumerate(rps):
+            cfg.return_periods[i] = float(r)
+        cfg.fail_every = int(fail_every)
+        self.engine = engine
+        self.return_periods = np.array(rps, dtype=np.float64)
+        self.svc = _native.ara_service_create(engine.ctx, cfg)
+        engine._service = self
+        self._ylt = {}  # ticket -> host YLT buffer kept alive until the request is collected
+
+    def submit(self, elt_handles: Sequence[int], occ_ret: float, occ_lim: float, agg_ret: float,
+               agg_lim: float, n_trials: int, precision: int = ARA_FP64, deadline_s: float = 0.0,
+               want_ylt: bool = False) -> int:
+        h = np.ascontiguousarray(elt_handles, dtype=np.int32)
+        rq = _native.Request()
+        rq.n_elts = int(h.shape[0])
+        rq.elt_handles = h.ctypes.data
+        rq.occ_ret, rq.occ_lim, rq.agg_ret, rq.agg_lim = map(float, (occ_ret, occ_lim, agg_ret, agg_lim))
+        rq.precision = int(precision)
+        rq.n_trials = int(n_trials)
+        rq.deadline_s = float(deadline_s)
+        ylt = np.empty(int(n_trials), dtype=np.float64) if want_ylt else None
+        rq.ylt_out = ylt.ctypes.data if ylt is not None else None
+        ticket = _native.ara_service_submit(self.svc, rq)
+        if ylt is not None:
+            self._ylt[ticket] = ylt
+        return ticket
+
+    def wait(self, ticket: int, timeout: float = 600.0) -> ServiceResult:
+        r = _native.ara_service_wait(self.svc, ticket, timeout)
+        return ServiceResult(r, self._ylt.pop(ticket, None))
+
+    def cancel(self, ticket: int) -> None:
+        _native.ara_service_cancel(self.svc, ticket)
+
+    def stats(self) -> dict:
+        s = _native.ara_service_get_stats(self.svc)
+        return {name: getattr(s, name) for name, _ in s._fields_}
+
+    def close(self) -> None:
+        if self.svc:
+            _native.ara_service_destroy(self.svc)
+            self.svc = 0
+            self.engine._service = None
+            self._ylt.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -24,8 +24,39 @@ ARA_TIMING_PML = 2
 STATUS_NAMES = {
     0: "ARA_OK", -1: "ARA_E_INVALID_ARG", -2: "ARA_E_EVENT_RANGE", -3: "ARA_E_DUP_EVENT",
     -4: "ARA_E_NOMEM", -5: "ARA_E_CUDA", -6: "ARA_E_TIMEOUT", -7: "ARA_E_NOT_FOUND",
-    -8: "ARA_E_STATE",
+    -8: "ARA_E_STATE", -9: "ARA_E_CANCELLED",
 }
+
+
+class ServiceConfig(C.Structure):
+    """ara_service_config."""
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("memory_budget", C.c_int64),
+                ("n_return_periods", C.c_int32), ("return_periods", C.c_double * 16),
+                ("fail_every", C.c_int32)]
+
+
+class Request(C.Structure):
+    """ara_request."""
+    _fields_ = [("n_elts", C.c_int32), ("elt_handles", C.c_void_p), ("occ_ret", C.c_double),
+                ("occ_lim", C.c_double), ("agg_ret", C.c_double), ("agg_lim", C.c_double),
+                ("precision", C.c_int32), ("n_trials", C.c_int64), ("deadline_s", C.c_double),
+                ("ylt_out", C.c_void_p)]
+
+
+class Result(C.Structure):
+    """ara_result."""
+    _fields_ = [("status", C.c_int32), ("batch_size", C.c_int32), ("slot", C.c_int32),
+                ("n_return_periods", C.c_int32), ("pml", C.c_double * 16), ("tvar", C.c_double * 16),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("message", C.c_char * 160)]
+
+
+class ServiceStats(C.Structure):
+    """ara_service_stats."""
+    _fields_ = [(n, C.c_int64) for n in (
+        "submitted", "completed", "failed", "cancelled", "timed_out", "batches", "queued", "in_flight",
+        "max_in_flight", "max_batch_seen", "bytes_in_flight", "max_bytes_in_flight", "memory_budget",
+        "max_slots_busy")]
 
 # C prototypes: name -> (restype, argtypes)
 _vp, _i32, _i64, _f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
@@ -47,6 +78,12 @@ PROTOTYPES = {
     "ara_pml_tvar_batch": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp]),
     "ara_set_kernel_timing": (_i32, [_vp, _i32]),
     "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
+    "ara_service_create": (_i32, [_vp, C.POINTER(ServiceConfig), C.POINTER(C.c_void_p)]),
+    "ara_service_submit": (_i32, [_vp, C.POINTER(Request), C.POINTER(_i64)]),
+    "ara_service_wait": (_i32, [_vp, _i64, _f64, C.POINTER(Result)]),
+    "ara_service_cancel": (_i32, [_vp, _i64]),
+    "ara_service_get_stats": (_i32, [_vp, C.POINTER(ServiceStats)]),
+    "ara_service_destroy": (None, [_vp]),
 }
 
 
@@ -168,3 +205,36 @@ def ara_kernel_timing(ctx: int, channel: int):
     n, ms = _i64(0), _f64(0.0)
     _check(ctx, lib.ara_kernel_timing(ctx, int(channel), C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def ara_service_create(ctx: int, config: ServiceConfig) -> int:
+    out = C.c_void_p()
+    _check(None, lib.ara_service_create(ctx, C.byref(config), C.byref(out)))
+    return out.value
+
+
+def ara_service_submit(svc: int, request: Request) -> int:
+    ticket = _i64(0)
+    _check(None, lib.ara_service_submit(svc, C.byref(request), C.byref(ticket)))
+    return ticket.value
+
+
+def ara_service_wait(svc: int, ticket: int, timeout_s: float) -> Result:
+    """The request's result; AraError(ARA_E_TIMEOUT) if it has not ended in time."""
+    out = Result()
+    _check(None, lib.ara_service_wait(svc, int(ticket), float(timeout_s), C.byref(out)))
+    return out
+
+
+def ara_service_cancel(svc: int, ticket: int) -> None:
+    _check(None, lib.ara_service_cancel(svc, int(ticket)))
+
+
+def ara_service_get_stats(svc: int) -> ServiceStats:
+    out = ServiceStats()
+    _check(None, lib.ara_service_get_stats(svc, C.byref(out)))
+    return out
+
+
+def ara_service_destroy(svc: int) -> None:
+    lib.ara_service_destroy(svc)

@@ -23,119 +23,13 @@
 #include <vector>
 
 #include "ara.h"
+#include "ara_ctx.h"
 #include "ara_internal.cuh"
 
 using namespace ara;
 
-namespace {
 
-struct EltMeta {
-  int32_t count = 0;
-  double deductible = 0.0;
-  double limit = 0.0;
-  double max_loss = 0.0;
-  int32_t max_id = -1;
-  const int32_t *d_ids = nullptr;
-  const double *d_losses = nullptr;
-  const int32_t *d_bucket = nullptr;
-  int32_t nb = 0;
-};
-
-struct LayerRec {
-  bool live = false;
-  std::vector<int32_t> elts;
-  double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
-  int32_t precision = ARA_FP64;
-  EltDesc *d_desc = nullptr;
-  int32_t desc_cap = 0;
-  ulonglong2 *d_table = nullptr;
-  uint32_t *d_bitmap = nullptr;
-  int32_t table_catalog = 0;
-  BitmapLayout bm{0u, 0};
-  int q = 0;
-  AggFixed agg_fx{{0ull, 0ull}, {0ull, 0ull}, 0};
-  int64_t folded_version = -1;
-  double upper = 0.0;  // upper bound of any per-event table value
-};
-
-// Device buffers of a released layer, kept for the next layer (defining and
-// releasing layers then needs no cudaMalloc/cudaFree, which would stall the
-// device).  Reuse is ordered by the context's stream.
-struct LayerBuffers {
-  EltDesc *d_desc = nullptr;
-  int32_t desc_cap = 0;
-  ulonglong2 *d_table = nullptr;
-  uint32_t *d_bitmap = nullptr;
-  int32_t table_catalog = 0;
-  BitmapLayout bm{0u, 0};
-};
-
-constexpr size_t kLayerPoolMax = 64;
-
-struct TimingChannel {
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
-  int64_t launches = 0;
-  double total_ms = 0.0;
-};
-
-}  // namespace
-
-struct ara_ctx {
-  int device = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  // YET
-  int64_t yet_version = 0;
-  bool yet_loaded = false;
-  int32_t catalog = 0;
-  int64_t n_trials = 0;
-  int64_t n_occ = 0;
-  int64_t max_trial_len = 0;
-  std::vector<int64_t> h_offsets;   // raw CSR offsets
-  std::vector<int64_t> h_coff;      // chunk offsets
-  int64_t *d_offsets = nullptr;     // raw offsets
-  size_t cap_offsets = 0;
-  int64_t *d_coff = nullptr;        // chunk offsets
-  size_t cap_coff = 0;
-  int4 *d_chunks = nullptr;         // id chunks + sentinel tail
-  size_t cap_chunks = 0;
-  bool packed = false;              // 6 ids of 21 bits per chunk
-  int32_t *d_raw = nullptr;         // staging for ids copied from the host
-  size_t cap_raw = 0;
-  float *d_ts = nullptr;
-  size_t cap_ts = 0;
-  bool has_ts = false;
-  // ELT pool
-  std::vector<EltMeta> elts;
-  std::vector<void *> elt_blocks;
-  // layers
-  std::vector<LayerRec> layers;
-  std::vector<LayerBuffers> pool;
-  // scratch
-  double *d_ylt_stage = nullptr;
-  size_t cap_ylt_stage = 0;
-  double *d_sel_in = nullptr;
-  size_t cap_sel_in = 0;
-  void *d_sel_ws = nullptr;
-  double *d_sel_out = nullptr;
-  unsigned char *d_sel_ws_batch = nullptr;  // per-layer selection states
-  size_t cap_sel_ws_batch = 0;
-  double *d_sel_out_batch = nullptr;
-  size_t cap_sel_out_batch = 0;
-  ulonglong2 *d_pair_table = nullptr;       // two layers' tables interleaved
-  size_t cap_pair_table = 0;
-  uint32_t *d_pair_bitmap = nullptr;        // union of their bitmaps
-  size_t cap_pair_bitmap = 0;
-  int tuned_unroll[3] = {0, 0, 0};          // YLT unroll picked by the autotuner, per G
-  unsigned long long *d_counter = nullptr;  // validation counters
-  unsigned int *d_err = nullptr;            // PML/TVaR input check flag
-  // timing
-  bool timing = false;
-  TimingChannel chan[3];
-};
-
-namespace {
+namespace ara {
 
 thread_local std::string g_create_error;
 
@@ -155,10 +49,15 @@ ara_status cuda_fail(ara_ctx *c, cudaError_t e, const char *what) {
   return fail(c, st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-#define ARA_CUDA(ctx, expr, what)                   \
-  do {                                              \
-    cudaError_t _e = (expr);                        \
-    if (_e != cudaSuccess) return cuda_fail((ctx), _e, (what)); \
+// Common entry of the ABI calls on a context: a context attached to a pricing
+// service is used by the service's thread alone, so other calls are refused
+// without touching its state (the message goes to ara_last_error(NULL)).
+#define ARA_ENTER(c)                                                                     \
+  do {                                                                                   \
+    if (!(c)) return ARA_E_INVALID_ARG;                                                  \
+    if ((c)->service)                                                                    \
+      return ara::fail_free(ARA_E_STATE, "the context is attached to a pricing service"); \
+    (c)->err.clear();                                                                    \
   } while (0)
 
 bool is_device_ptr(const void *p) {
@@ -169,17 +68,6 @@ bool is_device_ptr(const void *p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-template <typename T>
-cudaError_t ensure(T **buf, size_t *cap, size_t count) {
-  if (*cap >= count && *buf) return cudaSuccess;
-  if (*buf) cudaFree(*buf);
-  *buf = nullptr;
-  *cap = 0;
-  cudaError_t e = cudaMalloc((void **)buf, std::max<size_t>(count, 1) * sizeof(T));
-  if (e == cudaSuccess) *cap = std::max<size_t>(count, 1);
-  return e;
 }
 
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
@@ -345,7 +233,7 @@ void recycle_layer(ara_ctx *c, LayerRec &L) {
   B.table_catalog = L.table_catalog;
   B.bm = L.bm;
   L = LayerRec();
-  if (c->pool.size() < kLayerPoolMax) {
+  if (c->pool.size() < c->pool_max) {
     c->pool.push_back(B);
   } else {
     cudaStreamSynchronize(c->stream);
@@ -371,6 +259,30 @@ bool take_pooled(ara_ctx *c, int32_t n_elts, LayerRec &L) {
   return false;
 }
 
+ara_status reserve_layers(ara_ctx *c, size_t count, cudaStream_t s) {
+  size_t fitting = 0;
+  for (const LayerBuffers &B : c->pool)
+    if (B.table_catalog == c->catalog && B.d_table) ++fitting;
+  while (fitting < count && c->pool.size() < c->pool_max) {
+    LayerBuffers B;
+    B.bm = plan_bitmap(c->catalog + 1, ylt_smem_budget(c->device));
+    B.desc_cap = 64;
+    cudaError_t e = cudaMalloc(&B.d_desc, (size_t)B.desc_cap * sizeof(EltDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&B.d_table, ((size_t)c->catalog + 1) * sizeof(ulonglong2));
+    if (e == cudaSuccess) e = cudaMalloc(&B.d_bitmap, (size_t)B.bm.words * 4);
+    // the sentinel entry (id = catalog) stays zero for the buffers' lifetime
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.d_table + c->catalog, 0, sizeof(ulonglong2), s);
+    if (e != cudaSuccess) {
+      free_buffers(B);
+      return cuda_fail(c, e, "reserve layer buffers");
+    }
+    B.table_catalog = c->catalog;
+    c->pool.push_back(B);
+    ++fitting;
+  }
+  return ARA_OK;
+}
+
 ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out) {
   if (layer < 0 || layer >= (int32_t)c->layers.size() || !c->layers[layer].live)
     return fail(c, ARA_E_NOT_FOUND, "unknown layer handle %d", layer);
@@ -378,7 +290,155 @@ ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out) {
   return ARA_OK;
 }
 
-}  // namespace
+
+ara_status fail_free(ara_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_create_error = buf;
+  return st;
+}
+
+ara_status check_layer_args(const ara_ctx *c, int32_t n_elts, const int32_t *handles, double occ_ret,
+                            double occ_lim, double agg_ret, double agg_lim, int32_t precision) {
+  if (!handles) return fail_free(ARA_E_INVALID_ARG, "elt_handles is NULL");
+  if (n_elts < 1 || n_elts > kMaxLayerElts)
+    return fail_free(ARA_E_INVALID_ARG, "a layer covers 1..%d ELTs (got %d)", kMaxLayerElts, n_elts);
+  if (precision != ARA_FP64 && precision != ARA_FP32_TABLE)
+    return fail_free(ARA_E_INVALID_ARG, "precision must be ARA_FP64 or ARA_FP32_TABLE (got %d)", precision);
+  if (!finite_nonneg(occ_ret) || !finite_nonneg(agg_ret))
+    return fail_free(ARA_E_INVALID_ARG, "retentions must be finite and >= 0");
+  if (!limit_ok(occ_lim) || !limit_ok(agg_lim))
+    return fail_free(ARA_E_INVALID_ARG, "limits must be >= 0 (inf allowed)");
+  std::vector<int32_t> sorted(handles, handles + n_elts);
+  std::sort(sorted.begin(), sorted.end());
+  for (size_t i = 0; i < sorted.size(); ++i) {
+    if (sorted[i] < 0 || sorted[i] >= (int32_t)c->elts.size())
+      return fail_free(ARA_E_NOT_FOUND, "unknown ELT handle %d", sorted[i]);
+    if (i && sorted[i] == sorted[i - 1])
+      return fail_free(ARA_E_INVALID_ARG, "ELT handle %d appears twice in the layer", sorted[i]);
+  }
+  return ARA_OK;
+}
+
+ara_status tail_counts(int64_t n, const double *rps, int32_t n_rp, int64_t *k) {
+  if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps)
+    return fail_free(ARA_E_INVALID_ARG, "need 1..%d return periods", kMaxReturnPeriods);
+  for (int32_t r = 0; r < n_rp; ++r) {
+    if (!(rps[r] >= 1.0)) return fail_free(ARA_E_INVALID_ARG, "return period %d must be >= 1", r);
+    const double kk = std::floor((double)n / rps[r]);
+    if (kk < 1.0)
+      return fail_free(ARA_E_INVALID_ARG, "return period %g exceeds the %lld trials", rps[r], (long long)n);
+    k[r] = (int64_t)kk;
+  }
+  return ARA_OK;
+}
+
+size_t layer_bitmap_bytes(const ara_ctx *c) {
+  return (size_t)plan_bitmap(c->catalog + 1, ylt_smem_budget(c->device)).words * 4;
+}
+
+ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, double occ_ret,
+                           double occ_lim, double agg_ret, double agg_lim, int32_t precision,
+                           cudaStream_t s, int32_t *layer_out) {
+  std::vector<int32_t> el(handles, handles + n_elts);
+  LayerRec L;
+  L.live = true;
+  L.elts = el;
+  L.occ_ret = occ_ret;
+  L.occ_lim = occ_lim;
+  L.agg_ret = agg_ret;
+  L.agg_lim = agg_lim;
+  L.precision = precision;
+  // Upper bound of any per-event value: FT1 <= min(loss, limit), summed over
+  // the ELTs, capped by the occurrence limit.
+  double up = 0.0;
+  std::vector<EltDesc> desc((size_t)n_elts);
+  for (int32_t j = 0; j < n_elts; ++j) {
+    const EltMeta &m = c->elts[(size_t)el[(size_t)j]];
+    up += std::min(m.max_loss, m.limit);
+    desc[(size_t)j] = EltDesc{m.d_ids, m.d_losses, m.d_bucket, m.nb, m.count, m.deductible, m.limit};
+  }
+  L.upper = std::min(up * (1.0 + 1e-12), occ_lim);
+  if (!take_pooled(c, n_elts, L)) {
+    L.desc_cap = std::max<int32_t>(n_elts, 64);
+    ARA_CUDA(c, cudaMalloc(&L.d_desc, (size_t)L.desc_cap * sizeof(EltDesc)), "cudaMalloc(layer ELT list)");
+  }
+  // A copy from pageable memory returns once the data is staged, so `desc`
+  // may go out of scope; the stream orders it after earlier users of d_desc.
+  cudaError_t e = cudaMemcpyAsync(L.d_desc, desc.data(), desc.size() * sizeof(EltDesc),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    free_layer(L);
+    return cuda_fail(c, e, "upload layer ELT list");
+  }
+  ara_status st = fold_layer(c, L, s);
+  if (st != ARA_OK) {
+    free_layer(L);
+    return st;
+  }
+  int32_t id = -1;
+  for (size_t i = 0; i < c->layers.size(); ++i)
+    if (!c->layers[i].live) {
+      id = (int32_t)i;
+      break;
+    }
+  if (id < 0) {
+    id = (int32_t)c->layers.size();
+    c->layers.emplace_back();
+  }
+  c->layers[(size_t)id] = L;
+  *layer_out = id;
+  return ARA_OK;
+}
+
+ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, int64_t n_trials,
+                         double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap) {
+  std::vector<LayerRec *> Ls((size_t)n_layers);
+  for (int32_t i = 0; i < n_layers; ++i) {
+    ara_status st = get_layer(c, layers[i], &Ls[(size_t)i]);
+    if (st) return st;
+  }
+  for (LayerRec *L : Ls)
+    if (L->folded_version != c->yet_version) {
+      ara_status st = fold_layer(c, *L, s);
+      if (st) return st;
+    }
+  const BitmapLayout bm = Ls[0]->bm;  // every layer of a catalog shares the layout
+  const size_t entries = (size_t)c->catalog + 1;
+  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
+  for (int32_t i = 0; i < n_layers; i += 2) {
+    const int G = (i + 1 < n_layers) ? 2 : 1;
+    LayerOut outs[2];
+    for (int g = 0; g < G; ++g) {
+      const LayerRec *L = Ls[(size_t)(i + g)];
+      outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst + (size_t)(i + g) * (size_t)n_trials};
+    }
+    const ulonglong2 *table = Ls[(size_t)i]->d_table;
+    const uint32_t *bitmap = Ls[(size_t)i]->d_bitmap;
+    if (G == 2) {
+      ARA_CUDA(c, launch_interleave(Ls[(size_t)i]->d_table, Ls[(size_t)i + 1]->d_table, (int64_t)entries,
+                                    pair_table, Ls[(size_t)i]->d_bitmap, Ls[(size_t)i + 1]->d_bitmap,
+                                    bm.words, pair_bitmap, s),
+               "interleave layer tables");
+      table = pair_table;
+      bitmap = pair_bitmap;
+    }
+    YltLaunch cfg;
+    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, G, c->tuned_unroll[G], &cfg),
+             "plan YLT launch");
+    TimedLaunch tl(c, ARA_TIMING_YLT, s);
+    ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, bitmap, bm,
+                                 c->catalog, G, outs, cfg, s),
+             "YLT kernel launch");
+    tl.done();
+  }
+  return ARA_OK;
+}
+
+}  // namespace ara
 
 void ara::set_context_free_error(const char *msg) { g_create_error = msg ? msg : ""; }
 
@@ -396,6 +456,7 @@ const char *ara_status_string(ara_status s) {
     case ARA_E_TIMEOUT: return "ARA_E_TIMEOUT";
     case ARA_E_NOT_FOUND: return "ARA_E_NOT_FOUND";
     case ARA_E_STATE: return "ARA_E_STATE";
+    case ARA_E_CANCELLED: return "ARA_E_CANCELLED";
     default: return "ARA_E_UNKNOWN";
   }
 }
@@ -443,6 +504,7 @@ ara_status ara_create(ara_ctx **out, int device) {
 
 void ara_destroy(ara_ctx *c) {
   if (!c) return;
+  if (c->service) ara_service_destroy(c->service);
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &L : c->layers) free_layer(L);
@@ -474,19 +536,19 @@ void ara_destroy(ara_ctx *c) {
 }
 
 const char *ara_last_error(const ara_ctx *c) {
-  return c ? c->err.c_str() : g_create_error.c_str();
+  // An attached service's thread owns c->err; refusals go to the thread's slot.
+  return c && !c->service ? c->err.c_str() : g_create_error.c_str();
 }
 
 ara_status ara_set_stream(ara_ctx *c, void *stream) {
-  if (!c) return ARA_E_INVALID_ARG;
+  ARA_ENTER(c);
   c->stream = stream ? (cudaStream_t)stream : c->own_stream;
   return ARA_OK;
 }
 
 ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int64_t *offsets,
                         const int32_t *ids, const float *ts) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   if (catalog < 1) return fail(c, ARA_E_INVALID_ARG, "catalog_size must be >= 1 (got %d)", catalog);
   if (n_trials < 0 || n_trials > (int64_t)1 << 40)
@@ -572,8 +634,7 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
 ara_status ara_load_elts(ara_ctx *c, int32_t n_elts, const int64_t *off, const int32_t *ids,
                          const double *losses, const double *ded, const double *lim,
                          int32_t *first_handle) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "load the YET before ELTs (ids are checked against its catalog)");
   if (n_elts < 1) return fail(c, ARA_E_INVALID_ARG, "n_elts must be >= 1");
   if (!off || !ded || !lim || !first_handle) return fail(c, ARA_E_INVALID_ARG, "NULL argument");
@@ -666,83 +727,18 @@ ara_status ara_load_elts(ara_ctx *c, int32_t n_elts, const int64_t *off, const i
 ara_status ara_define_layer(ara_ctx *c, int32_t n_elts, const int32_t *handles, double occ_ret,
                             double occ_lim, double agg_ret, double agg_lim, int32_t precision,
                             int32_t *layer_out) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
-  if (!handles || !layer_out) return fail(c, ARA_E_INVALID_ARG, "NULL argument");
-  if (n_elts < 1 || n_elts > kMaxLayerElts)
-    return fail(c, ARA_E_INVALID_ARG, "a layer covers 1..%d ELTs (got %d)", kMaxLayerElts, n_elts);
-  if (precision != ARA_FP64 && precision != ARA_FP32_TABLE)
-    return fail(c, ARA_E_INVALID_ARG, "precision must be ARA_FP64 or ARA_FP32_TABLE (got %d)", precision);
-  if (!finite_nonneg(occ_ret) || !finite_nonneg(agg_ret))
-    return fail(c, ARA_E_INVALID_ARG, "retentions must be finite and >= 0");
-  if (!limit_ok(occ_lim) || !limit_ok(agg_lim))
-    return fail(c, ARA_E_INVALID_ARG, "limits must be >= 0 (inf allowed)");
-  std::vector<int32_t> el(handles, handles + n_elts);
-  {
-    std::vector<int32_t> sorted = el;
-    std::sort(sorted.begin(), sorted.end());
-    for (size_t i = 0; i < sorted.size(); ++i) {
-      if (sorted[i] < 0 || sorted[i] >= (int32_t)c->elts.size())
-        return fail(c, ARA_E_NOT_FOUND, "unknown ELT handle %d", sorted[i]);
-      if (i && sorted[i] == sorted[i - 1])
-        return fail(c, ARA_E_INVALID_ARG, "ELT handle %d appears twice in the layer", sorted[i]);
-    }
-  }
-  LayerRec L;
-  L.live = true;
-  L.elts = el;
-  L.occ_ret = occ_ret;
-  L.occ_lim = occ_lim;
-  L.agg_ret = agg_ret;
-  L.agg_lim = agg_lim;
-  L.precision = precision;
-  // Upper bound of any per-event value: FT1 <= min(loss, limit), summed over
-  // the ELTs, capped by the occurrence limit.
-  double up = 0.0;
-  std::vector<EltDesc> desc((size_t)n_elts);
-  for (int32_t j = 0; j < n_elts; ++j) {
-    const EltMeta &m = c->elts[(size_t)el[(size_t)j]];
-    up += std::min(m.max_loss, m.limit);
-    desc[(size_t)j] = EltDesc{m.d_ids, m.d_losses, m.d_bucket, m.nb, m.count, m.deductible, m.limit};
-  }
-  L.upper = std::min(up * (1.0 + 1e-12), occ_lim);
-  if (!take_pooled(c, n_elts, L)) {
-    L.desc_cap = std::max<int32_t>(n_elts, 64);
-    ARA_CUDA(c, cudaMalloc(&L.d_desc, (size_t)L.desc_cap * sizeof(EltDesc)), "cudaMalloc(layer ELT list)");
-  }
-  // A copy from pageable memory returns once the data is staged, so `desc`
-  // may go out of scope; the stream orders it after earlier users of d_desc.
-  cudaError_t e = cudaMemcpyAsync(L.d_desc, desc.data(), desc.size() * sizeof(EltDesc),
-                                  cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) {
-    free_layer(L);
-    return cuda_fail(c, e, "upload layer ELT list");
-  }
-  ara_status st = fold_layer(c, L, c->stream);
-  if (st != ARA_OK) {
-    free_layer(L);
-    return st;
-  }
-  int32_t id = -1;
-  for (size_t i = 0; i < c->layers.size(); ++i)
-    if (!c->layers[i].live) {
-      id = (int32_t)i;
-      break;
-    }
-  if (id < 0) {
-    id = (int32_t)c->layers.size();
-    c->layers.emplace_back();
-  }
-  c->layers[(size_t)id] = L;
-  *layer_out = id;
-  return ARA_OK;
+  if (!layer_out) return fail(c, ARA_E_INVALID_ARG, "NULL argument");
+  ara_status st = check_layer_args(c, n_elts, handles, occ_ret, occ_lim, agg_ret, agg_lim, precision);
+  if (st) return fail(c, st, "%s", ara_last_error(nullptr));
+  return define_layer_on(c, n_elts, handles, occ_ret, occ_lim, agg_ret, agg_lim, precision, c->stream,
+                         layer_out);
 }
 
 ara_status ara_release_layer(ara_ctx *c, int32_t layer) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   LayerRec *L = nullptr;
   ara_status st = get_layer(c, layer, &L);
   if (st) return st;
@@ -751,8 +747,7 @@ ara_status ara_release_layer(ara_ctx *c, int32_t layer) {
 }
 
 ara_status ara_layer_event_table(ara_ctx *c, int32_t layer, double *out) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   LayerRec *L = nullptr;
   ara_status st = get_layer(c, layer, &L);
@@ -778,8 +773,7 @@ ara_status ara_layer_event_table(ara_ctx *c, int32_t layer, double *out) {
 
 ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *ylt_out,
                          void *cuda_stream) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
   LayerRec *L = nullptr;
@@ -821,8 +815,7 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
 
 ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *rps, int32_t n_rp,
                         double *pml_out, double *tvar_out) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
   if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps || !pml_out || !tvar_out)
@@ -863,8 +856,7 @@ ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *
 
 ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, int64_t n_trials,
                           double *ylt_out, void *cuda_stream) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
   if (n_layers < 1 || !layers) return fail(c, ARA_E_INVALID_ARG, "need n_layers >= 1 layer handles");
@@ -872,18 +864,13 @@ ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, i
     return fail(c, ARA_E_INVALID_ARG, "n_trials %lld outside [0, %lld]", (long long)n_trials,
                 (long long)c->n_trials);
   if (n_trials > 0 && !ylt_out) return fail(c, ARA_E_INVALID_ARG, "ylt_out is NULL");
-  std::vector<LayerRec *> Ls((size_t)n_layers);
+  LayerRec *first = nullptr;
   for (int32_t i = 0; i < n_layers; ++i) {
-    ara_status st = get_layer(c, layers[i], &Ls[(size_t)i]);
+    ara_status st = get_layer(c, layers[i], &first);
     if (st) return st;
   }
   if (n_trials == 0) return ARA_OK;
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
-  for (LayerRec *L : Ls)
-    if (L->folded_version != c->yet_version) {
-      ara_status st = fold_layer(c, *L, s);
-      if (st) return st;
-    }
   const bool dev = is_device_ptr(ylt_out);
   double *dst = ylt_out;
   const size_t total = (size_t)n_layers * (size_t)n_trials;
@@ -891,39 +878,14 @@ ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, i
     ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, total), "stage buffer");
     dst = c->d_ylt_stage;
   }
-  const BitmapLayout bm = Ls[0]->bm;  // every layer of a catalog shares the layout
-  const size_t entries = (size_t)c->catalog + 1;
   if (n_layers > 1) {
+    const size_t entries = (size_t)c->catalog + 1;
+    const BitmapLayout bm = plan_bitmap(c->catalog + 1, ylt_smem_budget(c->device));
     ARA_CUDA(c, ensure(&c->d_pair_table, &c->cap_pair_table, 2 * entries), "pair table");
     ARA_CUDA(c, ensure(&c->d_pair_bitmap, &c->cap_pair_bitmap, (size_t)bm.words), "pair bitmap");
   }
-  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
-  for (int32_t i = 0; i < n_layers; i += 2) {
-    const int G = (i + 1 < n_layers) ? 2 : 1;
-    LayerOut outs[2];
-    for (int g = 0; g < G; ++g) {
-      const LayerRec *L = Ls[(size_t)(i + g)];
-      outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst + (size_t)(i + g) * (size_t)n_trials};
-    }
-    const ulonglong2 *table = Ls[(size_t)i]->d_table;
-    const uint32_t *bitmap = Ls[(size_t)i]->d_bitmap;
-    if (G == 2) {
-      ARA_CUDA(c, launch_interleave(Ls[(size_t)i]->d_table, Ls[(size_t)i + 1]->d_table, (int64_t)entries,
-                                    c->d_pair_table, Ls[(size_t)i]->d_bitmap, Ls[(size_t)i + 1]->d_bitmap,
-                                    bm.words, c->d_pair_bitmap, s),
-               "interleave layer tables");
-      table = c->d_pair_table;
-      bitmap = c->d_pair_bitmap;
-    }
-    YltLaunch cfg;
-    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, G, c->tuned_unroll[G], &cfg),
-             "plan YLT launch");
-    TimedLaunch tl(c, ARA_TIMING_YLT, s);
-    ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, bitmap, bm,
-                                 c->catalog, G, outs, cfg, s),
-             "YLT kernel launch");
-    tl.done();
-  }
+  ara_status st = layers_ylt_on(c, layers, n_layers, n_trials, dst, s, c->d_pair_table, c->d_pair_bitmap);
+  if (st) return st;
   if (!dev) {
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, dst, total * sizeof(double), cudaMemcpyDeviceToHost, s), "copy YLTs");
     ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -933,8 +895,7 @@ ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, i
 
 ara_status ara_pml_tvar_batch(ara_ctx *c, const double *ylt, int32_t n_layers, int64_t n,
                               const double *rps, int32_t n_rp, double *pml_out, double *tvar_out) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   if (n < 1 || !ylt || n_layers < 1) return fail(c, ARA_E_INVALID_ARG, "need n_layers >= 1 and n >= 1 trial losses");
   if (n_layers > 65535) return fail(c, ARA_E_INVALID_ARG, "at most 65535 layers per call");
@@ -984,8 +945,7 @@ ara_status ara_pml_tvar_batch(ara_ctx *c, const double *ylt, int32_t n_layers, i
 }
 
 ara_status ara_set_kernel_timing(ara_ctx *c, int32_t enable) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   for (auto &ch : c->chan) {
     for (auto &ev : ch.events) {
       cudaEventSynchronize(ev.second);
@@ -1001,8 +961,7 @@ ara_status ara_set_kernel_timing(ara_ctx *c, int32_t enable) {
 }
 
 ara_status ara_kernel_timing(ara_ctx *c, int32_t channel, int64_t *launches, double *total_ms) {
-  if (!c) return ARA_E_INVALID_ARG;
-  c->err.clear();
+  ARA_ENTER(c);
   if (channel < 0 || channel > 2 || !launches || !total_ms)
     return fail(c, ARA_E_INVALID_ARG, "bad timing channel or NULL output");
   TimingChannel &ch = c->chan[channel];
