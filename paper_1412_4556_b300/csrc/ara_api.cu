@@ -342,7 +342,7 @@ size_t layer_bitmap_bytes(const ara_ctx *c) {
 
 ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, double occ_ret,
                            double occ_lim, double agg_ret, double agg_lim, int32_t precision,
-                           cudaStream_t s, int32_t *layer_out) {
+                           cudaStream_t s, int32_t *layer_out, EltDesc *stage) {
   std::vector<int32_t> el(handles, handles + n_elts);
   LayerRec L;
   L.live = true;
@@ -368,7 +368,8 @@ ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, d
   }
   // A copy from pageable memory returns once the data is staged, so `desc`
   // may go out of scope; the stream orders it after earlier users of d_desc.
-  cudaError_t e = cudaMemcpyAsync(L.d_desc, desc.data(), desc.size() * sizeof(EltDesc),
+  if (stage) std::copy(desc.begin(), desc.end(), stage);
+  cudaError_t e = cudaMemcpyAsync(L.d_desc, stage ? stage : desc.data(), desc.size() * sizeof(EltDesc),
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     free_layer(L);
@@ -427,7 +428,7 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
       bitmap = pair_bitmap;
     }
     YltLaunch cfg;
-    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, G, c->tuned_unroll[G], &cfg),
+    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, G, c->tuned[G], &cfg),
              "plan YLT launch");
     TimedLaunch tl(c, ARA_TIMING_YLT, s);
     ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, bitmap, bm,
@@ -797,7 +798,7 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
   }
   const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, 1, c->tuned_unroll[1], &cfg),
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, 1, c->tuned[1], &cfg),
            "plan YLT launch");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst};
   TimedLaunch tl(c, ARA_TIMING_YLT, s);

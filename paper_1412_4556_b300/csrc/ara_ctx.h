@@ -116,7 +116,7 @@ struct ara_ctx {
   size_t cap_pair_table = 0;
   uint32_t *d_pair_bitmap = nullptr;        // union of their bitmaps
   size_t cap_pair_bitmap = 0;
-  int tuned_unroll[3] = {0, 0, 0};          // YLT unroll picked by the autotuner, per G
+  ara::YltShape tuned[3];                   // YLT launch shape picked by the autotuner, per G
   unsigned long long *d_counter = nullptr;  // validation counters
   unsigned int *d_err = nullptr;            // PML/TVaR input check flag
   // timing
@@ -175,9 +175,12 @@ ara_status tail_counts(int64_t n, const double *rps, int32_t n_rp, int64_t *k);
 size_t layer_bitmap_bytes(const ara_ctx *c);
 
 // ara_define_layer after check_layer_args, its device work queued on stream s.
+// stage: NULL, or pinned host memory for n_elts ELT descriptors that stays
+// untouched until the stream has run the upload (the copy is then fully
+// asynchronous; from pageable memory the driver may wait on the stream).
 ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, double occ_ret,
                            double occ_lim, double agg_ret, double agg_lim, int32_t precision,
-                           cudaStream_t s, int32_t *layer_out);
+                           cudaStream_t s, int32_t *layer_out, EltDesc *stage = nullptr);
 
 // The kernels of ara_layers_ylt on stream s: device output dst (layer-major),
 // pair_table / pair_bitmap scratch of 2 * (catalog + 1) entries and of the

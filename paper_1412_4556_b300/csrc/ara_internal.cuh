@@ -226,7 +226,14 @@ struct YltLaunch {
   int blocks;
   int threads;
   size_t smem;
-  int unroll;
+  int unroll;           // 16-byte id loads in flight per lane
+  int lanes_per_trial;  // 8, 16 or 32: a warp sums 32 / lanes_per_trial trials at once
+};
+
+// Launch-shape choice for the YLT kernel (0 = the planner's default).
+struct YltShape {
+  int unroll = 0;
+  int lanes_per_trial = 0;
 };
 
 // Per-layer constants and output of one YLT kernel launch.
@@ -249,9 +256,10 @@ cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packe
                              cudaStream_t s);
 
 // Pick the launch shape of the YLT kernel for a bitmap of bm.words words and
-// trials of mean_chunks 16-byte chunks (unroll_hint 1/2/4 forces the unroll).
+// trials of mean_chunks 16-byte chunks; non-zero fields of hint force the
+// unroll (1/2/4) or the lanes per trial (8/16/32).
 cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int G,
-                     int unroll_hint, YltLaunch *out);
+                     YltShape hint, YltLaunch *out);
 
 cudaError_t launch_interleave(const ulonglong2 *ta, const ulonglong2 *tb, int64_t entries,
                               ulonglong2 *out, const uint32_t *ba, const uint32_t *bb,

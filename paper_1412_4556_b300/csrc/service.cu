@@ -83,14 +83,17 @@ struct Slot {
   double *h_ylt = nullptr;  // pinned
   size_t cap_h_ylt = 0;
   unsigned int *h_err = nullptr;  // pinned
+  EltDesc *h_desc = nullptr;      // pinned ELT lists of the batch's layers
+  size_t cap_h_desc = 0;
 };
 
-cudaError_t ensure_pinned(double **buf, size_t *cap, size_t count) {
+template <typename T>
+cudaError_t ensure_pinned(T **buf, size_t *cap, size_t count) {
   if (*cap >= count && *buf) return cudaSuccess;
   if (*buf) cudaFreeHost(*buf);
   *buf = nullptr;
   *cap = 0;
-  cudaError_t e = cudaMallocHost((void **)buf, std::max<size_t>(count, 1) * sizeof(double));
+  cudaError_t e = cudaMallocHost((void **)buf, std::max<size_t>(count, 1) * sizeof(T));
   if (e == cudaSuccess) *cap = std::max<size_t>(count, 1);
   return e;
 }
@@ -109,6 +112,7 @@ void free_slot(Slot &sl) {
   cudaFreeHost(sl.h_out);
   cudaFreeHost(sl.h_ylt);
   cudaFreeHost(sl.h_err);
+  cudaFreeHost(sl.h_desc);
   sl = Slot();
 }
 
@@ -231,6 +235,11 @@ void ara_service::launch(Slot &slot, std::vector<Req *> &batch) {
   slot.launch_message.clear();
   slot.n = batch.front()->n_trials;
   std::vector<std::pair<Req *, std::pair<ara_status, std::string>>> failed;
+  size_t n_desc = 0;
+  for (Req *r : batch) n_desc += r->elts.size();
+  // A failed allocation leaves h_desc NULL: the uploads then go from pageable memory.
+  if (ensure_pinned(&slot.h_desc, &slot.cap_h_desc, n_desc) != cudaSuccess) cudaGetLastError();
+  size_t desc_off = 0;
   for (Req *r : batch) {
     bool inject = false;
     {
@@ -243,8 +252,10 @@ void ara_service::launch(Slot &slot, std::vector<Req *> &batch) {
       continue;
     }
     c->err.clear();
+    EltDesc *stage = slot.h_desc ? slot.h_desc + desc_off : nullptr;
+    desc_off += r->elts.size();
     const ara_status st = define_layer_on(c, (int32_t)r->elts.size(), r->elts.data(), r->occ_ret, r->occ_lim,
-                                          r->agg_ret, r->agg_lim, r->precision, slot.s, &r->layer);
+                                          r->agg_ret, r->agg_lim, r->precision, slot.s, &r->layer, stage);
     if (st) {
       failed.push_back({r, {st, c->err}});
       continue;

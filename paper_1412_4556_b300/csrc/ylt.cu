@@ -60,19 +60,6 @@ __device__ __forceinline__ ulonglong2 ld_entry(const ulonglong2 *p, unsigned lon
   return v;
 }
 
-// Table entry of `id` if `hit`, else zero: a predicated 16-byte gather, so
-// occurrences whose bitmap bit is clear cost no memory request.
-__device__ __forceinline__ ulonglong2 gather_if(const ulonglong2 *p, uint32_t hit,
-                                                unsigned long long pol) {
-  ulonglong2 v = make_ulonglong2(0ull, 0ull);
-  asm("{\n\t.reg .pred p;\n\t"
-      "setp.ne.u32 p, %2, 0;\n\t"
-      "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
-      : "+l"(v.x), "+l"(v.y)
-      : "r"(hit), "l"(p), "l"(pol));
-  return v;
-}
-
 // One bulk copy-engine request pulls a whole trial's ids (a contiguous,
 // 16-byte aligned run) into L2, so the warp's own loads of that trial hit L2.
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
@@ -99,13 +86,26 @@ __device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]
   }
 }
 
-// Table entries of `id` for G layers (16 bytes each, interleaved) if `hit`,
-// else zeros; G = 2 is one 32-byte load, i.e. one L2 sector for two layers.
+// Adds the table entries of `id` for G layers (16 bytes each, interleaved)
+// to the accumulators when `hit` is set: a predicated gather (G = 2 is one
+// 32-byte load, i.e. one L2 sector for two layers) and predicated
+// add/add-with-carry, so occurrences whose bitmap bit is clear cost neither a
+// memory request nor register moves.
+#ifndef ARA_GATHER_VARIANT
+#define ARA_GATHER_VARIANT 0
+#endif
 template <int G>
-__device__ __forceinline__ void gather_group(const ulonglong2 *table, uint32_t id, uint32_t hit,
-                                             unsigned long long pol, ulonglong2 (&x)[G]) {
+__device__ __forceinline__ void gather_add(U128 (&acc)[G], const ulonglong2 *table, uint32_t id,
+                                           uint32_t hit, unsigned long long pol) {
+#if ARA_GATHER_VARIANT == 0
   if constexpr (G == 1) {
-    x[0] = gather_if(table + id, hit, pol);
+    unsigned long long a = 0ull, b = 0ull;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
+        : "+l"(a), "+l"(b)
+        : "r"(hit), "l"(table + id), "l"(pol));
+    add128(acc[0], a, b);
   } else {
     unsigned long long a = 0ull, b = 0ull, c = 0ull, d = 0ull;
     asm("{\n\t.reg .pred p;\n\t"
@@ -113,9 +113,51 @@ __device__ __forceinline__ void gather_group(const ulonglong2 *table, uint32_t i
         "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%5], %6;\n\t}"
         : "+l"(a), "+l"(b), "+l"(c), "+l"(d)
         : "r"(hit), "l"(table + 2 * (size_t)id), "l"(pol));
-    x[0] = make_ulonglong2(a, b);
-    x[1] = make_ulonglong2(c, d);
+    add128(acc[0], a, b);
+    add128(acc[1], c, d);
   }
+#else
+  if constexpr (G == 1) {
+    unsigned long long a, b;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
+        : "=l"(a), "=l"(b)
+        : "r"(hit), "l"(table + id), "l"(pol));
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "@p add.cc.u64 %0, %0, %2;\n\t"
+        "@p addc.u64 %1, %1, %3;\n\t}"
+        : "+l"(acc[0].lo), "+l"(acc[0].hi)
+        : "l"(a), "l"(b), "r"(hit));
+  } else {
+    unsigned long long a, b, c, d;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%5], %6;\n\t}"
+        : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+        : "r"(hit), "l"(table + 2 * (size_t)id), "l"(pol));
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %8, 0;\n\t"
+        "@p add.cc.u64 %0, %0, %4;\n\t"
+        "@p addc.u64 %1, %1, %5;\n\t"
+        "@p add.cc.u64 %2, %2, %6;\n\t"
+        "@p addc.u64 %3, %3, %7;\n\t}"
+        : "+l"(acc[0].lo), "+l"(acc[0].hi), "+l"(acc[1].lo), "+l"(acc[1].hi)
+        : "l"(a), "l"(b), "l"(c), "l"(d), "r"(hit));
+  }
+#endif
+}
+
+// Sum over the LPT consecutive lanes of a group (LPT a power of two <= 32).
+template <int LPT>
+__device__ __forceinline__ U128 group_sum_u128(U128 v) {
+#pragma unroll
+  for (int m = LPT / 2; m > 0; m >>= 1) {
+    U128 o = shfl_xor_u128(v, m);
+    add128(v, o.lo, o.hi);
+  }
+  return v;
 }
 
 template <int G>
@@ -125,13 +167,16 @@ struct GroupOut {
 
 // G layers share one pass over the YET: one zero-skip bitmap (the union of
 // the layers' bitmaps), one gather per occurrence that any layer needs, and
-// one 128-bit accumulator per layer.
-template <int U, bool PACKED, int G>
+// one 128-bit accumulator per layer.  A warp sums 32 / LPT consecutive trials
+// side by side, LPT lanes per trial: fewer lanes idle in the last step of a
+// trial, and one group reduction and one epilogue serve 32 / LPT trials.
+template <int U, bool PACKED, int G, int LPT>
 __global__ void __launch_bounds__(kYltThreads, 1)
 ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
                 int64_t n_trials, const ulonglong2 *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
                 int4 sent4, GroupOut<G> out) {
+  constexpr int TPW = 32 / LPT;  // trials per warp step
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
   __syncthreads();
@@ -140,40 +185,69 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
   const unsigned long long pol_ids = policy_evict_first();
   const unsigned long long pol_tab = policy_evict_last();
   const int lane = threadIdx.x & 31;
+  const int grp = lane / LPT;
+  const int gl = lane % LPT;
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t t_begin = n_trials * w / n_warps;
   const int64_t t_end = n_trials * (w + 1) / n_warps;
 
-  int64_t p_next = t_begin < t_end ? coff[t_begin] : 0;
-  if (lane == 0 && t_begin < t_end) {
-    const int64_t b = coff[t_begin + 1];
-    if (b > p_next) prefetch_l2(chunks + p_next, (uint32_t)((b - p_next) * 16));
+  // Offsets of the next warp step's trials and the L2 prefetch range of the
+  // step after it are loaded one step ahead, so no step waits on them.
+  int64_t pa = 0, pe = 0;  // chunk range of this lane's trial in the next step
+  if (t_begin + grp < t_end) {
+    pa = coff[t_begin + grp];
+    pe = coff[t_begin + grp + 1];
   }
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    const int64_t p0 = p_next;
-    p_next = coff[t + 1];
-    // While this trial is summed, its successor's ids travel to L2.
-    if (lane == 0 && t + 1 < t_end) {
-      const int64_t b = coff[t + 2];
-      if (b > p_next) prefetch_l2(chunks + p_next, (uint32_t)((b - p_next) * 16));
+  int64_t fa = 0, fb = 0;  // lane 0: chunk range prefetched at the top of the next step
+  if (lane == 0 && t_begin < t_end) {
+    const int64_t a = coff[t_begin], b = coff[min(t_begin + TPW, t_end)];
+    if (b > a) prefetch_l2(chunks + a, (uint32_t)((b - a) * 16));
+    fa = b;
+    fb = coff[min(t_begin + 2 * TPW, t_end)];
+  }
+  for (int64_t t0 = t_begin; t0 < t_end; t0 += TPW) {
+    const int64_t t = t0 + grp;
+    const bool valid = t < t_end;
+    const int64_t p0 = pa;
+    const int nk = (int)(pe - pa);  // 16-byte chunks of trial t (0 if not valid)
+    pa = pe = 0;
+    if (t + TPW < t_end) {
+      pa = coff[t + TPW];
+      pe = coff[t + TPW + 1];
     }
+    // While these trials are summed, the next ones' ids travel to L2.
+    if (lane == 0) {
+      if (fb > fa) prefetch_l2(chunks + fa, (uint32_t)((fb - fa) * 16));
+      fa = fb;
+      fb = coff[min(t0 + 3 * TPW, t_end)];
+    }
+    int nk_max = nk;
+    if constexpr (TPW > 1) nk_max = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)nk);
     const int4 *tp = chunks + p0;
-    const int nk = (int)(p_next - p0);  // 16-byte chunks of this trial
     U128 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = U128{0ull, 0ull};
-    for (int base = 0; base < nk; base += 32 * U) {
-      int4 v[U];
+    // Software-pipelined: the ids of step base + LPT*U are in flight while
+    // the current step's bitmap tests and gathers run.
+    int4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = sent4;
+      const int j = LPT * u + gl;
+      if (j < nk) v[u] = ld_ids(tp + j, pol_ids);
+    }
+    for (int base = 0; base < nk_max; base += LPT * U) {
+      int4 vn[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        v[u] = sent4;
-        const int j = base + 32 * u + lane;
-        if (base + 32 * u < nk && j < nk) v[u] = ld_ids(tp + j, pol_ids);
+        vn[u] = sent4;
+        const int j = base + LPT * (U + u) + gl;
+        if (j < nk) vn[u] = ld_ids(tp + j, pol_ids);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (base + 32 * u >= nk) break;  // warp-uniform: the rest of this step is empty
+        if (base + LPT * u >= nk_max) break;  // warp-uniform: the rest of this step is empty
         uint32_t idv[PACKED ? 6 : 4];
         chunk_ids<PACKED>(v[u], idv);
 #pragma unroll
@@ -181,28 +255,28 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
           const uint32_t id = idv[i];
           const uint32_t word = s_bm[bitmap_word(id, bm_mul)];
           const uint32_t hit = __funnelshift_r(word, word, id) & 1u;  // bit id & 31
-          ulonglong2 x[G];
-          gather_group<G>(table, id, hit, pol_tab, x);
-#pragma unroll
-          for (int g = 0; g < G; ++g) add128(acc[g], x[g].x, x[g].y);
+          gather_add<G>(acc, table, id, hit, pol_tab);
         }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = vn[u];
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      const U128 sum = warp_sum_u128(acc[g]);
+      const U128 sum = group_sum_u128<LPT>(acc[g]);
       const LayerOut &L = out.l[g];
-      if (lane == 0) L.ylt[t] = trial_loss(sum, L.q, L.af, L.agg_ret, L.agg_lim);
+      const double y = trial_loss(sum, L.q, L.af, L.agg_ret, L.agg_lim);
+      if (gl == 0 && valid) L.ylt[t] = y;
     }
   }
 }
 
-template <int U, bool PACKED, int G>
+template <int U, bool PACKED, int G, int LPT>
 static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials,
                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
                             int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
                             cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED, G>,
+  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED, G, LPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.smem);
   if (err != cudaSuccess) return err;
@@ -210,10 +284,22 @@ static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_t
   const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
   GroupOut<G> go;
   for (int g = 0; g < G; ++g) go.l[g] = outs[g];
-  ylt_fp64_kernel<U, PACKED, G><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
+  ylt_fp64_kernel<U, PACKED, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
       coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul,
       sent4, go);
   return cudaGetLastError();
+}
+
+template <int U, bool PACKED, int G>
+static cudaError_t launch_l(const int64_t *coff, const int4 *chunks, int64_t n_trials,
+                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                            int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
+                            cudaStream_t s) {
+  switch (cfg.lanes_per_trial) {
+    case 8: return launch_u<U, PACKED, G, 8>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    case 16: return launch_u<U, PACKED, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    default: return launch_u<U, PACKED, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+  }
 }
 
 template <bool PACKED, int G>
@@ -222,9 +308,9 @@ static cudaError_t launch_pg(const int64_t *coff, const int4 *chunks, int64_t n_
                              int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
                              cudaStream_t s) {
   switch (cfg.unroll) {
-    case 1: return launch_u<1, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    case 2: return launch_u<2, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    default: return launch_u<4, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    case 1: return launch_l<1, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    case 2: return launch_l<2, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    default: return launch_l<4, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
   }
 }
 
@@ -240,33 +326,53 @@ cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packe
                 : launch_pg<false, 1>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
 }
 
+template <bool PACKED, int G, int LPT>
+static const void *kernel_ptr_l(int unroll) {
+  return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, G, LPT>
+       : unroll == 2 ? (const void *)ylt_fp64_kernel<2, PACKED, G, LPT>
+                     : (const void *)ylt_fp64_kernel<4, PACKED, G, LPT>;
+}
+
 template <bool PACKED, int G>
-static const void *kernel_ptr(int unroll) {
-  return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, G>
-       : unroll == 2 ? (const void *)ylt_fp64_kernel<2, PACKED, G>
-                     : (const void *)ylt_fp64_kernel<4, PACKED, G>;
+static const void *kernel_ptr(int unroll, int lpt) {
+  return lpt == 8 ? kernel_ptr_l<PACKED, G, 8>(unroll)
+       : lpt == 16 ? kernel_ptr_l<PACKED, G, 16>(unroll)
+                   : kernel_ptr_l<PACKED, G, 32>(unroll);
 }
 
 cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int G,
-                     int unroll_hint, YltLaunch *out) {
+                     YltShape hint, YltLaunch *out) {
   int sms = 0;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
-  // Chunks per lane of a typical trial.  Measured on B300 with ~8 chunks per
-  // lane (1000-event trials): U = 2 beats 4 and 8 (fewer wasted slots in the
-  // last step of a trial, more warps' worth of registers free).
-  const double per_lane = mean_chunks / 32.0;
-  int unroll = per_lane > 1.5 ? 2 : 1;
-  if (unroll_hint == 1 || unroll_hint == 2 || unroll_hint == 4) unroll = unroll_hint;
+  // Lanes per trial: a group of LPT lanes wastes on average LPT/2 chunk
+  // slots in the last step of each trial, and one group reduction plus one
+  // epilogue per warp step serve 32 / LPT trials; too few lanes per trial
+  // leave too few id loads in flight for short trials.
+  // Measured on B300 with 167-chunk trials (Poisson(1000) events, 6 ids a
+  // chunk): 16 lanes per trial beat 32 by 8% and 8 by 23%.
+  int lpt = mean_chunks >= 24.0 ? 16 : 32;
+  // Unroll: U chunk loads per lane per step; the loop already keeps the
+  // next step's loads in flight, and U = 1 measured as fast as U = 2 with 16
+  // lanes per trial (1.06 ms against 1.09 ms for 1e9 occurrences).
+  int unroll = 1;
+  if (hint.unroll == 1 || hint.unroll == 2 || hint.unroll == 4) unroll = hint.unroll;
+  if (hint.lanes_per_trial == 8 || hint.lanes_per_trial == 16 || hint.lanes_per_trial == 32)
+    lpt = hint.lanes_per_trial;
   if (const char *env = std::getenv("ARA_YLT_UNROLL")) {
     int u = std::atoi(env);
     if (u == 1 || u == 2 || u == 4) unroll = u;
   }
+  if (const char *env = std::getenv("ARA_YLT_LPT")) {
+    int l = std::atoi(env);
+    if (l == 8 || l == 16 || l == 32) lpt = l;
+  }
   out->threads = kYltThreads;
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
-  const void *fn = G == 2 ? (packed ? kernel_ptr<true, 2>(unroll) : kernel_ptr<false, 2>(unroll))
-                          : (packed ? kernel_ptr<true, 1>(unroll) : kernel_ptr<false, 1>(unroll));
+  out->lanes_per_trial = lpt;
+  const void *fn = G == 2 ? (packed ? kernel_ptr<true, 2>(unroll, lpt) : kernel_ptr<false, 2>(unroll, lpt))
+                          : (packed ? kernel_ptr<true, 1>(unroll, lpt) : kernel_ptr<false, 1>(unroll, lpt));
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
