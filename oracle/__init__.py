@@ -55,6 +55,9 @@ def load(path: Optional[str] = None):
     lib.ara_oracle_layer_ylt.argtypes = [i32, i64, p, p, i32, p, p, p, p, p, f64, f64, f64, f64,
                                          i32, i32, p, i64, p, p]
     lib.ara_oracle_layer_ylt.restype = C.c_int
+    lib.ara_oracle_layer_yelt.argtypes = [i32, i64, p, p, i32, p, p, p, p, p, f64, f64, f64, f64,
+                                          i32, i32, p, i64, p, p, p, p, p]
+    lib.ara_oracle_layer_yelt.restype = C.c_int
     lib.ara_oracle_trial_trace.argtypes = [i32, i64, p, i32, p, p, p, p, p, f64, f64, f64, f64,
                                            p, p, p, p, p]
     lib.ara_oracle_trial_trace.restype = C.c_int
@@ -119,6 +122,37 @@ def layer_ylt(yet, pool, layer, trials: Optional[np.ndarray] = None, mode: str =
                                   _ptr(sel), int(n), _ptr(ylt), _ptr(pre))
     _check(rc, "ara_oracle_layer_ylt")
     return ylt, pre
+
+
+def layer_yelt(yet, pool, layer, trials: Optional[np.ndarray] = None, mode: str = "memo",
+               threads: Optional[int] = None, lib=None):
+    """Year Event Loss Table of one layer (reading R11).
+
+    Returns (inc, out_off, occ_max, ylt, presum): the per-occurrence
+    increments of the selected trials concatenated in list order (trial i at
+    inc[out_off[i]:out_off[i+1]]), each trial's largest increment, its trial
+    loss and its pre-aggregate sum.
+    """
+    lib = lib or load()
+    off = _c(yet.offsets, np.int64)
+    ids = _c(yet.ids, np.int32)
+    e_off, e_ids, e_loss, ded, lim = _layer_elts(pool, layer.elts)
+    sel = None if trials is None else _c(trials, np.int64)
+    lens = np.diff(off) if sel is None else (off[sel + 1] - off[sel])
+    n = lens.shape[0]
+    out_off = np.zeros(n + 1, dtype=np.int64)
+    out_off[1:] = np.cumsum(lens)
+    inc = np.zeros(int(out_off[-1]), dtype=np.float64)
+    occ_max, ylt, pre = (np.zeros(n, dtype=np.float64) for _ in range(3))
+    rc = lib.ara_oracle_layer_yelt(int(yet.catalog_size), int(yet.n_trials), _ptr(off), _ptr(ids),
+                                   len(layer.elts), _ptr(e_off), _ptr(e_ids), _ptr(e_loss),
+                                   _ptr(ded), _ptr(lim), float(layer.occ_ret), float(layer.occ_lim),
+                                   float(layer.agg_ret), float(layer.agg_lim),
+                                   1 if mode == "memo" else 0, int(threads or os.cpu_count() or 1),
+                                   _ptr(sel), int(n), _ptr(out_off), _ptr(inc), _ptr(occ_max),
+                                   _ptr(ylt), _ptr(pre))
+    _check(rc, "ara_oracle_layer_yelt")
+    return inc, out_off, occ_max, ylt, pre
 
 
 def trial_trace(catalog_size: int, ids: np.ndarray, pool, layer, lib=None):

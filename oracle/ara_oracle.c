@@ -35,6 +35,12 @@
  *       descending and k = floor(N / RP) >= 1; the sum runs in descending
  *       order in FP64.
  *   R6  ELTs are summed in layer order, events in stored order.
+ *   R11 The Year Event Loss Table (YELT) holds, for every occurrence, the
+ *       increment of the aggregate-clamped running loss (inc_k = a_k -
+ *       a_{k-1}); a trial's occurrence loss for the occurrence exceedance
+ *       (OEP) report is its largest increment (0 for an empty trial), and a
+ *       Return Period Loss (Sec. III, reports) is the PML-style k-th largest
+ *       value of the YLT (aggregate, AEP) or of those maxima (OEP).
  *
  * All arithmetic is IEEE binary64 with round-to-nearest; the hot path has no
  * multiplications, and the file is built with -ffp-contract=off.
@@ -253,6 +259,85 @@ int ara_oracle_layer_ylt(int32_t catalog, int64_t n_trials, const int64_t *offse
     for (int32_t i = started; i < n_threads; ++i) run_job(&jobs[i]);
     for (int32_t i = 0; i < started; ++i) pthread_join(th[i], NULL);
   }
+  free_layer(&L);
+  return ORACLE_OK;
+}
+
+typedef struct {
+  const layer_t *L;
+  const int64_t *offsets;
+  const int32_t *ids;
+  const int64_t *sel;
+  const int64_t *out_off;
+  int64_t first, last;
+  double *inc, *occ_max, *ylt, *presum;
+} yelt_job_t;
+
+static void *run_yelt_job(void *arg) {
+  yelt_job_t *J = (yelt_job_t *)arg;
+  for (int64_t i = J->first; i < J->last; ++i) {
+    int64_t t = J->sel ? J->sel[i] : i;
+    int64_t a = J->offsets[t], b = J->offsets[t + 1];
+    double *inc = J->inc + J->out_off[i];
+    double s = 0.0;
+    J->ylt[i] = trial_loss(J->L, J->ids + a, b - a, &s, NULL, NULL, inc);
+    double m = 0.0; /* R11: 0 for an empty trial */
+    for (int64_t k = 0; k < b - a; ++k)
+      if (inc[k] > m) m = inc[k];
+    J->occ_max[i] = m;
+    if (J->presum) J->presum[i] = s;
+  }
+  return NULL;
+}
+
+/*
+ * Year Event Loss Table of one layer (reading R11) over the trials listed in
+ * sel[0..n_sel) (all trials when sel is NULL): the increments of every
+ * selected trial, concatenated in list order (trial i's at
+ * inc_out[out_off[i] .. out_off[i+1]), out_off int64[n+1] built by the
+ * caller from the trial lengths), each trial's largest increment
+ * (occ_max_out) and trial loss (ylt_out), and optionally its pre-aggregate
+ * sum.  Arguments otherwise as ara_oracle_layer_ylt.
+ */
+int ara_oracle_layer_yelt(int32_t catalog, int64_t n_trials, const int64_t *offsets,
+                          const int32_t *ids, int32_t n_elts, const int64_t *elt_off,
+                          const int32_t *elt_ids, const double *elt_losses, const double *ded,
+                          const double *lim, double occ_ret, double occ_lim, double agg_ret,
+                          double agg_lim, int32_t mode, int32_t n_threads, const int64_t *sel,
+                          int64_t n_sel, const int64_t *out_off, double *inc_out,
+                          double *occ_max_out, double *ylt_out, double *presum_out) {
+  int rc = check_yet(catalog, n_trials, offsets, ids);
+  if (rc) return rc;
+  int64_t n = sel ? n_sel : n_trials;
+  if (!out_off || out_off[0] != 0) return ORACLE_E_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t t = sel ? sel[i] : i;
+    if (t < 0 || t >= n_trials) return ORACLE_E_ARG;
+    if (out_off[i + 1] - out_off[i] != offsets[t + 1] - offsets[t]) return ORACLE_E_ARG;
+  }
+  layer_t L;
+  rc = init_layer(&L, catalog, n_elts, elt_off, elt_ids, elt_losses, ded, lim, occ_ret,
+                  occ_lim, agg_ret, agg_lim, mode == 1);
+  if (rc) {
+    free_layer(&L);
+    return rc;
+  }
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  if (n < n_threads) n_threads = n > 0 ? (int32_t)n : 1;
+  pthread_t th[256];
+  yelt_job_t jobs[256];
+  for (int32_t i = 0; i < n_threads; ++i) {
+    yelt_job_t J = {&L, offsets, ids, sel, out_off, n * i / n_threads, n * (i + 1) / n_threads,
+                    inc_out, occ_max_out, ylt_out, presum_out};
+    jobs[i] = J;
+  }
+  int32_t started = 0;
+  if (n_threads > 1)
+    for (; started < n_threads; ++started)
+      if (pthread_create(&th[started], NULL, run_yelt_job, &jobs[started])) break;
+  for (int32_t i = started; i < n_threads; ++i) run_yelt_job(&jobs[i]);
+  for (int32_t i = 0; i < started; ++i) pthread_join(th[i], NULL);
   free_layer(&L);
   return ORACLE_OK;
 }

@@ -334,3 +334,83 @@ def test_brute_force_three_event_catalog():
         # a sequential binary64 sum of m <= 6 non-negative terms is within
         # m ulps of the exact total; the clamps are 1-Lipschitz.
         assert abs(F(float(ylt[t])) - exact) <= F(8) * F(2) ** -52 * max(total, F(1)), tr
+
+
+# ------------------------------------------------------------------ YELT (R11)
+def test_hand_worked_yelt_and_oep():
+    g, yet, pool, layer = hand_instance()
+    y = g["yelt"]
+    for mode in ("literal", "memo"):
+        inc, out_off, occ_max, ylt, pre = oracle.layer_yelt(yet, pool, layer, mode=mode, threads=2)
+        for i, want in enumerate(y["inc"]):
+            assert inc[out_off[i]:out_off[i + 1]].tolist() == want
+        assert occ_max.tolist() == y["occ_max"]
+        assert ylt.tolist() == g["ylt"] and pre.tolist() == g["presum"]
+    oep, oep_tvar = oracle.pml_tvar(occ_max, y["return_periods"])
+    assert oep.tolist() == y["oep"] and oep_tvar.tolist() == y["oep_tvar"]
+    # a subset in another order
+    inc, out_off, occ_max, ylt, _ = oracle.layer_yelt(yet, pool, layer, trials=np.array([1, 0]))
+    assert inc.tolist() == y["inc"][1] + y["inc"][0]
+    assert occ_max.tolist() == [y["occ_max"][1], y["occ_max"][0]]
+
+
+@given(integer_instances())
+@settings(**small)
+def test_yelt_telescopes_and_bounds_occurrence_loss(inst):
+    """Integer losses: every running sum is exact, so the increments sum to the
+    trial loss exactly; the largest increment is at most the trial loss and at
+    least its share over the trial's events, and at most the occurrence limit."""
+    yet, pool, layer = inst
+    inc, out_off, occ_max, ylt, _ = oracle.layer_yelt(yet, pool, layer, threads=2)
+    ylt_ref, _ = oracle.layer_ylt(yet, pool, layer, threads=1)
+    np.testing.assert_array_equal(ylt, ylt_ref)
+    for t in range(yet.n_trials):
+        seg = inc[out_off[t]:out_off[t + 1]]
+        assert math.fsum(seg) == ylt[t]
+        assert np.all(seg >= 0.0)
+        assert occ_max[t] <= ylt[t] and occ_max[t] <= layer.occ_lim
+        if seg.size:
+            assert occ_max[t] == seg.max() and occ_max[t] * seg.size >= ylt[t]
+        else:
+            assert occ_max[t] == 0.0
+
+
+def test_yelt_brute_force_three_event_catalog():
+    """Every trial of length <= 5 over a 3-event catalog: each increment
+    against exact rationals of clamp(P_k) - clamp(P_{k-1})."""
+    rng = np.random.default_rng(12)
+    losses = rng.lognormal(6, 1.0, 6)
+    pool = ELTPool(np.array([0, 2, 4, 6], np.int64), np.array([0, 1, 1, 2, 2, 0], np.int32),
+                   losses, np.array([17.25, 3.5, 40.125]), np.array([700.5, 1e9, 333.0]))
+    layer = Layer([2, 0, 1], 11.75, 900.0, 250.5, 1700.25)
+    trials = [list(s) for m in range(6) for s in itertools.product(range(3), repeat=m)]
+    off = np.zeros(len(trials) + 1, np.int64)
+    off[1:] = np.cumsum([len(t) for t in trials])
+    yet = YET(3, off, np.array([e for t in trials for e in t], np.int32))
+    inc, out_off, occ_max, _, _ = oracle.layer_yelt(yet, pool, layer)
+    F = Fraction
+
+    def clamp(v, lo, hi):
+        return min(max(v, lo), hi)
+
+    occ = []
+    for e in range(3):
+        x = F(0)
+        for j in layer.elts:
+            ids, ls = pool.elt(j)
+            hit = [F(float(l)) for i, l in zip(ids, ls) if i == e]
+            x += clamp((hit[0] if hit else F(0)) - F(float(pool.deductibles[j])), F(0),
+                       F(float(pool.limits[j])))
+        occ.append(clamp(x - F(layer.occ_ret), F(0), F(layer.occ_lim)))
+    for t, tr in enumerate(trials):
+        P, prev, best = F(0), F(0), F(0)
+        for k, e in enumerate(tr):
+            P += occ[e]
+            a = clamp(P - F(layer.agg_ret), F(0), F(layer.agg_lim))
+            # the oracle's running sum is within k+1 ulps of P; both clamps are
+            # 1-Lipschitz and the subtraction rounds once
+            tol = F(16) * F(2) ** -52 * max(P, F(1))
+            assert abs(F(float(inc[out_off[t] + k])) - (a - prev)) <= tol, (tr, k)
+            best = max(best, a - prev)
+            prev = a
+        assert abs(F(float(occ_max[t])) - best) <= F(16) * F(2) ** -52 * max(prev + F(1), F(1))

@@ -26,8 +26,10 @@ MUTANTS = {
     "subtract_event": ("p = p + o;", "p = p - o;"),
     "first_elt_only": ("L->dats[(size_t)j * (size_t)L->catalog + (size_t)e]",
                        "L->dats[(size_t)0 * (size_t)L->catalog + (size_t)e]"),
-    "drop_last_event": ("J->ylt[i] = trial_loss(J->L, J->ids + a, b - a,",
-                        "J->ylt[i] = trial_loss(J->L, J->ids + a, b - a - (b > a),"),
+    "drop_last_event": ("J->ylt[i] = trial_loss(J->L, J->ids + a, b - a, &s, NULL, NULL, NULL);",
+                        "J->ylt[i] = trial_loss(J->L, J->ids + a, b - a - (b > a), &s, NULL, NULL, NULL);"),
+    "yelt_inc_not_differenced": ("if (inc) inc[k] = a - prev;", "if (inc) inc[k] = a;"),
+    "yelt_occ_max_first_event": ("if (inc[k] > m) m = inc[k];", "if (k == 0) m = inc[k];"),
     "pml_off_by_one": ("pml_out[r] = y[k - 1];", "pml_out[r] = y[k > 1 ? k - 2 : 0];"),
     "tvar_wrong_divisor": ("tvar_out[r] = s / (double)k;", "tvar_out[r] = s / (double)(k + 1);"),
     "clamp_occ_before_sum": ("x = x + ft1(l, L->ded[j], L->lim[j]);",
@@ -52,6 +54,11 @@ def pin_battery(lib):
     pml, tvar = oracle.pml_tvar(np.array(p["ylt"]), p["return_periods"], lib=lib)
     if pml.tolist() != p["pml"] or tvar.tolist() != p["tvar"]:
         failed.append("hand_pml_tvar")
+    y = g["yelt"]
+    inc, out_off, occ_max, _, _ = oracle.layer_yelt(yet, pool, layer, lib=lib)
+    if [inc[out_off[i]:out_off[i + 1]].tolist() for i in range(len(y["inc"]))] != y["inc"] or \
+            occ_max.tolist() != y["occ_max"]:
+        failed.append("hand_yelt")
     yet2, pool2, layer2 = _random_instance(1, neutral=True)
     raw = _dat_sum(pool2, layer2, yet2.catalog_size)
     trial_of = np.repeat(np.arange(yet2.n_trials), np.diff(yet2.offsets))
