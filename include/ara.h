@@ -229,6 +229,39 @@ ARA_API ara_status ara_pml_tvar_batch(ara_ctx *ctx, const double *ylt, int32_t n
                                       const double *return_periods, int32_t n_rp, double *pml_out,
                                       double *tvar_out);
 
+/* Year Event Loss Table of one layer over the first n_trials trials
+ * (Section III, step 4: the aggregate terms act on the running sum after
+ * every event; the YELT keeps each event's share of the trial loss).  For
+ * occurrence k of trial t (stored order), with P_k the running sum of
+ * occurrence-net losses and a_k = min(max(P_k - AggR, 0), AggL), a_0 = 0:
+ *   yelt_out[offsets[t] + k] = a_k - a_{k-1}     (>= 0; a trial's entries sum
+ *                                                 to its YLT entry up to rounding)
+ *   occ_max_out[t] = max_k (a_k - a_{k-1})       (0 for an empty trial: the
+ *                                                 trial's occurrence loss for OEP)
+ *   yelt_out     double[offsets[n_trials]], host or device, CSR by the YET's
+ *                trial offsets; NULL if not wanted
+ *   occ_max_out  double[n_trials], host or device; NULL if not wanted
+ *   cuda_stream  stream for this call, or NULL for the context's stream
+ * FP64 layers: the running sums are exact integers on the layer's grid; each
+ * entry is rounded once.  Errors as ara_layer_ylt. */
+ARA_API ara_status ara_layer_yelt(ara_ctx *ctx, int32_t layer, int64_t n_trials, double *yelt_out,
+                                  double *occ_max_out, void *cuda_stream);
+
+/* Return Period Loss report of one layer over the first n_trials trials
+ * (Section III names RPL reports beside PML and TVaR): for each return
+ * period RP, k = floor(n_trials / RP),
+ *   aep_out[r], aep_tvar_out[r]  k-th largest trial loss and mean of the k
+ *                                largest (aggregate exceedance: equal to
+ *                                ara_pml_tvar of the layer's YLT)
+ *   oep_out[r], oep_tvar_out[r]  the same over the trials' largest
+ *                                increments (occurrence exceedance)
+ * return_periods: double[n_rp] (host, 1..16 values, RP >= 1 and k >= 1);
+ * outputs: double[n_rp] each (host).  Errors as ara_layer_ylt and
+ * ara_pml_tvar. */
+ARA_API ara_status ara_rpl_report(ara_ctx *ctx, int32_t layer, int64_t n_trials,
+                                  const double *return_periods, int32_t n_rp, double *aep_out,
+                                  double *aep_tvar_out, double *oep_out, double *oep_tvar_out);
+
 /* Allocation-free variant of ara_pml_tvar.  The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc -- a service whose
  * pooling allocator already owns the device memory it may use, or a

@@ -91,6 +91,8 @@ class Engine:
         p_ids, k2 = _arg(ids, np.int32, "ids")
         p_ts, k3 = _arg(ts, np.float32, "ts")
         _native.ara_load_yet(self.ctx, int(catalog_size), n_trials, p_off, p_ids, p_ts)
+        self._offsets_host = (offsets.detach().cpu().numpy() if _is_tensor(offsets)
+                              else np.asarray(offsets, dtype=np.int64)).copy()
         self.catalog_size = int(catalog_size)
         self.n_trials = n_trials
 
@@ -162,6 +164,35 @@ class Engine:
         _native.ara_pml_tvar_batch(self.ctx, p, n_layers, n, rps.ctypes.data, int(rps.shape[0]),
                                    pml.ctypes.data, tvar.ctypes.data)
         return pml, tvar
+
+    def layer_yelt(self, layer: int, n_trials: Optional[int] = None, out=None, occ_max=None,
+                   want_yelt: bool = True, stream=None):
+        """Year Event Loss Table: (per-occurrence increments in the YET's CSR
+        order, largest increment per trial).  ``out``/``occ_max`` may be
+        float64 NumPy arrays or CUDA tensors; with ``want_yelt=False`` only
+        the per-trial maxima are produced (the first value is then None)."""
+        n = self.n_trials if n_trials is None else int(n_trials)
+        if out is None and want_yelt:
+            # (an n outside [0, n_trials] is rejected by the library)
+            out = np.empty(int(self._offsets_host[min(max(n, 0), self.n_trials)]), dtype=np.float64)
+        if occ_max is None:
+            occ_max = np.empty(max(n, 0), dtype=np.float64)
+        p1, k1 = _arg(out, np.float64, "out")
+        p2, k2 = _arg(occ_max, np.float64, "occ_max")
+        if (out is not None and k1 is not out) or k2 is not occ_max:
+            raise TypeError("outputs must be contiguous float64 arrays or tensors")
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+        _native.ara_layer_yelt(self.ctx, layer, n, p1, p2, int(handle or 0))
+        return out, occ_max
+
+    def rpl_report(self, layer: int, return_periods: Sequence[float], n_trials: Optional[int] = None):
+        """Return period losses: dict of aep, aep_tvar, oep, oep_tvar arrays."""
+        n = self.n_trials if n_trials is None else int(n_trials)
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        outs = [np.zeros(rps.shape[0]) for _ in range(4)]
+        _native.ara_rpl_report(self.ctx, layer, n, rps.ctypes.data, int(rps.shape[0]),
+                               *[o.ctypes.data for o in outs])
+        return dict(zip(("aep", "aep_tvar", "oep", "oep_tvar"), outs))
 
     def event_table(self, layer: int, out=None):
         """The layer's per-event occurrence-net loss (float64, one per catalog event)."""

@@ -78,6 +78,8 @@ PROTOTYPES = {
     "ara_pml_tvar_batch": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp]),
     "ara_set_kernel_timing": (_i32, [_vp, _i32]),
     "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
+    "ara_layer_yelt": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
+    "ara_rpl_report": (_i32, [_vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp, _vp]),
     "ara_service_create": (_i32, [_vp, C.POINTER(ServiceConfig), C.POINTER(C.c_void_p)]),
     "ara_service_submit": (_i32, [_vp, C.POINTER(Request), C.POINTER(_i64)]),
     "ara_service_wait": (_i32, [_vp, _i64, _f64, C.POINTER(Result)]),
@@ -195,6 +197,18 @@ def ara_pml_tvar_noalloc(ylt: int, n: int, return_periods: int, n_rp: int, pml_o
     """Context-free PML/TVaR that allocates no device memory (ylt on the device)."""
     _check(None, lib.ara_pml_tvar_noalloc(ylt or None, int(n), return_periods or None, int(n_rp),
                                           pml_out or None, tvar_out or None, stream or None))
+
+
+def ara_layer_yelt(ctx: int, layer: int, n_trials: int, yelt_out: int, occ_max_out: int,
+                   stream: int = 0) -> None:
+    _check(ctx, lib.ara_layer_yelt(ctx, int(layer), int(n_trials), yelt_out or None, occ_max_out or None,
+                                   stream or None))
+
+
+def ara_rpl_report(ctx: int, layer: int, n_trials: int, return_periods: int, n_rp: int, aep: int,
+                   aep_tvar: int, oep: int, oep_tvar: int) -> None:
+    _check(ctx, lib.ara_rpl_report(ctx, int(layer), int(n_trials), return_periods or None, int(n_rp),
+                                   aep or None, aep_tvar or None, oep or None, oep_tvar or None))
 
 
 def ara_set_kernel_timing(ctx: int, enable: bool) -> None:

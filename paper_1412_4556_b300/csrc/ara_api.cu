@@ -517,6 +517,7 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_raw);
   cudaFree(c->d_ts);
   cudaFree(c->d_ylt_stage);
+  cudaFree(c->d_yelt_stage);
   cudaFree(c->d_sel_in);
   cudaFree(c->d_sel_ws);
   cudaFree(c->d_sel_out);
@@ -890,6 +891,98 @@ ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, i
   if (!dev) {
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, dst, total * sizeof(double), cudaMemcpyDeviceToHost, s), "copy YLTs");
     ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
+  return ARA_OK;
+}
+
+ara_status ara_layer_yelt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yelt_out,
+                          double *occ_max_out, void *cuda_stream) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  LayerRec *L = nullptr;
+  ara_status st = get_layer(c, layer, &L);
+  if (st) return st;
+  if (n_trials < 0 || n_trials > c->n_trials)
+    return fail(c, ARA_E_INVALID_ARG, "n_trials %lld outside [0, %lld]", (long long)n_trials,
+                (long long)c->n_trials);
+  if (n_trials == 0) return ARA_OK;
+  const int64_t M = c->h_offsets[(size_t)n_trials];
+  if (M > 0 && !yelt_out && !occ_max_out) return fail(c, ARA_E_INVALID_ARG, "no output given");
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+  if (L->folded_version != c->yet_version) {
+    st = fold_layer(c, *L, s);
+    if (st) return st;
+  }
+  const bool ydev = yelt_out && is_device_ptr(yelt_out);
+  const bool odev = occ_max_out && is_device_ptr(occ_max_out);
+  double *ydst = ydev ? yelt_out : nullptr;
+  double *odst = odev ? occ_max_out : nullptr;
+  if (yelt_out && !ydev) {
+    ARA_CUDA(c, ensure(&c->d_yelt_stage, &c->cap_yelt_stage, (size_t)M), "YELT stage buffer");
+    ydst = c->d_yelt_stage;
+  }
+  if (occ_max_out && !odev) {
+    ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, (size_t)n_trials), "stage buffer");
+    odst = c->d_ylt_stage;
+  }
+  const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, nullptr};
+  ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table, L->d_bitmap,
+                          L->bm, c->catalog, out, ydst, odst, c->device, s),
+           "YELT kernel launch");
+  if (yelt_out && !ydev)
+    ARA_CUDA(c, cudaMemcpyAsync(yelt_out, ydst, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copy YELT");
+  if (occ_max_out && !odev)
+    ARA_CUDA(c, cudaMemcpyAsync(occ_max_out, odst, (size_t)n_trials * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copy occurrence maxima");
+  if ((yelt_out && !ydev) || (occ_max_out && !odev))
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return ARA_OK;
+}
+
+ara_status ara_rpl_report(ara_ctx *c, int32_t layer, int64_t n_trials, const double *rps, int32_t n_rp,
+                          double *aep_out, double *aep_tvar_out, double *oep_out, double *oep_tvar_out) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  LayerRec *L = nullptr;
+  ara_status st = get_layer(c, layer, &L);
+  if (st) return st;
+  if (n_trials < 1 || n_trials > c->n_trials)
+    return fail(c, ARA_E_INVALID_ARG, "n_trials %lld outside [1, %lld]", (long long)n_trials,
+                (long long)c->n_trials);
+  if (!aep_out || !aep_tvar_out || !oep_out || !oep_tvar_out)
+    return fail(c, ARA_E_INVALID_ARG, "NULL output array");
+  int64_t k[kMaxReturnPeriods];
+  if (tail_counts(n_trials, rps, n_rp, k) != ARA_OK) return fail(c, ARA_E_INVALID_ARG, "%s", ara_last_error(nullptr));
+  cudaStream_t s = c->stream;
+  if (L->folded_version != c->yet_version) {
+    st = fold_layer(c, *L, s);
+    if (st) return st;
+  }
+  // [0, n): trial losses (AEP); [n, 2n): largest increment per trial (OEP)
+  ARA_CUDA(c, ensure(&c->d_sel_in, &c->cap_sel_in, 2 * (size_t)n_trials), "report buffer");
+  const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, c->d_sel_in};
+  ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table, L->d_bitmap,
+                          L->bm, c->catalog, out, nullptr, c->d_sel_in + n_trials, c->device, s),
+           "YELT kernel launch");
+  ARA_CUDA(c, ensure(&c->d_sel_ws_batch, &c->cap_sel_ws_batch, 2 * select_workspace_bytes(kMaxReturnPeriods)),
+           "selection workspace");
+  ARA_CUDA(c, ensure(&c->d_sel_out_batch, &c->cap_sel_out_batch, 4 * (size_t)n_rp), "selection output");
+  ARA_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
+  ARA_CUDA(c, launch_pml_tvar_batch(c->d_sel_in, 2, n_trials, k, n_rp, c->d_sel_ws_batch, c->d_sel_out_batch,
+                                    c->d_err, c->device, s),
+           "PML/TVaR kernels");
+  std::vector<double> res(4 * (size_t)n_rp);
+  ARA_CUDA(c, cudaMemcpyAsync(res.data(), c->d_sel_out_batch, res.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copy report");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  for (int32_t r = 0; r < n_rp; ++r) {
+    aep_out[r] = res[(size_t)r];
+    aep_tvar_out[r] = res[(size_t)n_rp + r];
+    oep_out[r] = res[2 * (size_t)n_rp + r];
+    oep_tvar_out[r] = res[3 * (size_t)n_rp + r];
   }
   return ARA_OK;
 }

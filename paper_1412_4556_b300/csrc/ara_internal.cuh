@@ -272,6 +272,14 @@ cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t
 cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const float *ts,
                             unsigned long long *bad_count, cudaStream_t s);
 
+// Year Event Loss Table of one layer: per-occurrence increments into
+// yelt[raw_off[t] + k] (nullable), each trial's largest increment into
+// occ_max[t] (nullable), and the trial loss into L.ylt[t] (nullable).
+cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
+                        int64_t n_trials, const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                        int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max, int device,
+                        cudaStream_t s);
+
 // PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes
 // per layer; the batch form reads n_layers YLTs of n values each (layer-major)
 // and writes 2*n_rp values per layer (PML then TVaR).

@@ -1,0 +1,192 @@
+// Year Event Loss Table: the per-occurrence increments of Algorithm 1's
+// aggregate step (Section III, step 4 applied after every event of a trial),
+// and each trial's largest increment for occurrence exceedance (OEP) reports.
+//
+// For trial t with occurrence-net losses o_1..o_n (stored order):
+//     P_k   = o_1 + ... + o_k                      (running sum)
+//     a_k   = min(max(P_k - AggR, 0), AggL)        (aggregate terms)
+//     inc_k = a_k - a_{k-1},   a_0 = 0             (YELT entry of occurrence k)
+// and the trial loss is a_n (the YLT entry).
+//
+// B300 design: one warp per trial walks the trial's 16-byte id chunks in
+// order, 32 chunks per step.  Each lane gathers its chunk's table entries
+// (zero-skip bitmap in shared memory, as in the YLT kernel), forms their
+// prefix sums, and the warp turns the lane totals into an exclusive scan with
+// shuffles: a segmented scan whose segments are the trials.  The running
+// sums are 128-bit fixed-point integers, so every P_k is exact; when the
+// aggregate terms lie on the table's grid the clamps and differences are
+// exact integers too and each increment is rounded to binary64 once.
+#include "ara_internal.cuh"
+
+namespace ara {
+
+namespace {
+
+__device__ __forceinline__ ulonglong2 gather_or_zero(const ulonglong2 *p, uint32_t hit) {
+  unsigned long long a = 0ull, b = 0ull;
+  asm("{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p ld.global.nc.v2.u64 {%0, %1}, [%3];\n\t}"
+      : "+l"(a), "+l"(b)
+      : "r"(hit), "l"(p));
+  return make_ulonglong2(a, b);
+}
+
+__device__ __forceinline__ U128 add(U128 a, U128 b) {
+  add128(a, b.lo, b.hi);
+  return a;
+}
+
+// Aggregate clamp of a running sum on the fixed-point grid (exact terms).
+__device__ __forceinline__ U128 clamp_fixed(U128 P, const AggFixed &af) {
+  U128 d{0ull, 0ull};
+  if (ge128(P, af.ret)) d = sub128(P, af.ret);
+  if (ge128(d, af.lim)) d = af.lim;
+  return d;
+}
+
+__device__ __forceinline__ double clamp_fp64(U128 P, int q, double agg_ret, double agg_lim) {
+  return fmin(fmax(__dsub_rn(from_fixed(P, q), agg_ret), 0.0), agg_lim);
+}
+
+__device__ __forceinline__ U128 shfl_up_u128(U128 v, int d) {
+  U128 r;
+  r.lo = __shfl_up_sync(0xFFFFFFFFu, v.lo, d);
+  r.hi = __shfl_up_sync(0xFFFFFFFFu, v.hi, d);
+  return r;
+}
+
+__device__ __forceinline__ U128 shfl_u128(U128 v, int src) {
+  U128 r;
+  r.lo = __shfl_sync(0xFFFFFFFFu, v.lo, src);
+  r.hi = __shfl_sync(0xFFFFFFFFu, v.hi, src);
+  return r;
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void chunk_ids_y(int4 c, uint32_t (&id)[PACKED ? 6 : 4]) {
+  if constexpr (PACKED) {
+    constexpr uint32_t M = 0x1FFFFFu;
+    id[0] = (uint32_t)c.x & M;
+    id[1] = __funnelshift_r((uint32_t)c.x, (uint32_t)c.y, 21) & M;
+    id[2] = ((uint32_t)c.y >> 10) & M;
+    id[3] = (uint32_t)c.z & M;
+    id[4] = __funnelshift_r((uint32_t)c.z, (uint32_t)c.w, 21) & M;
+    id[5] = ((uint32_t)c.w >> 10) & M;
+  } else {
+    id[0] = (uint32_t)c.x;
+    id[1] = (uint32_t)c.y;
+    id[2] = (uint32_t)c.z;
+    id[3] = (uint32_t)c.w;
+  }
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kYltThreads, 1)
+yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
+            const int64_t *__restrict__ raw_off, int64_t n_trials, const ulonglong2 *__restrict__ table,
+            const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul, int4 sent4, LayerOut L,
+            double *__restrict__ yelt, double *__restrict__ occ_max) {
+  constexpr int IDS = PACKED ? 6 : 4;
+  extern __shared__ uint4 s_bm4[];
+  for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
+  __syncthreads();
+  const uint32_t *s_bm = reinterpret_cast<const uint32_t *>(s_bm4);
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t t_begin = n_trials * w / n_warps;
+  const int64_t t_end = n_trials * (w + 1) / n_warps;
+  const bool exact = L.af.exact != 0;
+
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    const int64_t p0 = coff[t];
+    const int nk = (int)(coff[t + 1] - p0);
+    const int64_t r0 = raw_off[t];
+    const int64_t nr = raw_off[t + 1] - r0;  // occurrences of trial t
+    U128 carry{0ull, 0ull};                  // running sum before this step
+    double best = 0.0;                       // largest increment seen by this lane
+    for (int base = 0; base < nk; base += 32) {
+      const int j = base + lane;
+      const int4 v = j < nk ? chunks[p0 + j] : sent4;
+      uint32_t id[IDS];
+      chunk_ids_y<PACKED>(v, id);
+      U128 x[IDS];
+      U128 tot{0ull, 0ull};
+#pragma unroll
+      for (int i = 0; i < IDS; ++i) {
+        const uint32_t word = s_bm[bitmap_word(id[i], bm_mul)];
+        const uint32_t hit = __funnelshift_r(word, word, id[i]) & 1u;
+        const ulonglong2 e = gather_or_zero(table + id[i], hit);
+        x[i] = U128{e.x, e.y};
+        tot = add(tot, x[i]);
+      }
+      // inclusive scan of the lane totals across the warp
+      U128 incl = tot;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const U128 o = shfl_up_u128(incl, d);
+        if (lane >= d) incl = add(incl, o);
+      }
+      const U128 step_total = shfl_u128(incl, 31);
+      // running sum before this lane's first id: carry + exclusive prefix
+      U128 P = sub128(add(carry, incl), tot);
+      U128 a_fx = exact ? clamp_fixed(P, L.af) : U128{0ull, 0ull};
+      double a_fp = exact ? 0.0 : clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
+      const int64_t k0 = (int64_t)j * IDS;  // index of id[0] within the trial
+#pragma unroll
+      for (int i = 0; i < IDS; ++i) {
+        P = add(P, x[i]);
+        double inc;
+        if (exact) {
+          const U128 a = clamp_fixed(P, L.af);
+          inc = from_fixed_int(sub128(a, a_fx), L.q);
+          a_fx = a;
+        } else {
+          const double a = clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
+          inc = __dsub_rn(a, a_fp);
+          a_fp = a;
+        }
+        if (k0 + i < nr) {
+          best = fmax(best, inc);
+          if (yelt) yelt[r0 + k0 + i] = inc;
+        }
+      }
+      carry = add(carry, step_total);
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) best = fmax(best, __shfl_xor_sync(0xFFFFFFFFu, best, m));
+    if (lane == 0) {
+      if (occ_max) occ_max[t] = best;
+      if (L.ylt) L.ylt[t] = trial_loss(carry, L.q, L.af, L.agg_ret, L.agg_lim);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
+                        int64_t n_trials, const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                        int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max, int device,
+                        cudaStream_t s) {
+  if (n_trials <= 0) return cudaSuccess;
+  int sms = 148;
+  cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (err != cudaSuccess) return err;
+  const size_t smem = (size_t)bm.words * 4u;
+  const void *fn = packed ? (const void *)yelt_kernel<true> : (const void *)yelt_kernel<false>;
+  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
+  const int4 sent4 = packed ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
+  const uint4 *bm4 = reinterpret_cast<const uint4 *>(bitmap);
+  if (packed)
+    yelt_kernel<true><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table, bm4, bm.words / 4,
+                                                     bm.mul, sent4, L, yelt, occ_max);
+  else
+    yelt_kernel<false><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table, bm4,
+                                                      bm.words / 4, bm.mul, sent4, L, yelt, occ_max);
+  return cudaGetLastError();
+}
+
+}  // namespace ara
