@@ -125,8 +125,10 @@ size_t ylt_smem_budget(int device) {
 }
 
 // Fixed-point exponent for a layer: any trial sum is at most upper * lmax;
-// keep the 128-bit integer below 2^127.
-bool choose_q(double upper, int64_t lmax, int *q) {
+// keep the integer below 2^(bits - 1): 2^127 for the 128-bit entries of FP64
+// layers, 2^63 for the 64-bit entries of FP32-table layers (each entry then
+// rounds to the grid, adding at most lmax / 2 grid steps to the sum).
+bool choose_q(double upper, int64_t lmax, int bits, int *q) {
   if (!(upper > 0.0) || lmax <= 0) {
     *q = 0;
     return true;
@@ -135,7 +137,7 @@ bool choose_q(double upper, int64_t lmax, int *q) {
   if (!std::isfinite(bound)) return false;
   int e = 0;
   std::frexp(bound, &e);  // bound < 2^e
-  *q = e + 1 - 127;
+  *q = e + 1 - bits;
   return true;
 }
 
@@ -179,7 +181,7 @@ AggFixed agg_terms_fixed(double agg_ret, double agg_lim, int q) {
 
 ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
   int q = 0;
-  if (!choose_q(L.upper, std::max<int64_t>(c->max_trial_len, 1), &q))
+  if (!choose_q(L.upper, std::max<int64_t>(c->max_trial_len, 1), L.entry_bytes() * 8 - 1, &q))
     return fail(c, ARA_E_INVALID_ARG,
                 "layer loss bound x longest trial overflows binary64; losses too large");
   if (L.table_catalog != c->catalog || !L.d_table) {
@@ -200,6 +202,11 @@ ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
   L.q = q;
   L.agg_fx = agg_terms_fixed(L.agg_ret, L.agg_lim, q);
   ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
+  // The sentinel entry (id = catalog) must read zero at this layer's entry
+  // width; a buffer used before at the other width may hold data there.
+  ARA_CUDA(c, cudaMemsetAsync(reinterpret_cast<unsigned char *>(L.d_table) + (size_t)c->catalog * L.entry_bytes(), 0,
+                              (size_t)L.entry_bytes(), s),
+           "cudaMemsetAsync(sentinel entry)");
   TimedLaunch tl(c, ARA_TIMING_FOLD, s);
   ARA_CUDA(c, launch_fold(L.d_desc, (int)L.elts.size(), c->catalog, L.occ_ret, L.occ_lim, q,
                           L.d_table, L.d_bitmap, L.bm, L.precision == ARA_FP32_TABLE, nullptr, s),
@@ -410,31 +417,44 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
   const BitmapLayout bm = Ls[0]->bm;  // every layer of a catalog shares the layout
   const size_t entries = (size_t)c->catalog + 1;
   const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
-  for (int32_t i = 0; i < n_layers; i += 2) {
-    const int G = (i + 1 < n_layers) ? 2 : 1;
-    LayerOut outs[2];
-    for (int g = 0; g < G; ++g) {
-      const LayerRec *L = Ls[(size_t)(i + g)];
-      outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst + (size_t)(i + g) * (size_t)n_trials};
+  // FP64 layers go two to a pass (2 x 16-byte entries per event), FP32-table
+  // layers four to a pass (4 x 8 bytes): one 32-byte L2 sector per gather.
+  for (const int eb : {16, 8}) {
+    std::vector<int32_t> idx;
+    for (int32_t i = 0; i < n_layers; ++i)
+      if (Ls[(size_t)i]->entry_bytes() == eb) idx.push_back(i);
+    const int gmax = 32 / eb;
+    for (size_t p = 0; p < idx.size();) {
+      int G = (int)std::min<size_t>((size_t)gmax, idx.size() - p);
+      if (G == 3) G = 2;
+      LayerOut outs[4];
+      Tables4 tabs{};
+      Bitmaps4 bms{};
+      for (int g = 0; g < G; ++g) {
+        const LayerRec *L = Ls[(size_t)idx[p + (size_t)g]];
+        outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim,
+                           dst + (size_t)idx[p + (size_t)g] * (size_t)n_trials};
+        tabs.t[g] = L->d_table;
+        bms.b[g] = L->d_bitmap;
+      }
+      const void *table = tabs.t[0];
+      const uint32_t *bitmap = bms.b[0];
+      if (G > 1) {
+        ARA_CUDA(c, launch_interleave(tabs, eb, G, (int64_t)entries, pair_table, bms, bm.words, pair_bitmap, s),
+                 "interleave layer tables");
+        table = pair_table;
+        bitmap = pair_bitmap;
+      }
+      YltLaunch cfg;
+      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, eb, G, c->tuned[G == 4 ? 3 : G], &cfg),
+               "plan YLT launch");
+      TimedLaunch tl(c, ARA_TIMING_YLT, s);
+      ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, eb, bitmap, bm, c->catalog,
+                                   G, outs, cfg, s),
+               "YLT kernel launch");
+      tl.done();
+      p += (size_t)G;
     }
-    const ulonglong2 *table = Ls[(size_t)i]->d_table;
-    const uint32_t *bitmap = Ls[(size_t)i]->d_bitmap;
-    if (G == 2) {
-      ARA_CUDA(c, launch_interleave(Ls[(size_t)i]->d_table, Ls[(size_t)i + 1]->d_table, (int64_t)entries,
-                                    pair_table, Ls[(size_t)i]->d_bitmap, Ls[(size_t)i + 1]->d_bitmap,
-                                    bm.words, pair_bitmap, s),
-               "interleave layer tables");
-      table = pair_table;
-      bitmap = pair_bitmap;
-    }
-    YltLaunch cfg;
-    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, G, c->tuned[G], &cfg),
-             "plan YLT launch");
-    TimedLaunch tl(c, ARA_TIMING_YLT, s);
-    ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, bitmap, bm,
-                                 c->catalog, G, outs, cfg, s),
-             "YLT kernel launch");
-    tl.done();
   }
   return ARA_OK;
 }
@@ -799,12 +819,12 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
   }
   const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, 1, c->tuned[1], &cfg),
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, L->entry_bytes(), 1, c->tuned[1], &cfg),
            "plan YLT launch");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst};
   TimedLaunch tl(c, ARA_TIMING_YLT, s);
-  ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, L->d_table, L->d_bitmap,
-                               L->bm, c->catalog, 1, &out, cfg, s),
+  ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, L->d_table, L->entry_bytes(),
+                               L->d_bitmap, L->bm, c->catalog, 1, &out, cfg, s),
            "YLT kernel launch");
   tl.done();
   if (!dev) {
@@ -927,8 +947,8 @@ ara_status ara_layer_yelt(ara_ctx *c, int32_t layer, int64_t n_trials, double *y
     odst = c->d_ylt_stage;
   }
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, nullptr};
-  ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table, L->d_bitmap,
-                          L->bm, c->catalog, out, ydst, odst, c->device, s),
+  ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table,
+                          L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, ydst, odst, c->device, s),
            "YELT kernel launch");
   if (yelt_out && !ydev)
     ARA_CUDA(c, cudaMemcpyAsync(yelt_out, ydst, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -964,8 +984,9 @@ ara_status ara_rpl_report(ara_ctx *c, int32_t layer, int64_t n_trials, const dou
   // [0, n): trial losses (AEP); [n, 2n): largest increment per trial (OEP)
   ARA_CUDA(c, ensure(&c->d_sel_in, &c->cap_sel_in, 2 * (size_t)n_trials), "report buffer");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, c->d_sel_in};
-  ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table, L->d_bitmap,
-                          L->bm, c->catalog, out, nullptr, c->d_sel_in + n_trials, c->device, s),
+  ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table,
+                          L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, nullptr, c->d_sel_in + n_trials,
+                          c->device, s),
            "YELT kernel launch");
   ARA_CUDA(c, ensure(&c->d_sel_ws_batch, &c->cap_sel_ws_batch, 2 * select_workspace_bytes(kMaxReturnPeriods)),
            "selection workspace");

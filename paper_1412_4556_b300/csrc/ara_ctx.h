@@ -39,6 +39,9 @@ struct LayerRec {
   AggFixed agg_fx{{0ull, 0ull}, {0ull, 0ull}, 0};
   int64_t folded_version = -1;
   double upper = 0.0;  // upper bound of any per-event table value
+  // Table entry width: 128-bit entries for FP64 layers, 64-bit entries (the
+  // first half of the same buffer) for FP32-table layers.
+  int entry_bytes() const { return precision == ARA_FP32_TABLE ? 8 : 16; }
 };
 
 // Device buffers of a released layer, kept for the next layer (defining and
@@ -118,7 +121,7 @@ struct ara_ctx {
   size_t cap_pair_table = 0;
   uint32_t *d_pair_bitmap = nullptr;        // union of their bitmaps
   size_t cap_pair_bitmap = 0;
-  ara::YltShape tuned[3];                   // YLT launch shape picked by the autotuner, per G
+  ara::YltShape tuned[4];                   // YLT launch shape picked by the autotuner, per G (3: G = 4)
   unsigned long long *d_counter = nullptr;  // validation counters
   unsigned int *d_err = nullptr;            // PML/TVaR input check flag
   // timing

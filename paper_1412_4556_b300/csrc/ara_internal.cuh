@@ -219,7 +219,7 @@ __device__ __forceinline__ U128 warp_sum_u128(U128 v) {
 // --------------------------------------------------------- launchers
 // Each returns cudaSuccess or the launch error.
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
-                        double occ_lim, int q, ulonglong2 *table, uint32_t *bitmap,
+                        double occ_lim, int q, void *table, uint32_t *bitmap,
                         BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s);
 
 struct YltLaunch {
@@ -247,23 +247,30 @@ struct LayerOut {
 
 // coff/chunks: the chunked YET layout written by launch_pad_ids (packed: 6
 // ids of 21 bits per chunk, else 4 plain ids); sentinel = catalog size (its
-// table entry is zero).  G = 1: one layer's table (16 bytes per event);
-// G = 2: two layers' tables interleaved (32 bytes per event) with the union
-// of their bitmaps.
+// table entry is zero).  entry_bytes = 16 for FP64 layers (128-bit
+// fixed-point entries) or 8 for FP32-table layers (64-bit entries whose trial
+// sums stay below 2^64); G layers' tables interleaved (entry_bytes x G <= 32
+// bytes per event, one L2 sector) with the union of their bitmaps.
 cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
-                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                             const void *table, int entry_bytes, const uint32_t *bitmap, BitmapLayout bm,
                              int32_t sentinel, int G, const LayerOut *outs, const YltLaunch &cfg,
                              cudaStream_t s);
 
 // Pick the launch shape of the YLT kernel for a bitmap of bm.words words and
 // trials of mean_chunks 16-byte chunks; non-zero fields of hint force the
-// unroll (1/2/4) or the lanes per trial (8/16/32).
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int G,
-                     YltShape hint, YltLaunch *out);
+// unroll (1/2) or the lanes per trial (16/32).  entry_bytes x G <= 32.
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int entry_bytes,
+                     int G, YltShape hint, YltLaunch *out);
 
-cudaError_t launch_interleave(const ulonglong2 *ta, const ulonglong2 *tb, int64_t entries,
-                              ulonglong2 *out, const uint32_t *ba, const uint32_t *bb,
-                              int32_t words, uint32_t *bout, cudaStream_t s);
+// Up to four layers' tables and bitmaps for launch_interleave.
+struct Tables4 {
+  const void *t[4];
+};
+struct Bitmaps4 {
+  const uint32_t *b[4];
+};
+cudaError_t launch_interleave(const Tables4 &in, int entry_bytes, int G, int64_t entries, void *out,
+                              const Bitmaps4 &bin, int32_t words, uint32_t *bout, cudaStream_t s);
 
 cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *coff,
                            int64_t n_trials, int4 *dst, int32_t catalog, bool packed,
@@ -276,9 +283,9 @@ cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const floa
 // yelt[raw_off[t] + k] (nullable), each trial's largest increment into
 // occ_max[t] (nullable), and the trial loss into L.ylt[t] (nullable).
 cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
-                        int64_t n_trials, const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                        int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max, int device,
-                        cudaStream_t s);
+                        int64_t n_trials, const void *table, int entry_bytes, const uint32_t *bitmap,
+                        BitmapLayout bm, int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max,
+                        int device, cudaStream_t s);
 
 // PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes
 // per layer; the batch form reads n_layers YLTs of n values each (layer-major)

@@ -13,12 +13,14 @@
 // One CTA owns kFoldEventsPerCta consecutive catalog events and keeps their
 // running sums in shared memory.  Each ELT is stored sorted by event id with
 // a bucket index, so the CTA finds its slice of every ELT with two loads.
-// Outputs per event: the 128-bit fixed-point table entry used by the YLT
-// kernel, one bit of the zero-skip bitmap, and (optionally) the FP64 value.
-// Reduced-precision layers run the same steps in binary32 (the paper's
-// "single precision when possible", Section IV-B); their values are then
-// binary32 numbers held exactly in the same fixed-point table, and each trial
-// is still summed exactly, so only the per-event values carry FP32 rounding.
+// Outputs per event: the fixed-point table entry used by the YLT kernel, one
+// bit of the zero-skip bitmap, and (optionally) the FP64 value.  FP64 layers
+// store round(o / 2^q) as a 128-bit integer (exact for every value the grid
+// can hold).  Reduced-precision layers run the same steps in binary32 (the
+// paper's "single precision when possible", Section IV-B) and store 64-bit
+// entries on a grid chosen so that no trial sum reaches 2^64: half the table
+// bytes; rounding to that grid moves a trial sum by less than its length x
+// 2^(q-1), far below the binary32 rounding of the values themselves.
 #include <type_traits>
 
 #include "ara_internal.cuh"
@@ -42,7 +44,7 @@ __device__ __forceinline__ float elt_terms32(double loss, double deductible, dou
 template <bool FP32>
 __global__ void __launch_bounds__(kFoldThreads)
 fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
-            double occ_lim, int q, ulonglong2 *__restrict__ table, uint32_t *__restrict__ bitmap,
+            double occ_lim, int q, void *__restrict__ table, uint32_t *__restrict__ bitmap,
             uint32_t bm_mul, double *__restrict__ f64_out) {
   using Real = typename std::conditional<FP32, float, double>::type;
   __shared__ Real x[kFoldEventsPerCta];
@@ -123,7 +125,10 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
     if (f64_out) f64_out[e] = o;
     if (table) {
       const U128 v = to_fixed(o, q);
-      table[e] = make_ulonglong2(v.lo, v.hi);
+      if constexpr (FP32)
+        static_cast<unsigned long long *>(table)[e] = v.lo;  // v.hi = 0 on this grid
+      else
+        static_cast<ulonglong2 *>(table)[e] = make_ulonglong2(v.lo, v.hi);
       if ((v.lo | v.hi) != 0ull) {
         atomicOr(bitmap + bitmap_word((uint32_t)e, bm_mul), 1u << (e & 31));
       }
@@ -132,7 +137,7 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
 }
 
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
-                        double occ_lim, int q, ulonglong2 *table, uint32_t *bitmap,
+                        double occ_lim, int q, void *table, uint32_t *bitmap,
                         BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s) {
   if (catalog <= 0) return cudaSuccess;
   const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;

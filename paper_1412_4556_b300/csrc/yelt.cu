@@ -32,6 +32,16 @@ __device__ __forceinline__ ulonglong2 gather_or_zero(const ulonglong2 *p, uint32
   return make_ulonglong2(a, b);
 }
 
+__device__ __forceinline__ unsigned long long gather_or_zero8(const unsigned long long *p, uint32_t hit) {
+  unsigned long long a = 0ull;
+  asm("{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "@p ld.global.nc.u64 %0, [%2];\n\t}"
+      : "+l"(a)
+      : "r"(hit), "l"(p));
+  return a;
+}
+
 __device__ __forceinline__ U128 add(U128 a, U128 b) {
   add128(a, b.lo, b.hi);
   return a;
@@ -81,10 +91,10 @@ __device__ __forceinline__ void chunk_ids_y(int4 c, uint32_t (&id)[PACKED ? 6 : 
   }
 }
 
-template <bool PACKED>
+template <bool PACKED, int EB>
 __global__ void __launch_bounds__(kYltThreads, 1)
 yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
-            const int64_t *__restrict__ raw_off, int64_t n_trials, const ulonglong2 *__restrict__ table,
+            const int64_t *__restrict__ raw_off, int64_t n_trials, const void *__restrict__ table,
             const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul, int4 sent4, LayerOut L,
             double *__restrict__ yelt, double *__restrict__ occ_max) {
   constexpr int IDS = PACKED ? 6 : 4;
@@ -117,8 +127,12 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       for (int i = 0; i < IDS; ++i) {
         const uint32_t word = s_bm[bitmap_word(id[i], bm_mul)];
         const uint32_t hit = __funnelshift_r(word, word, id[i]) & 1u;
-        const ulonglong2 e = gather_or_zero(table + id[i], hit);
-        x[i] = U128{e.x, e.y};
+        if constexpr (EB == 16) {
+          const ulonglong2 e = gather_or_zero(static_cast<const ulonglong2 *>(table) + id[i], hit);
+          x[i] = U128{e.x, e.y};
+        } else {
+          x[i] = U128{gather_or_zero8(static_cast<const unsigned long long *>(table) + id[i], hit), 0ull};
+        }
         tot = add(tot, x[i]);
       }
       // inclusive scan of the lane totals across the warp
@@ -165,28 +179,39 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
 
 }  // namespace
 
+template <bool PACKED, int EB>
+static cudaError_t launch_yelt_t(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, int64_t n_trials,
+                                 const void *table, const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel,
+                                 const LayerOut &L, double *yelt, double *occ_max, int sms, cudaStream_t s) {
+  const size_t smem = (size_t)bm.words * 4u;
+  cudaError_t err = cudaFuncSetAttribute(yelt_kernel<PACKED, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
+  const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
+  yelt_kernel<PACKED, EB><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table,
+                                                         reinterpret_cast<const uint4 *>(bitmap), bm.words / 4,
+                                                         bm.mul, sent4, L, yelt, occ_max);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
-                        int64_t n_trials, const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                        int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max, int device,
-                        cudaStream_t s) {
+                        int64_t n_trials, const void *table, int entry_bytes, const uint32_t *bitmap,
+                        BitmapLayout bm, int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max,
+                        int device, cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
   int sms = 148;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
-  const size_t smem = (size_t)bm.words * 4u;
-  const void *fn = packed ? (const void *)yelt_kernel<true> : (const void *)yelt_kernel<false>;
-  err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
-  const int4 sent4 = packed ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
-  const uint4 *bm4 = reinterpret_cast<const uint4 *>(bitmap);
-  if (packed)
-    yelt_kernel<true><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table, bm4, bm.words / 4,
-                                                     bm.mul, sent4, L, yelt, occ_max);
-  else
-    yelt_kernel<false><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table, bm4,
-                                                      bm.words / 4, bm.mul, sent4, L, yelt, occ_max);
-  return cudaGetLastError();
+  if (entry_bytes == 16)
+    return packed ? launch_yelt_t<true, 16>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
+                                            occ_max, sms, s)
+                  : launch_yelt_t<false, 16>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
+                                             occ_max, sms, s);
+  return packed ? launch_yelt_t<true, 8>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
+                                         occ_max, sms, s)
+                : launch_yelt_t<false, 8>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
+                                          occ_max, sms, s);
 }
 
 }  // namespace ara

@@ -20,13 +20,17 @@
 //  * The layer's zero-skip bitmap sits in shared memory.  Only occurrences
 //    whose bit is set fetch their table entry (a random 16-byte gather served
 //    by L2, evict-last); the rest add an exact zero and are skipped.
-//  * Table entries are 128-bit fixed-point integers; each lane sums them with
-//    add/add-with-carry, and the warp combines lanes with shuffles.  The
+//  * FP64 layers' table entries are 128-bit fixed-point integers; each lane
+//    sums them with add/add-with-carry, and the warp combines lanes with
+//    shuffles.  FP32-table layers use 64-bit entries on a grid chosen so that
+//    no trial sum reaches 2^64: half the table bytes, so one 32-byte sector
+//    holds an event's entries for four layers.  The
 //    integer sum is exact, so the result does not depend on the order of
 //    the additions or on the launch shape, and B300's low FP64 add rate is
 //    kept off the per-occurrence path.  One correctly rounded conversion to
 //    binary64 per trial precedes the FP64 aggregate clamp.
 #include <cstdlib>
+#include <type_traits>
 
 #include "ara_internal.cuh"
 
@@ -91,62 +95,65 @@ __device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]
 // 32-byte load, i.e. one L2 sector for two layers) and predicated
 // add/add-with-carry, so occurrences whose bitmap bit is clear cost neither a
 // memory request nor register moves.
-#ifndef ARA_GATHER_VARIANT
-#define ARA_GATHER_VARIANT 0
-#endif
+// Accumulators of G layers: 128-bit for 16-byte entries, 64-bit for 8-byte.
+template <int EB, int G>
+struct Acc {
+  U128 v[G];
+};
 template <int G>
-__device__ __forceinline__ void gather_add(U128 (&acc)[G], const ulonglong2 *table, uint32_t id,
-                                           uint32_t hit, unsigned long long pol) {
-#if ARA_GATHER_VARIANT == 0
-  if constexpr (G == 1) {
+struct Acc<8, G> {
+  unsigned long long v[G];
+};
+
+// Adds the table entries of `id` for G layers (EB bytes each, interleaved,
+// EB * G <= 32: one L2 sector) to the accumulators when `hit` is set.  The
+// gather is predicated, so occurrences whose bitmap bit is clear cost no
+// memory request.
+template <int EB, int G>
+__device__ __forceinline__ void gather_add(Acc<EB, G> &acc, const void *table, uint32_t id, uint32_t hit,
+                                           unsigned long long pol) {
+  if constexpr (EB == 16 && G == 1) {
     unsigned long long a = 0ull, b = 0ull;
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %2, 0;\n\t"
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
         "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
         : "+l"(a), "+l"(b)
-        : "r"(hit), "l"(table + id), "l"(pol));
-    add128(acc[0], a, b);
-  } else {
+        : "r"(hit), "l"(static_cast<const ulonglong2 *>(table) + id), "l"(pol));
+    add128(acc.v[0], a, b);
+  } else if constexpr (EB == 16 && G == 2) {
     unsigned long long a = 0ull, b = 0ull, c = 0ull, d = 0ull;
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %4, 0;\n\t"
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
         "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%5], %6;\n\t}"
         : "+l"(a), "+l"(b), "+l"(c), "+l"(d)
-        : "r"(hit), "l"(table + 2 * (size_t)id), "l"(pol));
-    add128(acc[0], a, b);
-    add128(acc[1], c, d);
-  }
-#else
-  if constexpr (G == 1) {
-    unsigned long long a, b;
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %2, 0;\n\t"
+        : "r"(hit), "l"(static_cast<const ulonglong2 *>(table) + 2 * (size_t)id), "l"(pol));
+    add128(acc.v[0], a, b);
+    add128(acc.v[1], c, d);
+  } else if constexpr (EB == 8 && G == 1) {
+    unsigned long long a = 0ull;
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%2], %3;\n\t}"
+        : "+l"(a)
+        : "r"(hit), "l"(static_cast<const unsigned long long *>(table) + id), "l"(pol));
+    acc.v[0] += a;
+  } else if constexpr (EB == 8 && G == 2) {
+    unsigned long long a = 0ull, b = 0ull;
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
         "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
-        : "=l"(a), "=l"(b)
-        : "r"(hit), "l"(table + id), "l"(pol));
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %4, 0;\n\t"
-        "@p add.cc.u64 %0, %0, %2;\n\t"
-        "@p addc.u64 %1, %1, %3;\n\t}"
-        : "+l"(acc[0].lo), "+l"(acc[0].hi)
-        : "l"(a), "l"(b), "r"(hit));
+        : "+l"(a), "+l"(b)
+        : "r"(hit), "l"(static_cast<const unsigned long long *>(table) + 2 * (size_t)id), "l"(pol));
+    acc.v[0] += a;
+    acc.v[1] += b;
   } else {
-    unsigned long long a, b, c, d;
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %4, 0;\n\t"
+    static_assert(EB == 8 && G == 4, "entry width x group must fill at most one 32-byte sector");
+    unsigned long long a = 0ull, b = 0ull, c = 0ull, d = 0ull;
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
         "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%5], %6;\n\t}"
-        : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
-        : "r"(hit), "l"(table + 2 * (size_t)id), "l"(pol));
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %8, 0;\n\t"
-        "@p add.cc.u64 %0, %0, %4;\n\t"
-        "@p addc.u64 %1, %1, %5;\n\t"
-        "@p add.cc.u64 %2, %2, %6;\n\t"
-        "@p addc.u64 %3, %3, %7;\n\t}"
-        : "+l"(acc[0].lo), "+l"(acc[0].hi), "+l"(acc[1].lo), "+l"(acc[1].hi)
-        : "l"(a), "l"(b), "l"(c), "l"(d), "r"(hit));
+        : "+l"(a), "+l"(b), "+l"(c), "+l"(d)
+        : "r"(hit), "l"(static_cast<const unsigned long long *>(table) + 4 * (size_t)id), "l"(pol));
+    acc.v[0] += a;
+    acc.v[1] += b;
+    acc.v[2] += c;
+    acc.v[3] += d;
   }
-#endif
 }
 
 // Sum over the LPT consecutive lanes of a group (LPT a power of two <= 32).
@@ -160,6 +167,13 @@ __device__ __forceinline__ U128 group_sum_u128(U128 v) {
   return v;
 }
 
+template <int LPT>
+__device__ __forceinline__ unsigned long long group_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int m = LPT / 2; m > 0; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+  return v;
+}
+
 template <int G>
 struct GroupOut {
   LayerOut l[G];
@@ -170,10 +184,10 @@ struct GroupOut {
 // one 128-bit accumulator per layer.  A warp sums 32 / LPT consecutive trials
 // side by side, LPT lanes per trial: fewer lanes idle in the last step of a
 // trial, and one group reduction and one epilogue serve 32 / LPT trials.
-template <int U, bool PACKED, int G, int LPT>
+template <int U, bool PACKED, int EB, int G, int LPT>
 __global__ void __launch_bounds__(kYltThreads, 1)
 ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
-                int64_t n_trials, const ulonglong2 *__restrict__ table,
+                int64_t n_trials, const void *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
                 int4 sent4, GroupOut<G> out) {
   constexpr int TPW = 32 / LPT;  // trials per warp step
@@ -225,9 +239,14 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
     int nk_max = nk;
     if constexpr (TPW > 1) nk_max = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)nk);
     const int4 *tp = chunks + p0;
-    U128 acc[G];
+    Acc<EB, G> acc;
 #pragma unroll
-    for (int g = 0; g < G; ++g) acc[g] = U128{0ull, 0ull};
+    for (int g = 0; g < G; ++g) {
+      if constexpr (EB == 16)
+        acc.v[g] = U128{0ull, 0ull};
+      else
+        acc.v[g] = 0ull;
+    }
     // Software-pipelined: the ids of step base + LPT*U are in flight while
     // the current step's bitmap tests and gathers run.
     int4 v[U];
@@ -255,7 +274,7 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
           const uint32_t id = idv[i];
           const uint32_t word = s_bm[bitmap_word(id, bm_mul)];
           const uint32_t hit = __funnelshift_r(word, word, id) & 1u;  // bit id & 31
-          gather_add<G>(acc, table, id, hit, pol_tab);
+          gather_add<EB, G>(acc, table, id, hit, pol_tab);
         }
       }
 #pragma unroll
@@ -263,7 +282,11 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      const U128 sum = group_sum_u128<LPT>(acc[g]);
+      U128 sum;
+      if constexpr (EB == 16)
+        sum = group_sum_u128<LPT>(acc.v[g]);
+      else
+        sum = U128{group_sum_u64<LPT>(acc.v[g]), 0ull};
       const LayerOut &L = out.l[g];
       const double y = trial_loss(sum, L.q, L.af, L.agg_ret, L.agg_lim);
       if (gl == 0 && valid) L.ylt[t] = y;
@@ -271,108 +294,115 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
   }
 }
 
-template <int U, bool PACKED, int G, int LPT>
-static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials,
-                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
-                            cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED, G, LPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cfg.smem);
+template <int U, bool PACKED, int EB, int G, int LPT>
+static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
+                            const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
+                            const YltLaunch &cfg, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED, EB, G, LPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
   if (err != cudaSuccess) return err;
   int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
   const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
   GroupOut<G> go;
   for (int g = 0; g < G; ++g) go.l[g] = outs[g];
-  ylt_fp64_kernel<U, PACKED, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
-      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul,
-      sent4, go);
+  ylt_fp64_kernel<U, PACKED, EB, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
+      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sent4, go);
   return cudaGetLastError();
 }
 
-template <int U, bool PACKED, int G>
-static cudaError_t launch_l(const int64_t *coff, const int4 *chunks, int64_t n_trials,
-                            const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                            int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
-                            cudaStream_t s) {
-  switch (cfg.lanes_per_trial) {
-    case 8: return launch_u<U, PACKED, G, 8>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    case 16: return launch_u<U, PACKED, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    default: return launch_u<U, PACKED, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+// The kernel for (unroll, lanes per trial) as a function pointer and as a
+// launch, for one (PACKED, EB, G).
+template <bool PACKED, int EB, int G>
+struct YltVariants {
+  static const void *fn(int unroll, int lpt) {
+    if (lpt == 16)
+      return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, EB, G, 16>
+                         : (const void *)ylt_fp64_kernel<2, PACKED, EB, G, 16>;
+    return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, EB, G, 32>
+                       : (const void *)ylt_fp64_kernel<2, PACKED, EB, G, 32>;
   }
+  static cudaError_t launch(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
+                            const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
+                            const YltLaunch &cfg, cudaStream_t s) {
+    if (cfg.lanes_per_trial == 16)
+      return cfg.unroll == 1
+                 ? launch_u<1, PACKED, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
+                 : launch_u<2, PACKED, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    return cfg.unroll == 1
+               ? launch_u<1, PACKED, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
+               : launch_u<2, PACKED, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+  }
+};
+
+// Dispatch on (packed, entry bytes, group size) -> F<PACKED, EB, G>.
+template <template <bool, int, int> class F, typename... A>
+static auto dispatch(bool packed, int eb, int G, A... a) {
+  if (eb == 16) {
+    if (G == 2) return packed ? F<true, 16, 2>::call(a...) : F<false, 16, 2>::call(a...);
+    return packed ? F<true, 16, 1>::call(a...) : F<false, 16, 1>::call(a...);
+  }
+  if (G == 4) return packed ? F<true, 8, 4>::call(a...) : F<false, 8, 4>::call(a...);
+  if (G == 2) return packed ? F<true, 8, 2>::call(a...) : F<false, 8, 2>::call(a...);
+  return packed ? F<true, 8, 1>::call(a...) : F<false, 8, 1>::call(a...);
 }
 
-template <bool PACKED, int G>
-static cudaError_t launch_pg(const int64_t *coff, const int4 *chunks, int64_t n_trials,
-                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
-                             int32_t sentinel, const LayerOut *outs, const YltLaunch &cfg,
-                             cudaStream_t s) {
-  switch (cfg.unroll) {
-    case 1: return launch_l<1, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    case 2: return launch_l<2, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    default: return launch_l<4, PACKED, G>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+template <bool PACKED, int EB, int G>
+struct LaunchF {
+  static cudaError_t call(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
+                          const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
+                          const YltLaunch *cfg, cudaStream_t s) {
+    return YltVariants<PACKED, EB, G>::launch(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, *cfg, s);
   }
-}
+};
+
+template <bool PACKED, int EB, int G>
+struct FnF {
+  static const void *call(int unroll, int lpt) { return YltVariants<PACKED, EB, G>::fn(unroll, lpt); }
+};
 
 cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
-                             const ulonglong2 *table, const uint32_t *bitmap, BitmapLayout bm,
+                             const void *table, int entry_bytes, const uint32_t *bitmap, BitmapLayout bm,
                              int32_t sentinel, int G, const LayerOut *outs, const YltLaunch &cfg,
                              cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
-  if (G == 2)
-    return packed ? launch_pg<true, 2>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
-                  : launch_pg<false, 2>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-  return packed ? launch_pg<true, 1>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
-                : launch_pg<false, 1>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+  if (!(entry_bytes == 16 && (G == 1 || G == 2)) && !(entry_bytes == 8 && (G == 1 || G == 2 || G == 4)))
+    return cudaErrorInvalidValue;
+  return dispatch<LaunchF>(packed, entry_bytes, G, coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
+                           &cfg, s);
 }
 
-template <bool PACKED, int G, int LPT>
-static const void *kernel_ptr_l(int unroll) {
-  return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, G, LPT>
-       : unroll == 2 ? (const void *)ylt_fp64_kernel<2, PACKED, G, LPT>
-                     : (const void *)ylt_fp64_kernel<4, PACKED, G, LPT>;
-}
-
-template <bool PACKED, int G>
-static const void *kernel_ptr(int unroll, int lpt) {
-  return lpt == 8 ? kernel_ptr_l<PACKED, G, 8>(unroll)
-       : lpt == 16 ? kernel_ptr_l<PACKED, G, 16>(unroll)
-                   : kernel_ptr_l<PACKED, G, 32>(unroll);
-}
-
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int G,
-                     YltShape hint, YltLaunch *out) {
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int entry_bytes,
+                     int G, YltShape hint, YltLaunch *out) {
+  if (!(entry_bytes == 16 && (G == 1 || G == 2)) && !(entry_bytes == 8 && (G == 1 || G == 2 || G == 4)))
+    return cudaErrorInvalidValue;
   int sms = 0;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
   // Lanes per trial: a group of LPT lanes wastes on average LPT/2 chunk
   // slots in the last step of each trial, and one group reduction plus one
-  // epilogue per warp step serve 32 / LPT trials; too few lanes per trial
-  // leave too few id loads in flight for short trials.
-  // Measured on B300 with 167-chunk trials (Poisson(1000) events, 6 ids a
-  // chunk): 16 lanes per trial beat 32 by 8% and 8 by 23%.
+  // epilogue per warp step serve 32 / LPT trials.  Measured on B300 with
+  // 167-chunk trials (Poisson(1000) events, 6 ids a chunk): 16 lanes per
+  // trial beat 32 by 8% and 8 by 23%.
   int lpt = mean_chunks >= 24.0 ? 16 : 32;
   // Unroll: U chunk loads per lane per step; the loop already keeps the
   // next step's loads in flight, and U = 1 measured as fast as U = 2 with 16
   // lanes per trial (1.06 ms against 1.09 ms for 1e9 occurrences).
   int unroll = 1;
-  if (hint.unroll == 1 || hint.unroll == 2 || hint.unroll == 4) unroll = hint.unroll;
-  if (hint.lanes_per_trial == 8 || hint.lanes_per_trial == 16 || hint.lanes_per_trial == 32)
-    lpt = hint.lanes_per_trial;
+  if (hint.unroll == 1 || hint.unroll == 2) unroll = hint.unroll;
+  if (hint.lanes_per_trial == 16 || hint.lanes_per_trial == 32) lpt = hint.lanes_per_trial;
   if (const char *env = std::getenv("ARA_YLT_UNROLL")) {
     int u = std::atoi(env);
-    if (u == 1 || u == 2 || u == 4) unroll = u;
+    if (u == 1 || u == 2) unroll = u;
   }
   if (const char *env = std::getenv("ARA_YLT_LPT")) {
     int l = std::atoi(env);
-    if (l == 8 || l == 16 || l == 32) lpt = l;
+    if (l == 16 || l == 32) lpt = l;
   }
   out->threads = kYltThreads;
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
   out->lanes_per_trial = lpt;
-  const void *fn = G == 2 ? (packed ? kernel_ptr<true, 2>(unroll, lpt) : kernel_ptr<false, 2>(unroll, lpt))
-                          : (packed ? kernel_ptr<true, 1>(unroll, lpt) : kernel_ptr<false, 1>(unroll, lpt));
+  const void *fn = dispatch<FnF>(packed, entry_bytes, G, unroll, lpt);
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
@@ -383,25 +413,38 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   return cudaSuccess;
 }
 
-// Interleave two layers' tables (entry e of layer a then of layer b, 32 bytes
-// per event) and OR their zero-skip bitmaps, for a two-layer pass.
-__global__ void interleave_kernel(const ulonglong2 *__restrict__ ta, const ulonglong2 *__restrict__ tb,
-                                  int64_t entries, ulonglong2 *__restrict__ out,
-                                  const uint32_t *__restrict__ ba, const uint32_t *__restrict__ bb,
+// Interleave G layers' tables (entry e of layer 0, then of layer 1, ...:
+// EB * G bytes per event, one 32-byte sector for G = 32 / EB) and OR their
+// zero-skip bitmaps, for a G-layer pass.
+template <int EB, int G>
+__global__ void interleave_kernel(Tables4 in, int64_t entries, void *__restrict__ out, Bitmaps4 bin,
                                   int32_t words, uint32_t *__restrict__ bout) {
+  using E = typename std::conditional<EB == 16, ulonglong2, unsigned long long>::type;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  E *o = static_cast<E *>(out);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < entries; e += stride) {
-    out[2 * e] = ta[e];
-    out[2 * e + 1] = tb[e];
+#pragma unroll
+    for (int g = 0; g < G; ++g) o[G * e + g] = static_cast<const E *>(in.t[g])[e];
   }
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride)
-    bout[w] = ba[w] | bb[w];
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride) {
+    uint32_t v = 0u;
+#pragma unroll
+    for (int g = 0; g < G; ++g) v |= bin.b[g][w];
+    bout[w] = v;
+  }
 }
 
-cudaError_t launch_interleave(const ulonglong2 *ta, const ulonglong2 *tb, int64_t entries,
-                              ulonglong2 *out, const uint32_t *ba, const uint32_t *bb,
-                              int32_t words, uint32_t *bout, cudaStream_t s) {
-  interleave_kernel<<<148 * 8, 256, 0, s>>>(ta, tb, entries, out, ba, bb, words, bout);
+cudaError_t launch_interleave(const Tables4 &in, int entry_bytes, int G, int64_t entries, void *out,
+                              const Bitmaps4 &bin, int32_t words, uint32_t *bout, cudaStream_t s) {
+  const dim3 grid(148 * 8), block(256);
+  if (entry_bytes == 16 && G == 2)
+    interleave_kernel<16, 2><<<grid, block, 0, s>>>(in, entries, out, bin, words, bout);
+  else if (entry_bytes == 8 && G == 2)
+    interleave_kernel<8, 2><<<grid, block, 0, s>>>(in, entries, out, bin, words, bout);
+  else if (entry_bytes == 8 && G == 4)
+    interleave_kernel<8, 4><<<grid, block, 0, s>>>(in, entries, out, bin, words, bout);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

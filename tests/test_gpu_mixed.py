@@ -75,3 +75,24 @@ def test_fp32_and_fp64_layers_mix_in_one_batch(engine):
     batch = engine.layers_ylt(hs)
     for i, h in enumerate(hs):
         np.testing.assert_array_equal(batch[i], engine.layer_ylt(h))
+
+
+@pytest.mark.parametrize("n_layers", [3, 9])
+def test_fp32_layers_four_per_pass(engine, n_layers):
+    """FP32-table layers go four to a YET pass (4 x 8-byte entries = one L2
+    sector): every grouping (4 + 4 + 1, 2 + 1) gives the single-layer bits."""
+    from paper_1412_4556_b300 import ARA_FP32_TABLE
+    w = S.batched(n_layers=n_layers, n_trials=2_500, lam=150.0, catalog_size=120_000, n_pool=30)
+    engine.load_yet_from(w.yet)
+    first = engine.load_pool(w.pool)
+    hs = [engine.define_layer([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim,
+                              precision=ARA_FP32_TABLE) for L in w.layers]
+    batch = engine.layers_ylt(hs)
+    for i, (h, lay) in enumerate(zip(hs, w.layers)):
+        single = engine.layer_ylt(h)
+        np.testing.assert_array_equal(batch[i].view(np.uint64), single.view(np.uint64))
+        o, pre = oracle.layer_ylt(w.yet, w.pool, lay, mode="memo")
+        assert_reduced_parity(single, o, pre, what=f"layer {i}")
+    rev = engine.layers_ylt(hs[::-1], n_trials=777)
+    for i, h in enumerate(hs[::-1]):
+        np.testing.assert_array_equal(rev[i], batch[hs.index(h)][:777])

@@ -176,12 +176,14 @@ def test_result_independent_of_launch_shape(engine, monkeypatch):
     w = S.paper_scale(n_trials=3_000, catalog_size=300_000)
     (L,) = load_workload(engine, w)
     ref = None
-    for u in ("1", "2", "4", "8"):
-        monkeypatch.setenv("ARA_YLT_UNROLL", u)
-        g = engine.layer_ylt(L)
-        if ref is None:
-            ref = g.copy()
-        np.testing.assert_array_equal(g.view(np.uint64), ref.view(np.uint64))
+    for u in ("1", "2"):
+        for lpt in ("16", "32"):
+            monkeypatch.setenv("ARA_YLT_UNROLL", u)
+            monkeypatch.setenv("ARA_YLT_LPT", lpt)
+            g = engine.layer_ylt(L)
+            if ref is None:
+                ref = g.copy()
+            np.testing.assert_array_equal(g.view(np.uint64), ref.view(np.uint64))
 
 
 def test_device_buffers_and_streams(engine):
