@@ -285,6 +285,49 @@ ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const doub
                                         int32_t n_rp, double *pml_out, double *tvar_out,
                                         void *cuda_stream);
 
+/* ------------------------------------------------------------ pricing plans */
+/*
+ * A plan prices a fixed list of layers (Section III: a Program or Portfolio
+ * is a set of Layers) as one CUDA graph: every layer's ELT fold (the
+ * pre-pass of ara_define_layer), the grouped passes of ara_layers_ylt over
+ * the first n_trials trials, and the PML/TVaR selection of
+ * ara_pml_tvar_batch.  ara_plan_run replays it with one graph launch and
+ * gives the same values as those calls.  With autotune != 0, plan creation
+ * first times the YLT kernel's launch shapes (lanes per trial -- the trials a
+ * warp sums side by side -- and id loads per lane) on the plan's own layers
+ * and the first min(n_trials, 2^20) trials, and keeps the fastest for this
+ * plan and for later ara_layers_ylt / ara_layer_ylt calls on the context.
+ * The plan owns its output buffers.  A plan stops working (ARA_E_STATE from
+ * ara_plan_run) when the YET is reloaded or one of its layers is released;
+ * ara_destroy destroys the context's plans.
+ */
+typedef struct ara_plan ara_plan;
+
+/* layers: n_layers handles (1..65535); return_periods: double[n_rp] (host,
+ * 1..16 values, floor(n_trials / RP) >= 1).  Errors: ARA_E_INVALID_ARG,
+ * ARA_E_NOT_FOUND, ARA_E_STATE (no YET, or a service owns the context),
+ * ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_plan_create(ara_ctx *ctx, const int32_t *layers, int32_t n_layers, int64_t n_trials,
+                                   const double *return_periods, int32_t n_rp, int32_t autotune,
+                                   ara_plan **out);
+
+/* Replay the plan on cuda_stream (NULL = the context's stream).
+ *   ylt_out   NULL, or double[n_layers][n_trials] (host or device)
+ *   pml_out, tvar_out  NULL, or double[n_layers][n_rp] (host)
+ * Returns once the outputs are written (host outputs), or once the work is
+ * queued (device or no outputs).  Errors: ARA_E_STATE, ARA_E_CUDA. */
+ARA_API ara_status ara_plan_run(ara_plan *plan, double *ylt_out, double *pml_out, double *tvar_out,
+                                void *cuda_stream);
+
+/* The plan's YLT passes: *n_passes receives their number and, for the first
+ * max_passes, info[5*i .. 5*i+4] = entry bytes (16 FP64, 8 FP32-table),
+ * layers in the pass, lanes per trial, id loads per lane, and the position
+ * in the plan's layer list of the pass's first layer. */
+ARA_API ara_status ara_plan_passes(const ara_plan *plan, int32_t max_passes, int32_t *info,
+                                   int32_t *n_passes);
+
+ARA_API void ara_plan_destroy(ara_plan *plan);
+
 /* ---------------------------------------------------------- pricing service */
 /*
  * Ad hoc pricing (Section I: an underwriter quotes a contract while on the

@@ -22,7 +22,7 @@ from . import _native
 from ._native import (ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_FOLD, ARA_TIMING_PML, ARA_TIMING_YLT,
                       AraError)
 
-__all__ = ["Engine", "Service", "ServiceResult", "AraError", "ARA_FP64", "ARA_FP32_TABLE",
+__all__ = ["Engine", "Plan", "Service", "ServiceResult", "AraError", "ARA_FP64", "ARA_FP32_TABLE",
            "ARA_TIMING_YLT", "ARA_TIMING_FOLD", "ARA_TIMING_PML"]
 
 
@@ -54,6 +54,7 @@ class Engine:
         self.ctx = _native.ara_create(device)
         self.device = device
         self._service = None
+        self._plans = []
         self.catalog_size = 0
         self.n_trials = 0
         if stream is not None:
@@ -63,6 +64,8 @@ class Engine:
     def close(self) -> None:
         if self._service is not None:
             self._service.close()
+        for p in list(self._plans):
+            p.close()
         if self.ctx:
             _native.ara_destroy(self.ctx)
             self.ctx = 0
@@ -220,6 +223,50 @@ class Engine:
     def kernel_timing(self, channel: int = ARA_TIMING_YLT):
         """(launches, total milliseconds) recorded on a timing channel."""
         return _native.ara_kernel_timing(self.ctx, channel)
+
+
+class Plan:
+    """A fixed list of layers priced as one CUDA graph (see ``ara_plan_create``)."""
+
+    def __init__(self, engine: Engine, layers: Sequence[int], return_periods: Sequence[float],
+                 n_trials: Optional[int] = None, autotune: bool = True):
+        h = np.ascontiguousarray(layers, dtype=np.int32)
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        self.engine = engine
+        self.n_layers = int(h.shape[0])
+        self.n_trials = engine.n_trials if n_trials is None else int(n_trials)
+        self.n_rp = int(rps.shape[0])
+        self.plan = _native.ara_plan_create(engine.ctx, self.n_layers, h.ctypes.data, self.n_trials,
+                                            rps.ctypes.data, self.n_rp, autotune)
+        engine._plans.append(self)
+
+    def run(self, ylt_out=None, stream=None, want_pml: bool = True):
+        """Replay: (pml, tvar) arrays [n_layers, n_rp] (None with want_pml=False);
+        ``ylt_out`` (NumPy array or CUDA tensor [n_layers, n_trials]) receives the YLTs."""
+        p, keep = _arg(ylt_out, np.float64, "ylt_out")
+        if ylt_out is not None and keep is not ylt_out:
+            raise TypeError("ylt_out must be a contiguous float64 array or tensor")
+        pml = np.zeros((self.n_layers, self.n_rp)) if want_pml else None
+        tvar = np.zeros((self.n_layers, self.n_rp)) if want_pml else None
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+        _native.ara_plan_run(self.engine.ctx, self.plan, p, pml.ctypes.data if want_pml else 0,
+                             tvar.ctypes.data if want_pml else 0, int(handle or 0))
+        return pml, tvar
+
+    def passes(self):
+        return _native.ara_plan_passes(self.engine.ctx, self.plan)
+
+    def close(self) -> None:
+        if self.plan:
+            _native.ara_plan_destroy(self.plan)
+            self.plan = 0
+            self.engine._plans.remove(self)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class ServiceResult:

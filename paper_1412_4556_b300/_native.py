@@ -80,6 +80,10 @@ PROTOTYPES = {
     "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
     "ara_layer_yelt": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
     "ara_rpl_report": (_i32, [_vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "ara_plan_create": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i32, C.POINTER(C.c_void_p)]),
+    "ara_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "ara_plan_passes": (_i32, [_vp, _i32, _vp, C.POINTER(_i32)]),
+    "ara_plan_destroy": (None, [_vp]),
     "ara_service_create": (_i32, [_vp, C.POINTER(ServiceConfig), C.POINTER(C.c_void_p)]),
     "ara_service_submit": (_i32, [_vp, C.POINTER(Request), C.POINTER(_i64)]),
     "ara_service_wait": (_i32, [_vp, _i64, _f64, C.POINTER(Result)]),
@@ -209,6 +213,32 @@ def ara_rpl_report(ctx: int, layer: int, n_trials: int, return_periods: int, n_r
                    aep_tvar: int, oep: int, oep_tvar: int) -> None:
     _check(ctx, lib.ara_rpl_report(ctx, int(layer), int(n_trials), return_periods or None, int(n_rp),
                                    aep or None, aep_tvar or None, oep or None, oep_tvar or None))
+
+
+def ara_plan_create(ctx: int, n_layers: int, layers: int, n_trials: int, return_periods: int, n_rp: int,
+                    autotune: bool) -> int:
+    out = C.c_void_p()
+    _check(ctx, lib.ara_plan_create(ctx, layers or None, int(n_layers), int(n_trials), return_periods or None,
+                                    int(n_rp), 1 if autotune else 0, C.byref(out)))
+    return out.value
+
+
+def ara_plan_run(ctx: int, plan: int, ylt_out: int, pml_out: int, tvar_out: int, stream: int = 0) -> None:
+    """(ctx is the plan's context, for the error message.)"""
+    _check(ctx, lib.ara_plan_run(plan, ylt_out or None, pml_out or None, tvar_out or None, stream or None))
+
+
+def ara_plan_passes(ctx: int, plan: int):
+    """List of (entry bytes, layers, lanes per trial, unroll, first layer) per YLT pass."""
+    n = _i32(0)
+    _check(ctx, lib.ara_plan_passes(plan, 0, None, C.byref(n)))
+    info = (_i32 * (5 * max(n.value, 1)))()
+    _check(ctx, lib.ara_plan_passes(plan, n.value, info, C.byref(n)))
+    return [tuple(info[5 * i:5 * i + 5]) for i in range(n.value)]
+
+
+def ara_plan_destroy(plan: int) -> None:
+    lib.ara_plan_destroy(plan)
 
 
 def ara_set_kernel_timing(ctx: int, enable: bool) -> None:

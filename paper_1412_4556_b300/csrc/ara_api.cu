@@ -179,6 +179,21 @@ AggFixed agg_terms_fixed(double agg_ret, double agg_lim, int q) {
   return af;
 }
 
+ara_status enqueue_fold(ara_ctx *c, const LayerRec &L, cudaStream_t s) {
+  ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
+  // The sentinel entry (id = catalog) must read zero at this layer's entry
+  // width; a buffer used before at the other width may hold data there.
+  ARA_CUDA(c, cudaMemsetAsync(reinterpret_cast<unsigned char *>(L.d_table) + (size_t)c->catalog * L.entry_bytes(), 0,
+                              (size_t)L.entry_bytes(), s),
+           "cudaMemsetAsync(sentinel entry)");
+  TimedLaunch tl(c, ARA_TIMING_FOLD, s);
+  ARA_CUDA(c, launch_fold(L.d_desc, (int)L.elts.size(), c->catalog, L.occ_ret, L.occ_lim, L.q,
+                          L.d_table, L.d_bitmap, L.bm, L.precision == ARA_FP32_TABLE, nullptr, s),
+           "fold kernel launch");
+  tl.done();
+  return ARA_OK;
+}
+
 ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
   int q = 0;
   if (!choose_q(L.upper, std::max<int64_t>(c->max_trial_len, 1), L.entry_bytes() * 8 - 1, &q))
@@ -201,17 +216,8 @@ ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s) {
   }
   L.q = q;
   L.agg_fx = agg_terms_fixed(L.agg_ret, L.agg_lim, q);
-  ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
-  // The sentinel entry (id = catalog) must read zero at this layer's entry
-  // width; a buffer used before at the other width may hold data there.
-  ARA_CUDA(c, cudaMemsetAsync(reinterpret_cast<unsigned char *>(L.d_table) + (size_t)c->catalog * L.entry_bytes(), 0,
-                              (size_t)L.entry_bytes(), s),
-           "cudaMemsetAsync(sentinel entry)");
-  TimedLaunch tl(c, ARA_TIMING_FOLD, s);
-  ARA_CUDA(c, launch_fold(L.d_desc, (int)L.elts.size(), c->catalog, L.occ_ret, L.occ_lim, q,
-                          L.d_table, L.d_bitmap, L.bm, L.precision == ARA_FP32_TABLE, nullptr, s),
-           "fold kernel launch");
-  tl.done();
+  ara_status st = enqueue_fold(c, L, s);
+  if (st) return st;
   L.folded_version = c->yet_version;
   return ARA_OK;
 }
@@ -397,6 +403,7 @@ ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, d
     id = (int32_t)c->layers.size();
     c->layers.emplace_back();
   }
+  L.gen = ++c->layer_gen;
   c->layers[(size_t)id] = L;
   *layer_out = id;
   return ARA_OK;
@@ -446,7 +453,7 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
         bitmap = pair_bitmap;
       }
       YltLaunch cfg;
-      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, eb, G, c->tuned[G == 4 ? 3 : G], &cfg),
+      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, eb, G, c->tuned[eb == 8 ? 1 : 0][G], &cfg),
                "plan YLT launch");
       TimedLaunch tl(c, ARA_TIMING_YLT, s);
       ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, eb, bitmap, bm, c->catalog,
@@ -526,6 +533,7 @@ ara_status ara_create(ara_ctx **out, int device) {
 void ara_destroy(ara_ctx *c) {
   if (!c) return;
   if (c->service) ara_service_destroy(c->service);
+  while (!c->plans.empty()) ara_plan_destroy(c->plans.back());
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &L : c->layers) free_layer(L);
@@ -819,7 +827,7 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
   }
   const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, L->entry_bytes(), 1, c->tuned[1], &cfg),
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, L->entry_bytes(), 1, c->tuned[L->entry_bytes() == 8 ? 1 : 0][1], &cfg),
            "plan YLT launch");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst};
   TimedLaunch tl(c, ARA_TIMING_YLT, s);

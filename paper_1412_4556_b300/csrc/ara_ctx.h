@@ -26,6 +26,7 @@ struct EltMeta {
 
 struct LayerRec {
   bool live = false;
+  uint64_t gen = 0;  // distinct for every definition (plans detect redefinition)
   std::vector<int32_t> elts;
   double occ_ret = 0, occ_lim = 0, agg_ret = 0, agg_lim = 0;
   int32_t precision = ARA_FP64;
@@ -79,6 +80,7 @@ struct ara_ctx {
   std::string err;
   // YET
   int64_t yet_version = 0;
+  uint64_t layer_gen = 0;           // last LayerRec::gen handed out
   bool yet_loaded = false;
   int32_t catalog = 0;
   int64_t n_trials = 0;
@@ -121,7 +123,7 @@ struct ara_ctx {
   size_t cap_pair_table = 0;
   uint32_t *d_pair_bitmap = nullptr;        // union of their bitmaps
   size_t cap_pair_bitmap = 0;
-  ara::YltShape tuned[4];                   // YLT launch shape picked by the autotuner, per G (3: G = 4)
+  ara::YltShape tuned[2][5];                // YLT launch shape chosen by the autotuner: [entry 8 B][G]
   unsigned long long *d_counter = nullptr;  // validation counters
   unsigned int *d_err = nullptr;            // PML/TVaR input check flag
   // timing
@@ -129,6 +131,8 @@ struct ara_ctx {
   TimingChannel chan[3];
   // pricing service that owns the context while attached (service.cu)
   ara_service *service = nullptr;
+  // live pricing plans (plan.cu), destroyed with the context
+  std::vector<ara_plan *> plans;
   size_t pool_max = ara::kLayerPoolMax;     // released layers kept for reuse
 };
 
@@ -161,6 +165,9 @@ cudaError_t ensure(T **buf, size_t *cap, size_t count) {
 ara_status fail_free(ara_status st, const char *fmt, ...);
 
 ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s);
+// The device work of fold_layer for a layer whose buffers exist and whose
+// grid (q) is set: queue only memsets and the fold kernel (stream capture).
+ara_status enqueue_fold(ara_ctx *c, const LayerRec &L, cudaStream_t s);
 void recycle_layer(ara_ctx *c, LayerRec &L);
 ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out);
 // Fill the pool with buffers for `count` layers of the loaded catalog (within

@@ -1,0 +1,318 @@
+// Pricing plans: the whole batched step for a fixed list of layers -- every
+// layer's ELT fold, the grouped YLT passes over the YET and the batched
+// PML/TVaR selection -- captured once into a CUDA graph and replayed with one
+// launch (Section III: a Program or Portfolio is a set of Layers, each priced
+// by Algorithm 1).  Before capture an optional autotuner times the YLT
+// kernel's launch shapes (lanes per trial, i.e. trials summed side by side
+// per warp, and id loads per lane) on the plan's own layers and trials, and
+// the captured passes use the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ara.h"
+#include "ara_ctx.h"
+#include "ara_internal.cuh"
+
+using namespace ara;
+
+struct ara_plan {
+  ara_ctx *c = nullptr;
+  std::vector<int32_t> layers;
+  std::vector<uint64_t> gens;
+  int64_t n_trials = 0;
+  int64_t yet_version = -1;
+  int32_t n_rp = 0;
+  int64_t k[kMaxReturnPeriods] = {};
+  cudaStream_t cap = nullptr;  // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double *d_ylt = nullptr;           // [n_layers][n_trials]
+  ulonglong2 *d_pair = nullptr;      // interleaved tables of one pass
+  uint32_t *d_pair_bm = nullptr;     // their union bitmap
+  unsigned char *d_ws = nullptr;     // selection state per layer
+  double *d_out = nullptr;           // PML then TVaR per layer
+  unsigned int *d_err = nullptr;
+  double *h_out = nullptr;           // pinned copy of d_out
+  unsigned int *h_err = nullptr;     // pinned copy of d_err
+  std::vector<int32_t> pass_info;    // 5 per pass: entry bytes, layers, lanes per trial, unroll, first layer
+};
+
+namespace {
+
+void free_plan(ara_plan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap) {
+    cudaStreamSynchronize(p->cap);
+    cudaStreamDestroy(p->cap);
+  }
+  cudaFree(p->d_ylt);
+  cudaFree(p->d_pair);
+  cudaFree(p->d_pair_bm);
+  cudaFree(p->d_ws);
+  cudaFree(p->d_out);
+  cudaFree(p->d_err);
+  cudaFreeHost(p->h_out);
+  cudaFreeHost(p->h_err);
+  cudaGetLastError();
+  delete p;
+}
+
+// The passes ara_layers_ylt makes for these layers: FP64 layers two at a
+// time, FP32-table layers four at a time (groups of three split 2 + 1).
+struct Pass {
+  int eb;
+  std::vector<int32_t> idx;  // positions in the plan's layer list
+};
+
+std::vector<Pass> group_passes(ara_ctx *c, const std::vector<int32_t> &layers) {
+  std::vector<Pass> out;
+  for (const int eb : {16, 8}) {
+    std::vector<int32_t> idx;
+    for (size_t i = 0; i < layers.size(); ++i)
+      if (c->layers[(size_t)layers[i]].entry_bytes() == eb) idx.push_back((int32_t)i);
+    const int gmax = 32 / eb;
+    for (size_t p = 0; p < idx.size();) {
+      int G = (int)std::min<size_t>((size_t)gmax, idx.size() - p);
+      if (G == 3) G = 2;
+      out.push_back(Pass{eb, std::vector<int32_t>(idx.begin() + (long)p, idx.begin() + (long)p + G)});
+      p += (size_t)G;
+    }
+  }
+  return out;
+}
+
+// Time the YLT kernel of one pass in every launch shape on the first n trials
+// and keep the fastest in the context (ara_layers_ylt then uses it too).
+ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
+  ara_ctx *c = p->c;
+  const int G = (int)ps.idx.size();
+  LayerOut outs[4];
+  Tables4 tabs{};
+  Bitmaps4 bms{};
+  for (int g = 0; g < G; ++g) {
+    const LayerRec &L = c->layers[(size_t)p->layers[(size_t)ps.idx[(size_t)g]]];
+    outs[g] = LayerOut{L.q, L.agg_fx, L.agg_ret, L.agg_lim, p->d_ylt + (size_t)g * (size_t)n};
+    tabs.t[g] = L.d_table;
+    bms.b[g] = L.d_bitmap;
+  }
+  const BitmapLayout bm = c->layers[(size_t)p->layers[(size_t)ps.idx[0]]].bm;
+  const void *table = tabs.t[0];
+  const uint32_t *bitmap = bms.b[0];
+  if (G > 1) {
+    ARA_CUDA(c, launch_interleave(tabs, ps.eb, G, (int64_t)c->catalog + 1, p->d_pair, bms, bm.words, p->d_pair_bm,
+                                  p->cap),
+             "interleave layer tables");
+    table = p->d_pair;
+    bitmap = p->d_pair_bm;
+  }
+  const double mean_chunks = (double)c->h_coff[(size_t)n] / (double)n;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ARA_CUDA(c, cudaEventCreate(&a), "cudaEventCreate");
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cuda_fail(c, e, "cudaEventCreate");
+  }
+  YltShape best{};
+  float best_ms = 1e30f;
+  for (const int lpt : {16, 32})
+    for (const int unroll : {1, 2}) {
+      YltShape hint;
+      hint.lanes_per_trial = lpt;
+      hint.unroll = unroll;
+      YltLaunch cfg;
+      e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, hint, &cfg);
+      float ms = 1e30f;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first run warms L2 and the clocks
+        e = cudaEventRecord(a, p->cap);
+        if (e == cudaSuccess)
+          e = launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n, table, ps.eb, bitmap, bm, c->catalog, G,
+                               outs, cfg, p->cap);
+        if (e == cudaSuccess) e = cudaEventRecord(b, p->cap);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e == cudaSuccess && rep > 0) ms = std::min(ms, t);
+      }
+      if (e != cudaSuccess) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = YltShape{cfg.unroll, cfg.lanes_per_trial};
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune YLT launch shapes");
+  c->tuned[ps.eb == 8 ? 1 : 0][G] = best;
+  return ARA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, int64_t n_trials,
+                           const double *rps, int32_t n_rp, int32_t autotune, ara_plan **out) {
+  if (out) *out = nullptr;
+  if (!c || !out) return fail_free(ARA_E_INVALID_ARG, "NULL argument");
+  if (c->service) return fail_free(ARA_E_STATE, "the context is attached to a pricing service");
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  if (n_layers < 1 || n_layers > 65535 || !layers) return fail(c, ARA_E_INVALID_ARG, "need 1..65535 layer handles");
+  if (n_trials < 1 || n_trials > c->n_trials)
+    return fail(c, ARA_E_INVALID_ARG, "n_trials %lld outside [1, %lld]", (long long)n_trials, (long long)c->n_trials);
+  ara_plan *p = new ara_plan();
+  p->c = c;
+  p->n_trials = n_trials;
+  p->n_rp = n_rp;
+  if (tail_counts(n_trials, rps, n_rp, p->k) != ARA_OK) {
+    delete p;
+    return fail(c, ARA_E_INVALID_ARG, "%s", ara_last_error(nullptr));
+  }
+  for (int32_t i = 0; i < n_layers; ++i) {
+    LayerRec *L = nullptr;
+    ara_status st = get_layer(c, layers[i], &L);
+    if (st) {
+      delete p;
+      return st;
+    }
+    p->layers.push_back(layers[i]);
+    p->gens.push_back(L->gen);
+  }
+  auto bail = [&](ara_status st) {
+    free_plan(p);
+    return st;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+  // Layers not yet folded for this YET are folded now (their grids are set
+  // here; the graph re-runs the folds with the same grids).
+  for (const int32_t h : p->layers) {
+    LayerRec &L = c->layers[(size_t)h];
+    if (L.folded_version != c->yet_version) {
+      ara_status st = fold_layer(c, L, c->stream);
+      if (st) return bail(st);
+    }
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamSynchronize"));
+  p->yet_version = c->yet_version;
+  const size_t nl = (size_t)n_layers;
+  const BitmapLayout bm = c->layers[(size_t)p->layers[0]].bm;
+  if ((e = cudaMalloc(&p->d_ylt, nl * (size_t)n_trials * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_pair, 2 * ((size_t)c->catalog + 1) * sizeof(ulonglong2))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_pair_bm, (size_t)bm.words * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_ws, nl * select_workspace_bytes(kMaxReturnPeriods))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_out, nl * 2 * (size_t)n_rp * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_out, nl * 2 * (size_t)n_rp * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_err, sizeof(unsigned int))) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(c, ARA_E_NOMEM, "plan buffers: %s", cudaGetErrorString(e)));
+  }
+  const std::vector<Pass> passes = group_passes(c, p->layers);
+  if (autotune) {
+    const int64_t n_tune = std::min<int64_t>(n_trials, 1 << 20);
+    bool seen[2][5] = {};
+    for (const Pass &ps : passes) {
+      const int G = (int)ps.idx.size();
+      if (seen[ps.eb == 8][G]) continue;
+      seen[ps.eb == 8][G] = true;
+      ara_status st = tune_pass(p, ps, n_tune);
+      if (st) return bail(st);
+    }
+  }
+  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
+  for (const Pass &ps : passes) {
+    const int G = (int)ps.idx.size();
+    YltLaunch cfg;
+    e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, c->tuned[ps.eb == 8][G], &cfg);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "plan YLT launch"));
+    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, ps.idx[0]});
+  }
+  // Capture: folds, grouped YLT passes, batched selection, result copies.
+  const bool timing = c->timing;
+  c->timing = false;
+  e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+  ara_status st = e == cudaSuccess ? ARA_OK : cuda_fail(c, e, "cudaStreamBeginCapture");
+  for (size_t i = 0; i < nl && st == ARA_OK; ++i) st = enqueue_fold(c, c->layers[(size_t)p->layers[i]], p->cap);
+  if (st == ARA_OK)
+    st = layers_ylt_on(c, p->layers.data(), n_layers, n_trials, p->d_ylt, p->cap, p->d_pair, p->d_pair_bm);
+  if (st == ARA_OK && (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), p->cap)) != cudaSuccess)
+    st = cuda_fail(c, e, "cudaMemsetAsync");
+  if (st == ARA_OK && (e = launch_pml_tvar_batch(p->d_ylt, n_layers, n_trials, p->k, n_rp, p->d_ws, p->d_out,
+                                                  p->d_err, c->device, p->cap)) != cudaSuccess)
+    st = cuda_fail(c, e, "PML/TVaR kernels");
+  if (st == ARA_OK && (e = cudaMemcpyAsync(p->h_out, p->d_out, nl * 2 * (size_t)n_rp * sizeof(double),
+                                           cudaMemcpyDeviceToHost, p->cap)) != cudaSuccess)
+    st = cuda_fail(c, e, "copy PML/TVaR");
+  if (st == ARA_OK && (e = cudaMemcpyAsync(p->h_err, p->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                           p->cap)) != cudaSuccess)
+    st = cuda_fail(c, e, "copy flag");
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(p->cap, &g);
+  c->timing = timing;
+  if (st == ARA_OK && e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamEndCapture");
+  p->graph = g;
+  if (st != ARA_OK) return bail(st);
+  e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGraphInstantiate"));
+  c->plans.push_back(p);
+  *out = p;
+  return ARA_OK;
+}
+
+ara_status ara_plan_run(ara_plan *p, double *ylt_out, double *pml_out, double *tvar_out, void *cuda_stream) {
+  if (!p) return fail_free(ARA_E_INVALID_ARG, "NULL plan");
+  ara_ctx *c = p->c;
+  if (c->service) return fail_free(ARA_E_STATE, "the context is attached to a pricing service");
+  c->err.clear();
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->yet_version != p->yet_version) return fail(c, ARA_E_STATE, "the YET was reloaded after the plan was made");
+  for (size_t i = 0; i < p->layers.size(); ++i) {
+    const int32_t h = p->layers[i];
+    if (h >= (int32_t)c->layers.size() || !c->layers[(size_t)h].live || c->layers[(size_t)h].gen != p->gens[i])
+      return fail(c, ARA_E_STATE, "layer %d was released or redefined after the plan was made", h);
+  }
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+  ARA_CUDA(c, cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
+  const size_t total = p->layers.size() * (size_t)p->n_trials;
+  if (ylt_out)
+    ARA_CUDA(c, cudaMemcpyAsync(ylt_out, p->d_ylt, total * sizeof(double), cudaMemcpyDefault, s), "copy YLTs");
+  if (pml_out || tvar_out || (ylt_out && !is_device_ptr(ylt_out))) {
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (*p->h_err) return fail(c, ARA_E_INVALID_ARG, "trial losses must be finite and >= 0");
+    const int32_t n_rp = p->n_rp;
+    for (size_t l = 0; l < p->layers.size(); ++l)
+      for (int32_t r = 0; r < n_rp; ++r) {
+        if (pml_out) pml_out[l * (size_t)n_rp + (size_t)r] = p->h_out[l * 2 * (size_t)n_rp + (size_t)r];
+        if (tvar_out) tvar_out[l * (size_t)n_rp + (size_t)r] = p->h_out[l * 2 * (size_t)n_rp + (size_t)(n_rp + r)];
+      }
+  }
+  return ARA_OK;
+}
+
+ara_status ara_plan_passes(const ara_plan *p, int32_t max_passes, int32_t *info, int32_t *n_passes) {
+  if (!p || !n_passes) return fail_free(ARA_E_INVALID_ARG, "NULL argument");
+  const int32_t n = (int32_t)(p->pass_info.size() / 5);
+  *n_passes = n;
+  if (info)
+    for (int32_t i = 0; i < std::min(n, max_passes); ++i)
+      for (int j = 0; j < 5; ++j) info[5 * i + j] = p->pass_info[(size_t)(5 * i + j)];
+  return ARA_OK;
+}
+
+void ara_plan_destroy(ara_plan *p) {
+  if (!p) return;
+  ara_ctx *c = p->c;
+  cudaSetDevice(c->device);
+  c->plans.erase(std::remove(c->plans.begin(), c->plans.end(), p), c->plans.end());
+  free_plan(p);
+}
+
+}  // extern "C"
