@@ -223,3 +223,31 @@ def test_context_is_owned_while_attached_and_checks_at_submit(workload):
         submit(svc, first, rq, 0)
     e.close()
     assert svc.svc == 0
+
+
+def test_service_full_size_requests_sampled():
+    """Config 4 shapes at full size: requests over 1e5 / 2.5e5 / 1e6-trial
+    prefixes of the paper-scale YET with the 256-ELT pool, FP32 tables, all
+    submitted at once; sampled trials against the oracle; and each result
+    equals the same request priced alone."""
+    from paper_1412_4556_b300 import ARA_FP32_TABLE, Engine, Service
+    w = S.batched(n_layers=1)
+    reqs = S.service_requests(n_requests=24, rate_per_s=1000.0)
+    with Engine(0) as e:
+        e.load_yet_from(w.yet)
+        first = e.load_pool(w.pool)
+        with Service(e, RPS, slots=4, max_batch=8) as svc:
+            tickets = [submit(svc, first, rq, ARA_FP32_TABLE, want_ylt=(i % 6 == 0)) for i, rq in enumerate(reqs)]
+            mixed = [svc.wait(t) for t in tickets]
+            alone = [svc.wait(submit(svc, first, reqs[i], ARA_FP32_TABLE, want_ylt=True)) for i in range(0, 24, 6)]
+    assert all(r.ok for r in mixed + alone)
+    rng = np.random.default_rng(6)
+    for a, i in zip(alone, range(0, 24, 6)):
+        m = mixed[i]
+        np.testing.assert_array_equal(m.ylt.view(np.uint64), a.ylt.view(np.uint64))
+        np.testing.assert_array_equal(m.pml, a.pml)
+        rq = reqs[i]
+        sel = np.sort(rng.choice(rq.n_trials, 300, replace=False))
+        o, pre = oracle.layer_ylt(w.yet, w.pool, rq.layer, trials=sel, mode="memo")
+        err = np.abs(m.ylt[sel] - o)
+        assert np.all(err <= np.maximum(1e-5 * np.maximum(np.abs(o), pre), 1.0)), f"request {i}"
