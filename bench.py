@@ -570,6 +570,8 @@ def run_service(args):
         if bad:
             raise RuntimeError(f"{len(bad)} requests failed: {bad[0].status_name} {bad[0].message}")
         lat = np.array([r.latency for r in res]) * 1e3
+        queue_ms = np.array([r.t_start - r.t_submit for r in res]) * 1e3
+        run_ms = np.array([r.t_done - r.t_start for r in res]) * 1e3
         span = max(r.t_done for r in res) - min(r.t_submit for r in res)
         occ = sum(int(w.yet.offsets[rq.n_trials]) for rq in reqs)
         by_n = {}
@@ -583,6 +585,8 @@ def run_service(args):
             "requests_per_s": len(res) / span, "layer_trial_events_per_s": occ / span,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "mean_batch": float(np.mean([r.batch_size for r in res])),
+            "queue_p50_ms": float(np.percentile(queue_ms, 50)), "queue_p99_ms": float(np.percentile(queue_ms, 99)),
+            "run_p50_ms": float(np.percentile(run_ms, 50)), "run_p99_ms": float(np.percentile(run_ms, 99)),
             "max_batch": st["max_batch_seen"], "max_in_flight": st["max_in_flight"],
             "max_slots_busy": st["max_slots_busy"], "max_device_bytes_in_flight": st["max_bytes_in_flight"],
         }
