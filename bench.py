@@ -505,8 +505,8 @@ def run_batched(args):
         "ylt_kernels_ms_per_step": ylt_b,
         "ylt_kernels_note": "CUDA events around the YLT launches of ara_layers_ylt (the graph replays the "
                             "same kernels in the same shapes)",
-        "passes": [{"entry_bytes": eb, "layers": g, "lanes_per_trial": lpt, "unroll": u}
-                   for eb, g, lpt, u, _ in passes],
+        "passes": [{"entry_bytes": eb, "layers": g, "lanes_per_trial": lpt, "unroll": u, "l2_prefetch": pf}
+                   for eb, g, lpt, u, pf, _ in passes],
         "calls_per_step": {"ms_per_step": ms_b, "ylt_kernels_ms_per_step": ylt_b,
                            "value": G * M / (ms_b / 1e3),
                            "step": "64 x ara_define_layer + ara_layers_ylt + ara_pml_tvar_batch"},

@@ -294,7 +294,8 @@ ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const doub
  * ara_pml_tvar_batch.  ara_plan_run replays it with one graph launch and
  * gives the same values as those calls.  With autotune != 0, plan creation
  * first times the YLT kernel's launch shapes (lanes per trial -- the trials a
- * warp sums side by side -- and id loads per lane) on the plan's own layers
+ * warp sums side by side --, id loads per lane, and whether the id stream is
+ * prefetched into L2) on the plan's own layers
  * and the first min(n_trials, 2^20) trials, and keeps the fastest for this
  * plan and for later ara_layers_ylt / ara_layer_ylt calls on the context.
  * The plan owns its output buffers.  A plan stops working (ARA_E_STATE from
@@ -320,9 +321,9 @@ ARA_API ara_status ara_plan_run(ara_plan *plan, double *ylt_out, double *pml_out
                                 void *cuda_stream);
 
 /* The plan's YLT passes: *n_passes receives their number and, for the first
- * max_passes, info[5*i .. 5*i+4] = entry bytes (16 FP64, 8 FP32-table),
- * layers in the pass, lanes per trial, id loads per lane, and the position
- * in the plan's layer list of the pass's first layer. */
+ * max_passes, info[6*i .. 6*i+5] = entry bytes (16 FP64, 8 FP32-table),
+ * layers in the pass, lanes per trial, id loads per lane, L2 prefetch (1/0),
+ * and the position in the plan's layer list of the pass's first layer. */
 ARA_API ara_status ara_plan_passes(const ara_plan *plan, int32_t max_passes, int32_t *info,
                                    int32_t *n_passes);
 

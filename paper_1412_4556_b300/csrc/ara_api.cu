@@ -453,7 +453,8 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
         bitmap = pair_bitmap;
       }
       YltLaunch cfg;
-      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, eb, G, c->tuned[eb == 8 ? 1 : 0][G], &cfg),
+      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, eb, G, entries * (size_t)(eb * G),
+                           c->tuned[eb == 8 ? 1 : 0][G], &cfg),
                "plan YLT launch");
       TimedLaunch tl(c, ARA_TIMING_YLT, s);
       ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, eb, bitmap, bm, c->catalog,
@@ -827,7 +828,9 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
   }
   const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, L->entry_bytes(), 1, c->tuned[L->entry_bytes() == 8 ? 1 : 0][1], &cfg),
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, L->entry_bytes(), 1,
+                       ((size_t)c->catalog + 1) * (size_t)L->entry_bytes(),
+                       c->tuned[L->entry_bytes() == 8 ? 1 : 0][1], &cfg),
            "plan YLT launch");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst};
   TimedLaunch tl(c, ARA_TIMING_YLT, s);

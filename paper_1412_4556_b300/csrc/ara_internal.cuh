@@ -227,13 +227,15 @@ struct YltLaunch {
   int threads;
   size_t smem;
   int unroll;           // 16-byte id loads in flight per lane
-  int lanes_per_trial;  // 8, 16 or 32: a warp sums 32 / lanes_per_trial trials at once
+  int lanes_per_trial;  // 16 or 32: a warp sums 32 / lanes_per_trial trials at once
+  int prefetch;         // 1: bulk-prefetch the next trials' ids into L2
 };
 
 // Launch-shape choice for the YLT kernel (0 = the planner's default).
 struct YltShape {
   int unroll = 0;
   int lanes_per_trial = 0;
+  int prefetch = -1;  // 0 off, 1 on, -1 the planner's choice
 };
 
 // Per-layer constants and output of one YLT kernel launch.
@@ -257,10 +259,11 @@ cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packe
                              cudaStream_t s);
 
 // Pick the launch shape of the YLT kernel for a bitmap of bm.words words and
-// trials of mean_chunks 16-byte chunks; non-zero fields of hint force the
-// unroll (1/2) or the lanes per trial (16/32).  entry_bytes x G <= 32.
+// trials of mean_chunks 16-byte chunks and a (possibly interleaved) table of
+// table_bytes; fields of hint force the unroll (1/2), the lanes per trial
+// (16/32) or the L2 prefetch (0/1).  entry_bytes x G <= 32.
 cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int entry_bytes,
-                     int G, YltShape hint, YltLaunch *out);
+                     int G, size_t table_bytes, YltShape hint, YltLaunch *out);
 
 // Up to four layers' tables and bitmaps for launch_interleave.
 struct Tables4 {

@@ -4,8 +4,8 @@
 // launch (Section III: a Program or Portfolio is a set of Layers, each priced
 // by Algorithm 1).  Before capture an optional autotuner times the YLT
 // kernel's launch shapes (lanes per trial, i.e. trials summed side by side
-// per warp, and id loads per lane) on the plan's own layers and trials, and
-// the captured passes use the fastest.
+// per warp, id loads per lane, and the L2 prefetch of the id stream) on the
+// plan's own layers and trials, and the captured passes use the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,7 +37,7 @@ struct ara_plan {
   unsigned int *d_err = nullptr;
   double *h_out = nullptr;           // pinned copy of d_out
   unsigned int *h_err = nullptr;     // pinned copy of d_err
-  std::vector<int32_t> pass_info;    // 5 per pass: entry bytes, layers, lanes per trial, unroll, first layer
+  std::vector<int32_t> pass_info;    // 6 per pass: entry bytes, layers, lanes per trial, unroll, prefetch, first layer
 };
 
 namespace {
@@ -117,15 +117,18 @@ ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
     cudaEventDestroy(a);
     return cuda_fail(c, e, "cudaEventCreate");
   }
+  const size_t table_bytes = ((size_t)c->catalog + 1) * (size_t)(ps.eb * G);
   YltShape best{};
   float best_ms = 1e30f;
   for (const int lpt : {16, 32})
-    for (const int unroll : {1, 2}) {
+    for (const int unroll : {1, 2})
+      for (const int prefetch : {0, 1}) {
       YltShape hint;
       hint.lanes_per_trial = lpt;
       hint.unroll = unroll;
+      hint.prefetch = prefetch;
       YltLaunch cfg;
-      e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, hint, &cfg);
+      e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, table_bytes, hint, &cfg);
       float ms = 1e30f;
       for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first run warms L2 and the clocks
         e = cudaEventRecord(a, p->cap);
@@ -141,7 +144,7 @@ ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
       if (e != cudaSuccess) break;
       if (ms < best_ms) {
         best_ms = ms;
-        best = YltShape{cfg.unroll, cfg.lanes_per_trial};
+        best = YltShape{cfg.unroll, cfg.lanes_per_trial, cfg.prefetch};
       }
     }
   cudaEventDestroy(a);
@@ -231,9 +234,10 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
   for (const Pass &ps : passes) {
     const int G = (int)ps.idx.size();
     YltLaunch cfg;
-    e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, c->tuned[ps.eb == 8][G], &cfg);
+    e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, ((size_t)c->catalog + 1) * (size_t)(ps.eb * G),
+                 c->tuned[ps.eb == 8][G], &cfg);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "plan YLT launch"));
-    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, ps.idx[0]});
+    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch, ps.idx[0]});
   }
   // Capture: folds, grouped YLT passes, batched selection, result copies.
   const bool timing = c->timing;
@@ -299,11 +303,11 @@ ara_status ara_plan_run(ara_plan *p, double *ylt_out, double *pml_out, double *t
 
 ara_status ara_plan_passes(const ara_plan *p, int32_t max_passes, int32_t *info, int32_t *n_passes) {
   if (!p || !n_passes) return fail_free(ARA_E_INVALID_ARG, "NULL argument");
-  const int32_t n = (int32_t)(p->pass_info.size() / 5);
+  const int32_t n = (int32_t)(p->pass_info.size() / 6);
   *n_passes = n;
   if (info)
     for (int32_t i = 0; i < std::min(n, max_passes); ++i)
-      for (int j = 0; j < 5; ++j) info[5 * i + j] = p->pass_info[(size_t)(5 * i + j)];
+      for (int j = 0; j < 6; ++j) info[6 * i + j] = p->pass_info[(size_t)(6 * i + j)];
   return ARA_OK;
 }
 

@@ -12,7 +12,7 @@
 //  * One warp per trial; each warp owns a contiguous run of trials, so the
 //    YET id stream is read once, in 16-byte coalesced loads, U loads in flight
 //    per lane, with an evict-first L2 policy; one lane bulk-prefetches the
-//    next trial into L2.  The engine stores every trial as whole 16-byte
+//    next trials into L2 (when the table leaves L2 room for it).  The engine stores every trial as whole 16-byte
 //    chunks (4 plain ids, or 6 ids of 21 bits when the catalog allows, which
 //    cuts the id stream by a third), padded with a sentinel event whose table
 //    entry is zero, so each chunk belongs to one trial and no per-event
@@ -66,8 +66,11 @@ __device__ __forceinline__ ulonglong2 ld_entry(const ulonglong2 *p, unsigned lon
 
 // One bulk copy-engine request pulls a whole trial's ids (a contiguous,
 // 16-byte aligned run) into L2, so the warp's own loads of that trial hit L2.
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+// The prefetched lines carry the id stream's evict-first policy, so the
+// stream does not push the layer tables out of L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes, unsigned long long pol) {
+  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(bytes), "l"(pol)
+               : "memory");
 }
 
 // The ids of one 16-byte chunk: four plain 32-bit ids, or six 21-bit ids
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kYltThreads, 1)
 ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
                 int64_t n_trials, const void *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
-                int4 sent4, GroupOut<G> out) {
+                int4 sent4, GroupOut<G> out, int do_prefetch) {
   constexpr int TPW = 32 / LPT;  // trials per warp step
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
@@ -216,7 +219,7 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
   int64_t fa = 0, fb = 0;  // lane 0: chunk range prefetched at the top of the next step
   if (lane == 0 && t_begin < t_end) {
     const int64_t a = coff[t_begin], b = coff[min(t_begin + TPW, t_end)];
-    if (b > a) prefetch_l2(chunks + a, (uint32_t)((b - a) * 16));
+    if (b > a && do_prefetch) prefetch_l2(chunks + a, (uint32_t)((b - a) * 16), pol_ids);
     fa = b;
     fb = coff[min(t_begin + 2 * TPW, t_end)];
   }
@@ -232,7 +235,7 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
     }
     // While these trials are summed, the next ones' ids travel to L2.
     if (lane == 0) {
-      if (fb > fa) prefetch_l2(chunks + fa, (uint32_t)((fb - fa) * 16));
+      if (fb > fa && do_prefetch) prefetch_l2(chunks + fa, (uint32_t)((fb - fa) * 16), pol_ids);
       fa = fb;
       fb = coff[min(t0 + 3 * TPW, t_end)];
     }
@@ -306,7 +309,8 @@ static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_t
   GroupOut<G> go;
   for (int g = 0; g < G; ++g) go.l[g] = outs[g];
   ylt_fp64_kernel<U, PACKED, EB, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
-      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sent4, go);
+      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sent4, go,
+      cfg.prefetch);
   return cudaGetLastError();
 }
 
@@ -372,7 +376,7 @@ cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packe
 }
 
 cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int entry_bytes,
-                     int G, YltShape hint, YltLaunch *out) {
+                     int G, size_t table_bytes, YltShape hint, YltLaunch *out) {
   if (!(entry_bytes == 16 && (G == 1 || G == 2)) && !(entry_bytes == 8 && (G == 1 || G == 2 || G == 4)))
     return cudaErrorInvalidValue;
   int sms = 0;
@@ -388,6 +392,12 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   // next step's loads in flight, and U = 1 measured as fast as U = 2 with 16
   // lanes per trial (1.06 ms against 1.09 ms for 1e9 occurrences).
   int unroll = 1;
+  // L2 bulk prefetch of the next trials' ids: measured on B300 it takes the
+  // one-layer kernel from 1.30 to 1.06 ms (32 MB table), but with a 64 MB
+  // interleaved table (two FP64 or four FP32-table layers) the prefetched ids
+  // push table lines out of L2 and turning it off saves 10-14%.
+  int prefetch = table_bytes <= (size_t)40 << 20 ? 1 : 0;
+  if (hint.prefetch == 0 || hint.prefetch == 1) prefetch = hint.prefetch;
   if (hint.unroll == 1 || hint.unroll == 2) unroll = hint.unroll;
   if (hint.lanes_per_trial == 16 || hint.lanes_per_trial == 32) lpt = hint.lanes_per_trial;
   if (const char *env = std::getenv("ARA_YLT_UNROLL")) {
@@ -402,6 +412,7 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
   out->lanes_per_trial = lpt;
+  out->prefetch = prefetch;
   const void *fn = dispatch<FnF>(packed, entry_bytes, G, unroll, lpt);
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;

@@ -47,7 +47,7 @@ def test_plan_equals_direct_calls(engine, autotune):
         passes = plan.passes()
     # 4 FP64 layers -> 2 passes of 2; 3 FP32-table layers -> 2 + 1
     assert sorted((eb, g) for eb, g, *_ in passes) == [(8, 1), (8, 2), (16, 2), (16, 2)]
-    assert all(lpt in (16, 32) and u in (1, 2) for _, _, lpt, u, _ in passes)
+    assert all(lpt in (16, 32) and u in (1, 2) and pf in (0, 1) for _, _, lpt, u, pf, _ in passes)
     for i, (lay, p) in enumerate(zip(w.layers, precs)):
         if p == ARA_FP64 and i < 3:
             o, pre = oracle.layer_ylt(w.yet, w.pool, lay, mode="memo")
