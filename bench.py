@@ -116,9 +116,14 @@ class ClockSampler:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         lo, hi = self.window
-        for ts, ln in self.lines:
-            if not (lo <= ts <= hi):
-                continue
+        inside = [x for x in self.lines if lo <= x[0] <= hi]
+        nearest = False
+        if not inside and self.lines and lo > 0.0:
+            # a timed region shorter than the 200 ms sampling period: take the
+            # samples read within 0.3 s after it (they cover its last moments)
+            inside = [x for x in self.lines if lo <= x[0] <= hi + 0.3]
+            nearest = bool(inside)
+        for ts, ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -132,8 +137,11 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if nearest:
+            out["note"] = "timed region shorter than the sampling period; samples from just after it"
+        return out
 
 
 # -------------------------------------------------------------- roofline
