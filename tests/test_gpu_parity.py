@@ -295,3 +295,39 @@ def test_paper_scale_full_size_sampled(paper_full):
         k = int(math.floor(g.size / r))
         assert p == s[k - 1]
         assert t == pytest.approx(math.fsum(s[:k]) / k, rel=1e-13)
+
+
+@pytest.mark.parametrize("catalog", [(1 << 21) - 1, 1 << 21])
+def test_packing_boundary_catalogs(engine, catalog):
+    """The largest catalog whose ids (and the sentinel) pack into 21 bits, and
+    the smallest that does not: both layouts give the oracle's YLT."""
+    pool = _custom_pool(catalog, [40_000, 25_000, 5], 8)
+    hot = [0, catalog - 1, catalog - 2] + [int(x) for x in pool.ids[:20]]
+    yet = _custom_yet(catalog, LENGTHS * 4, 17, hot)
+    engine.load_yet_from(yet)
+    first = engine.load_pool(pool)
+    lay = S.Layer([0, 1, 2], 1e3, 5e6, 1e4, 1e8)
+    L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret, lay.agg_lim)
+    o, pre = oracle.layer_ylt(yet, pool, lay, mode="memo")
+    assert_fp64_parity(engine.layer_ylt(L), o, pre)
+
+
+def test_layer_with_the_most_elts(engine):
+    """A layer over 1,024 ELTs (the limit): the fold stays bit-identical to the
+    oracle's ELT loop and the YLT matches; 1,025 ELTs are refused."""
+    from paper_1412_4556_b300 import AraError
+    catalog = 60_000
+    pool = _custom_pool(catalog, [25 + (j % 17) for j in range(1025)], 9)
+    yet = _custom_yet(catalog, LENGTHS * 2, 19)
+    engine.load_yet_from(yet)
+    first = engine.load_pool(pool)
+    order = list(np.random.default_rng(2).permutation(1024))
+    lay = S.Layer([int(j) for j in order], 2e3, 1e7, 5e4, 2e8)
+    L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret, lay.agg_lim)
+    np.testing.assert_array_equal(engine.event_table(L).view(np.uint64),
+                                  oracle.event_table(catalog, pool, lay).view(np.uint64))
+    o, pre = oracle.layer_ylt(yet, pool, lay, mode="memo")
+    assert_fp64_parity(engine.layer_ylt(L), o, pre)
+    with pytest.raises(AraError) as ei:
+        engine.define_layer(list(range(first, first + 1025)), 0.0, math.inf, 0.0, math.inf)
+    assert ei.value.name == "ARA_E_INVALID_ARG"
