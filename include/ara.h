@@ -138,6 +138,8 @@ ARA_API ara_status ara_load_yet(ara_ctx *ctx, int32_t catalog_size, int64_t n_tr
  *   limits      double[n_elts]: >= 0; +inf means "no limit"
  *   first_elt_handle (out): handle of the first new ELT; the others follow
  *               contiguously.  Handles stay valid until ara_destroy.
+ * The entries are checked, and grouped for the fold, on the device; one call
+ * takes at most 2^31 - 1 entries.
  * Requires a loaded YET (ARA_E_STATE otherwise).  Errors:
  * ARA_E_INVALID_ARG, ARA_E_EVENT_RANGE, ARA_E_DUP_EVENT, ARA_E_NOMEM,
  * ARA_E_CUDA; on error no ELT of the call is added. */

@@ -547,6 +547,7 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_ts);
   cudaFree(c->d_ylt_stage);
   cudaFree(c->d_yelt_stage);
+  cudaFree(c->d_elt_scratch);
   cudaFree(c->d_sel_in);
   cudaFree(c->d_sel_ws);
   cudaFree(c->d_sel_out);
@@ -684,72 +685,86 @@ ara_status ara_load_elts(ara_ctx *c, int32_t n_elts, const int64_t *off, const i
   }
   const int64_t total = off[n_elts];
   if (total > 0 && (!ids || !losses)) return fail(c, ARA_E_INVALID_ARG, "event_ids/losses NULL");
-  // Sort each ELT by event id, reject duplicates, build the fold buckets.
-  std::vector<int32_t> s_ids((size_t)total);
-  std::vector<double> s_loss((size_t)total);
-  std::vector<int32_t> bucket;
-  std::vector<size_t> bucket_start((size_t)n_elts);
-  std::vector<EltMeta> meta((size_t)n_elts);
-  std::vector<int64_t> perm;
-  for (int32_t j = 0; j < n_elts; ++j) {
-    const int64_t a = off[j], b = off[j + 1], n = b - a;
-    perm.resize((size_t)n);
-    std::iota(perm.begin(), perm.end(), a);
-    for (int64_t i = a; i < b; ++i) {
-      if (ids[i] < 0 || ids[i] >= c->catalog)
-        return fail(c, ARA_E_EVENT_RANGE, "ELT %d: event id %d outside [0, %d)", j, ids[i], c->catalog);
-      if (!finite_nonneg(losses[i]))
-        return fail(c, ARA_E_INVALID_ARG, "ELT %d: loss at position %lld must be finite and >= 0", j,
-                    (long long)(i - a));
-    }
-    std::sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
-    double mx = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-      s_ids[(size_t)(a + i)] = ids[perm[(size_t)i]];
-      s_loss[(size_t)(a + i)] = losses[perm[(size_t)i]];
-      mx = std::max(mx, s_loss[(size_t)(a + i)]);
-      if (i > 0 && s_ids[(size_t)(a + i)] == s_ids[(size_t)(a + i - 1)])
-        return fail(c, ARA_E_DUP_EVENT, "ELT %d: event id %d appears twice", j, s_ids[(size_t)(a + i)]);
-    }
-    EltMeta &m = meta[(size_t)j];
-    m.count = (int32_t)n;
-    m.deductible = ded[j];
-    m.limit = lim[j];
-    m.max_loss = mx;
-    m.max_id = n ? s_ids[(size_t)(b - 1)] : -1;
-    m.nb = n ? m.max_id / kFoldEventsPerCta + 1 : 0;
-    bucket_start[(size_t)j] = bucket.size();
-    int64_t i = 0;
-    for (int32_t bk = 0; bk <= m.nb; ++bk) {
-      const int64_t lo = (int64_t)bk * kFoldEventsPerCta;
-      while (i < n && s_ids[(size_t)(a + i)] < lo) ++i;
-      bucket.push_back((int32_t)i);
-    }
-  }
-  // One device block: ids | losses | buckets (8-byte aligned sections).
-  const size_t n_ids_b = ((size_t)total * 4 + 7) / 8 * 8;
+  if (total > ((int64_t)1 << 31) - 1)
+    return fail(c, ARA_E_INVALID_ARG, "one call loads at most 2^31-1 ELT entries (got %lld)", (long long)total);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  // The entries go to the device as given; the device checks them, groups
+  // each ELT by fold bucket and finds each ELT's largest loss and id.
+  const int nb = (c->catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
+  const size_t nbk = (size_t)n_elts * (size_t)(nb + 1);
+  const int64_t seen_words = ((int64_t)c->catalog + 31) / 32;
+  const size_t n_ids_b = ((size_t)total * 4 + 15) / 16 * 16;
   const size_t n_loss_b = (size_t)total * 8;
-  const size_t n_bk_b = bucket.size() * 4;
+  const size_t n_bk_b = nbk * 4;
+  // scratch: raw ids | raw losses | offsets | seen bits | counts | cursors | maxima | error counts
+  const size_t sc_ids = 0, sc_loss = sc_ids + n_ids_b, sc_off = sc_loss + (n_loss_b + 15) / 16 * 16;
+  const size_t sc_seen = sc_off + ((size_t)(n_elts + 1) * 8 + 15) / 16 * 16;
+  const size_t sc_cnt = sc_seen + ((size_t)n_elts * (size_t)seen_words * 4 + 15) / 16 * 16;
+  const size_t sc_cur = sc_cnt + (nbk * 4 + 15) / 16 * 16;
+  const size_t sc_maxl = sc_cur + (nbk * 4 + 15) / 16 * 16;
+  const size_t sc_maxi = sc_maxl + (size_t)n_elts * 8;
+  const size_t sc_bad = sc_maxi + ((size_t)n_elts * 4 + 15) / 16 * 16;
+  const size_t sc_total = sc_bad + 3 * 8;
+  ARA_CUDA(c, ensure(&c->d_elt_scratch, &c->cap_elt_scratch, sc_total), "ELT ingest scratch");
+  unsigned char *sc = c->d_elt_scratch;
   char *blk = nullptr;
-  ARA_CUDA(c, cudaMalloc(&blk, std::max<size_t>(n_ids_b + n_loss_b + n_bk_b, 8)), "cudaMalloc(ELT pool)");
+  ARA_CUDA(c, cudaMalloc(&blk, std::max<size_t>(n_ids_b + n_loss_b + n_bk_b, 16)), "cudaMalloc(ELT pool)");
   cudaStream_t s = c->stream;
-  cudaError_t e = cudaMemcpyAsync(blk, s_ids.data(), (size_t)total * 4, cudaMemcpyHostToDevice, s);
+  std::vector<unsigned long long> h_maxl((size_t)n_elts);
+  std::vector<int> h_maxi((size_t)n_elts);
+  unsigned long long h_bad[3] = {0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(sc + sc_off, off, (size_t)(n_elts + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && total > 0)
+    e = cudaMemcpyAsync(sc + sc_ids, ids, (size_t)total * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && total > 0)
+    e = cudaMemcpyAsync(sc + sc_loss, losses, (size_t)total * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + sc_seen, 0, sc_cnt - sc_seen, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + sc_cnt, 0, sc_cur - sc_cnt, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + sc_maxl, 0, (size_t)n_elts * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + sc_maxi, 0xFF, (size_t)n_elts * 4, s);  // -1
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + sc_bad, 0, 3 * 8, s);
+  int32_t *d_bucket = reinterpret_cast<int32_t *>(blk + n_ids_b + n_loss_b);
+  if (e == cudaSuccess && total == 0) e = cudaMemsetAsync(d_bucket, 0, n_bk_b, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(blk + n_ids_b, s_loss.data(), n_loss_b, cudaMemcpyHostToDevice, s);
+    e = launch_elt_ingest(reinterpret_cast<const int64_t *>(sc + sc_off), n_elts, total,
+                          reinterpret_cast<const int32_t *>(sc + sc_ids), reinterpret_cast<const double *>(sc + sc_loss),
+                          c->catalog, nb, reinterpret_cast<uint32_t *>(sc + sc_seen), seen_words,
+                          reinterpret_cast<int32_t *>(sc + sc_cnt), reinterpret_cast<int32_t *>(sc + sc_cur), d_bucket,
+                          reinterpret_cast<unsigned long long *>(sc + sc_maxl), reinterpret_cast<int *>(sc + sc_maxi),
+                          reinterpret_cast<unsigned long long *>(sc + sc_bad), reinterpret_cast<int32_t *>(blk),
+                          reinterpret_cast<double *>(blk + n_ids_b), s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(blk + n_ids_b + n_loss_b, bucket.data(), n_bk_b, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(h_maxl.data(), sc + sc_maxl, (size_t)n_elts * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_maxi.data(), sc + sc_maxi, (size_t)n_elts * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_bad, sc + sc_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaFree(blk);
     return cuda_fail(c, e, "upload ELTs");
   }
+  if (h_bad[0] || h_bad[1] || h_bad[2]) {
+    cudaFree(blk);
+    if (h_bad[0]) return fail(c, ARA_E_EVENT_RANGE, "%llu ELT event ids lie outside [0, %d)", h_bad[0], c->catalog);
+    if (h_bad[2]) return fail(c, ARA_E_DUP_EVENT, "%llu event ids repeat within an ELT", h_bad[2]);
+    return fail(c, ARA_E_INVALID_ARG, "%llu ELT losses are not finite and >= 0", h_bad[1]);
+  }
   c->elt_blocks.push_back(blk);
   *first_handle = (int32_t)c->elts.size();
   for (int32_t j = 0; j < n_elts; ++j) {
-    EltMeta m = meta[(size_t)j];
+    EltMeta m;
+    m.count = (int32_t)(off[j + 1] - off[j]);
+    m.deductible = ded[j];
+    m.limit = lim[j];
+    unsigned long long bits = h_maxl[(size_t)j];
+    double mx = 0.0;
+    std::memcpy(&mx, &bits, sizeof(mx));
+    m.max_loss = mx;
+    m.max_id = h_maxi[(size_t)j];
+    m.nb = m.count ? nb : 0;
     m.d_ids = reinterpret_cast<const int32_t *>(blk) + off[j];
     m.d_losses = reinterpret_cast<const double *>(blk + n_ids_b) + off[j];
-    m.d_bucket = reinterpret_cast<const int32_t *>(blk + n_ids_b + n_loss_b) + bucket_start[(size_t)j];
+    m.d_bucket = d_bucket + (size_t)j * (size_t)(nb + 1);
     c->elts.push_back(m);
   }
   return ARA_OK;

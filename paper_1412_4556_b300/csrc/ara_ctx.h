@@ -111,6 +111,8 @@ struct ara_ctx {
   size_t cap_ylt_stage = 0;
   double *d_yelt_stage = nullptr;           // per-occurrence output for host callers
   size_t cap_yelt_stage = 0;
+  unsigned char *d_elt_scratch = nullptr;   // ELT ingest: raw entries, counts, checks
+  size_t cap_elt_scratch = 0;
   double *d_sel_in = nullptr;
   size_t cap_sel_in = 0;
   void *d_sel_ws = nullptr;

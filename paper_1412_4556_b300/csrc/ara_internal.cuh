@@ -275,6 +275,18 @@ struct Bitmaps4 {
 cudaError_t launch_interleave(const Tables4 &in, int entry_bytes, int G, int64_t entries, void *out,
                               const Bitmaps4 &bin, int32_t words, uint32_t *bout, cudaStream_t s);
 
+// ELT ingest (ingest.cu): check the entries of n_elts ELTs (CSR by d_off,
+// device), group each ELT by fold bucket into s_ids / s_losses (same CSR) and
+// write the bucket index bucket[j][0..nb]; per ELT the largest loss (as
+// binary64 bits) and id; bad[0..2] count ids outside the catalog, losses not
+// finite and >= 0, and ids repeated within an ELT.  seen, count and the
+// maxima start zeroed (max_id at -1).
+cudaError_t launch_elt_ingest(const int64_t *d_off, int n_elts, int64_t total, const int32_t *d_raw_ids,
+                              const double *d_raw_losses, int32_t catalog, int nb, uint32_t *seen,
+                              int64_t seen_words, int32_t *count, int32_t *cursor, int32_t *bucket,
+                              unsigned long long *max_loss, int *max_id, unsigned long long *bad,
+                              int32_t *s_ids, double *s_losses, cudaStream_t s);
+
 cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *coff,
                            int64_t n_trials, int4 *dst, int32_t catalog, bool packed,
                            unsigned long long *bad_count, cudaStream_t s);
