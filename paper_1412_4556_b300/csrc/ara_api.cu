@@ -587,28 +587,65 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
     return fail(c, ARA_E_INVALID_ARG, "n_trials out of range (got %lld)", (long long)n_trials);
   if (!offsets) return fail(c, ARA_E_INVALID_ARG, "trial_offsets is NULL");
   cudaStream_t s = c->stream;
-  // Offsets: validated on the host (a device array is brought back first).
+  // The id copy (the bulk of the bytes) starts first; the offsets are
+  // checked and the chunk layout computed on the host while it runs.
+  const bool dev_off = is_device_ptr(offsets);
+  int64_t M_claimed = 0;
+  if (dev_off) {
+    ARA_CUDA(c, cudaMemcpyAsync(&M_claimed, offsets + n_trials, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+             "copy trial_offsets");
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  } else {
+    M_claimed = offsets[n_trials];
+  }
+  if (M_claimed < 0) return fail(c, ARA_E_INVALID_ARG, "trial_offsets[n_trials] must be >= 0");
+  if (M_claimed > 0 && !ids)
+    return fail(c, ARA_E_INVALID_ARG, "event_ids is NULL but offsets hold %lld events", (long long)M_claimed);
+  // The ids go to a staging buffer the loaded YET does not use, so a failed
+  // check below still leaves the previous YET loaded.
+  const bool dev_ids = M_claimed > 0 && is_device_ptr(ids);
+  if (M_claimed > 0 && !dev_ids) {
+    ARA_CUDA(c, ensure(&c->d_raw, &c->cap_raw, (size_t)M_claimed), "allocate YET buffers");
+    ARA_CUDA(c, cudaMemcpyAsync(c->d_raw, ids, (size_t)M_claimed * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+             "copy event_ids");
+  }
   std::vector<int64_t> h((size_t)n_trials + 1);
-  ARA_CUDA(c, cudaMemcpyAsync(h.data(), offsets, h.size() * sizeof(int64_t), cudaMemcpyDefault, s),
-           "copy trial_offsets");
-  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
-  if (h[0] != 0) return fail(c, ARA_E_INVALID_ARG, "trial_offsets[0] must be 0");
+  if (dev_off) {
+    ARA_CUDA(c, cudaMemcpyAsync(h.data(), offsets, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+             "copy trial_offsets");
+    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  } else {
+    std::memcpy(h.data(), offsets, h.size() * sizeof(int64_t));
+  }
+  // Errors below wait for the id copy before returning (the caller may free ids).
+  auto fail_sync = [&](ara_status st, const char *msg) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return fail(c, st, "%s", msg);
+  };
+  if (h[0] != 0) return fail_sync(ARA_E_INVALID_ARG, "trial_offsets[0] must be 0");
   int64_t lmax = 0;
   for (int64_t t = 0; t < n_trials; ++t) {
     const int64_t d = h[t + 1] - h[t];
-    if (d < 0) return fail(c, ARA_E_INVALID_ARG, "trial_offsets decreases at trial %lld", (long long)t);
+    if (d < 0) {
+      char msg[128];
+      snprintf(msg, sizeof(msg), "trial_offsets decreases at trial %lld", (long long)t);
+      return fail_sync(ARA_E_INVALID_ARG, msg);
+    }
     lmax = std::max(lmax, d);
   }
   const int64_t M = h[n_trials];
+  if (M != M_claimed) return fail_sync(ARA_E_INVALID_ARG, "trial_offsets changed while being read");
   if (lmax > ((int64_t)1 << 31) - 1024)
-    return fail(c, ARA_E_INVALID_ARG, "a trial holds %lld events; at most 2^31-1024 are supported",
-                (long long)lmax);
-  if (M > 0 && !ids) return fail(c, ARA_E_INVALID_ARG, "event_ids is NULL but offsets hold %lld events", (long long)M);
+    return fail_sync(ARA_E_INVALID_ARG, "a trial holds more than 2^31-1024 events");
   // ELTs already loaded must still fit the new catalog.
   for (size_t j = 0; j < c->elts.size(); ++j)
-    if (c->elts[j].max_id >= catalog)
-      return fail(c, ARA_E_EVENT_RANGE, "loaded ELT %zu holds event id %d outside the new catalog of %d",
-                  j, c->elts[j].max_id, catalog);
+    if (c->elts[j].max_id >= catalog) {
+      char msg[160];
+      snprintf(msg, sizeof(msg), "loaded ELT %zu holds event id %d outside the new catalog of %d", j,
+               c->elts[j].max_id, catalog);
+      return fail_sync(ARA_E_EVENT_RANGE, msg);
+    }
   // Chunked layout: every trial rounded up to whole 16-byte chunks.
   const bool packed = catalog <= kPackedIdLimit;
   const int64_t ipc = packed ? 6 : 4;
@@ -621,21 +658,18 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
   // failure leaves the context without a YET.
   c->yet_loaded = false;
   c->yet_version++;
-  const bool dev_ids = M > 0 && is_device_ptr(ids);
   cudaError_t e = ensure(&c->d_offsets, &c->cap_offsets, (size_t)n_trials + 1);
   if (e == cudaSuccess) e = ensure(&c->d_coff, &c->cap_coff, (size_t)n_trials + 1);
   if (e == cudaSuccess) e = ensure(&c->d_chunks, &c->cap_chunks, (size_t)Mc + kChunkTail);
-  if (e == cudaSuccess && M > 0 && !dev_ids) e = ensure(&c->d_raw, &c->cap_raw, (size_t)M);
   if (e == cudaSuccess && ts) e = ensure(&c->d_ts, &c->cap_ts, (size_t)std::max<int64_t>(M, 1));
-  if (e != cudaSuccess) return cuda_fail(c, e, "allocate YET buffers");
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    return cuda_fail(c, e, "allocate YET buffers");
+  }
   e = cudaMemcpyAsync(c->d_offsets, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_coff, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  const int32_t *src = ids;
-  if (e == cudaSuccess && M > 0 && !dev_ids) {
-    e = cudaMemcpyAsync(c->d_raw, ids, (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    src = c->d_raw;
-  }
+  const int32_t *src = (M > 0 && !dev_ids) ? c->d_raw : ids;
   if (e == cudaSuccess && ts && M > 0)
     e = cudaMemcpyAsync(c->d_ts, ts, (size_t)M * sizeof(float), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, 2 * sizeof(unsigned long long), s);

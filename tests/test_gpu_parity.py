@@ -331,3 +331,29 @@ def test_layer_with_the_most_elts(engine):
     with pytest.raises(AraError) as ei:
         engine.define_layer(list(range(first, first + 1025)), 0.0, math.inf, 0.0, math.inf)
     assert ei.value.name == "ARA_E_INVALID_ARG"
+
+
+def test_rejected_yet_keeps_the_previous_one(engine):
+    """Offsets that fail their checks (found while the ids are being copied)
+    leave the loaded YET and its layers usable; ids outside the catalog,
+    found on the device after the copy, leave no YET."""
+    from paper_1412_4556_b300 import AraError
+    w = S.tiny()
+    (L,) = load_workload(engine, w)
+    ref = engine.layer_ylt(L)
+    bad = w.yet.offsets.copy()
+    bad[5], bad[6] = bad[6], bad[5] - 1  # decreasing
+    with pytest.raises(AraError) as ei:
+        engine.load_yet(w.yet.catalog_size, bad, w.yet.ids)
+    assert ei.value.name == "ARA_E_INVALID_ARG"
+    np.testing.assert_array_equal(engine.layer_ylt(L), ref)
+    ids = w.yet.ids.copy()
+    ids[7] = w.yet.catalog_size
+    with pytest.raises(AraError) as ei:
+        engine.load_yet(w.yet.catalog_size, w.yet.offsets, ids)
+    assert ei.value.name == "ARA_E_EVENT_RANGE"
+    with pytest.raises(AraError) as ei:
+        engine.layer_ylt(L)
+    assert ei.value.name == "ARA_E_STATE"
+    engine.load_yet_from(w.yet)
+    np.testing.assert_array_equal(engine.layer_ylt(L), ref)
