@@ -32,22 +32,51 @@ __global__ void elt_count_kernel(const int64_t *__restrict__ off, int n_elts, co
                                  unsigned long long *__restrict__ max_loss, int *__restrict__ max_id,
                                  unsigned long long *__restrict__ bad) {
   const int64_t total = off[n_elts];
+  const int lane = threadIdx.x & 31;
   unsigned long long n_range = 0, n_loss = 0, n_dup = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int j = elt_of(off, n_elts, i);
-    const int32_t e = ids[i];
-    const double l = losses[i];
-    if (e < 0 || e >= catalog) {
-      ++n_range;
-      continue;
+  // Warp-uniform loop: a warp takes 32 consecutive entries, which almost
+  // always belong to one ELT, so the per-ELT maxima are reduced in the warp
+  // before one atomic (thousands of entries share each ELT's address).
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < total; w0 += stride) {
+    const int64_t i = w0 + lane;
+    const bool in = i < total;
+    int j = -1;
+    unsigned long long lbits = 0ull;
+    int e = -1;
+    if (in) {
+      j = elt_of(off, n_elts, i);
+      e = ids[i];
+      const double l = losses[i];
+      if (e < 0 || e >= catalog) {
+        ++n_range;
+        e = -1;
+      } else {
+        if (!(l >= 0.0) || isinf(l)) ++n_loss;  // NaN, negative or infinite
+        else lbits = (unsigned long long)__double_as_longlong(l);
+        const uint32_t bit = 1u << (e & 31);
+        if (atomicOr(&seen[(size_t)j * (size_t)seen_words + (e >> 5)], bit) & bit) ++n_dup;
+        atomicAdd(&count[(size_t)j * (size_t)(nb + 1) + e / kFoldEventsPerCta], 1);
+      }
     }
-    if (!(l >= 0.0) || isinf(l)) ++n_loss;  // NaN, negative or infinite
-    const uint32_t bit = 1u << (e & 31);
-    if (atomicOr(&seen[(size_t)j * (size_t)seen_words + (e >> 5)], bit) & bit) ++n_dup;
-    atomicAdd(&count[(size_t)j * (size_t)(nb + 1) + e / kFoldEventsPerCta], 1);
-    if (l >= 0.0 && !isinf(l)) atomicMax(&max_loss[j], (unsigned long long)__double_as_longlong(l));
-    atomicMax(&max_id[j], e);
+    const int j0 = __shfl_sync(0xFFFFFFFFu, j, 0);
+    if (__all_sync(0xFFFFFFFFu, j == j0 || !in) && j0 >= 0) {
+      unsigned long long mb = lbits;
+      int me = e;
+      for (int m = 16; m > 0; m >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xFFFFFFFFu, mb, m);
+        const int oe = __shfl_xor_sync(0xFFFFFFFFu, me, m);
+        mb = ob > mb ? ob : mb;
+        me = oe > me ? oe : me;
+      }
+      if (lane == 0) {
+        if (mb) atomicMax(&max_loss[j0], mb);
+        if (me >= 0) atomicMax(&max_id[j0], me);
+      }
+    } else if (in && j >= 0) {
+      if (lbits) atomicMax(&max_loss[j], lbits);
+      if (e >= 0) atomicMax(&max_id[j], e);
+    }
   }
   if (n_range) atomicAdd(&bad[0], n_range);
   if (n_loss) atomicAdd(&bad[1], n_loss);
