@@ -103,6 +103,10 @@ class Engine:
         """Load an :class:`ara_synth.YET`-like object (catalog_size, offsets, ids, ts)."""
         self.load_yet(yet.catalog_size, yet.offsets, yet.ids, yet.ts)
 
+    def compact_yet(self) -> None:
+        """Sorted, difference-coded id stream for later YLT passes (same results)."""
+        _native.ara_compact_yet(self.ctx)
+
     def load_elts(self, offsets, ids, losses, deductibles, limits) -> int:
         n = int(np.asarray(offsets).shape[0]) - 1
         p = [_arg(offsets, np.int64, "offsets"), _arg(ids, np.int32, "ids"),

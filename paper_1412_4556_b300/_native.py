@@ -78,6 +78,7 @@ PROTOTYPES = {
     "ara_pml_tvar_batch": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp]),
     "ara_set_kernel_timing": (_i32, [_vp, _i32]),
     "ara_kernel_timing": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_f64)]),
+    "ara_compact_yet": (_i32, [_vp]),
     "ara_layer_yelt": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
     "ara_rpl_report": (_i32, [_vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp, _vp]),
     "ara_plan_create": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i32, C.POINTER(C.c_void_p)]),
@@ -201,6 +202,10 @@ def ara_pml_tvar_noalloc(ylt: int, n: int, return_periods: int, n_rp: int, pml_o
     """Context-free PML/TVaR that allocates no device memory (ylt on the device)."""
     _check(None, lib.ara_pml_tvar_noalloc(ylt or None, int(n), return_periods or None, int(n_rp),
                                           pml_out or None, tvar_out or None, stream or None))
+
+
+def ara_compact_yet(ctx: int) -> None:
+    _check(ctx, lib.ara_compact_yet(ctx))
 
 
 def ara_layer_yelt(ctx: int, layer: int, n_trials: int, yelt_out: int, occ_max_out: int,

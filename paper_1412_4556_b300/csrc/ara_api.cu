@@ -179,6 +179,12 @@ AggFixed agg_terms_fixed(double agg_ret, double agg_lim, int q) {
   return af;
 }
 
+YltStream ylt_stream(const ara_ctx *c, int G) {
+  if (G == 1 && c->compact_version == c->yet_version && c->d_dchunks)
+    return YltStream{c->d_dcoff, c->d_dchunks, 2, c->h_dcoff.data()};
+  return YltStream{c->d_coff, c->d_chunks, c->packed ? 1 : 0, c->h_coff.data()};
+}
+
 ara_status enqueue_fold(ara_ctx *c, const LayerRec &L, cudaStream_t s) {
   ARA_CUDA(c, cudaMemsetAsync(L.d_bitmap, 0, (size_t)L.bm.words * 4, s), "cudaMemsetAsync(bitmap)");
   // The sentinel entry (id = catalog) must read zero at this layer's entry
@@ -423,7 +429,6 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
     }
   const BitmapLayout bm = Ls[0]->bm;  // every layer of a catalog shares the layout
   const size_t entries = (size_t)c->catalog + 1;
-  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   // FP64 layers go two to a pass (2 x 16-byte entries per event), FP32-table
   // layers four to a pass (4 x 8 bytes): one 32-byte L2 sector per gather.
   for (const int eb : {16, 8}) {
@@ -452,12 +457,14 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
         table = pair_table;
         bitmap = pair_bitmap;
       }
+      const YltStream ys = ylt_stream(c, G);
+      const double mean_chunks = (double)ys.h_coff[(size_t)n_trials] / (double)n_trials;
       YltLaunch cfg;
-      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, c->packed, eb, G, entries * (size_t)(eb * G),
+      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, ys.layout, eb, G, entries * (size_t)(eb * G),
                            c->tuned[eb == 8 ? 1 : 0][G], &cfg),
                "plan YLT launch");
       TimedLaunch tl(c, ARA_TIMING_YLT, s);
-      ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, table, eb, bitmap, bm, c->catalog,
+      ARA_CUDA(c, launch_ylt_group(ys.coff, ys.chunks, ys.layout, n_trials, table, eb, bitmap, bm, c->catalog,
                                    G, outs, cfg, s),
                "YLT kernel launch");
       tl.done();
@@ -543,6 +550,9 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_offsets);
   cudaFree(c->d_coff);
   cudaFree(c->d_chunks);
+  cudaFree(c->d_dcoff);
+  cudaFree(c->d_dchunks);
+  cudaFree(c->d_cflag);
   cudaFree(c->d_raw);
   cudaFree(c->d_ts);
   cudaFree(c->d_ylt_stage);
@@ -694,6 +704,47 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
   c->h_offsets.swap(h);
   c->h_coff.swap(hp);
   c->packed = packed;
+  return ARA_OK;
+}
+
+ara_status ara_compact_yet(ara_ctx *c) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
+  if (!c->packed || c->compact_version == c->yet_version) return ARA_OK;  // nothing to do
+  const int64_t n = c->n_trials, M = c->n_occ;
+  cudaStream_t s = c->stream;
+  ARA_CUDA(c, ensure(&c->d_raw, &c->cap_raw, (size_t)std::max<int64_t>(M, 1)), "compact YET scratch");
+  ARA_CUDA(c, ensure(&c->d_cflag, &c->cap_cflag, (size_t)std::max<int64_t>(n, 1)), "compact YET scratch");
+  ARA_CUDA(c, launch_compact_sort(c->d_offsets, c->d_coff, c->d_chunks, n, reinterpret_cast<uint32_t *>(c->d_raw),
+                                  c->d_cflag, s),
+           "sort trials");
+  std::vector<int64_t> cf((size_t)n);
+  if (n > 0)
+    ARA_CUDA(c, cudaMemcpyAsync(cf.data(), c->d_cflag, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+             "copy chunk counts");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  std::vector<int64_t> dcoff((size_t)n + 1), plain((size_t)n + 1);
+  int64_t run = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t v = cf[(size_t)t];
+    plain[(size_t)t] = run;
+    dcoff[(size_t)t] = run | (v & ((int64_t)1 << 62));
+    run += v & kCompactOffsetMask;
+  }
+  plain[(size_t)n] = run;
+  dcoff[(size_t)n] = run;
+  c->compact_version = -1;
+  ARA_CUDA(c, ensure(&c->d_dcoff, &c->cap_dcoff, (size_t)n + 1), "compact YET offsets");
+  ARA_CUDA(c, ensure(&c->d_dchunks, &c->cap_dchunks, (size_t)run + kChunkTail), "compact YET chunks");
+  ARA_CUDA(c, cudaMemcpyAsync(c->d_dcoff, dcoff.data(), dcoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+           "copy compact offsets");
+  ARA_CUDA(c, launch_compact_encode(c->d_offsets, c->d_coff, c->d_chunks, n, reinterpret_cast<const uint32_t *>(c->d_raw),
+                                    c->d_dcoff, c->d_dchunks, s),
+           "encode compact YET");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  c->h_dcoff.swap(plain);
+  c->compact_version = c->yet_version;
   return ARA_OK;
 }
 
@@ -875,15 +926,16 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
     ARA_CUDA(c, ensure(&c->d_ylt_stage, &c->cap_ylt_stage, (size_t)n_trials), "stage buffer");
     dst = c->d_ylt_stage;
   }
-  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
+  const YltStream ys = ylt_stream(c, 1);
+  const double mean_chunks = (double)ys.h_coff[(size_t)n_trials] / (double)n_trials;
   YltLaunch cfg;
-  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, c->packed, L->entry_bytes(), 1,
+  ARA_CUDA(c, plan_ylt(c->device, L->bm, mean_chunks, ys.layout, L->entry_bytes(), 1,
                        ((size_t)c->catalog + 1) * (size_t)L->entry_bytes(),
                        c->tuned[L->entry_bytes() == 8 ? 1 : 0][1], &cfg),
            "plan YLT launch");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst};
   TimedLaunch tl(c, ARA_TIMING_YLT, s);
-  ARA_CUDA(c, launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n_trials, L->d_table, L->entry_bytes(),
+  ARA_CUDA(c, launch_ylt_group(ys.coff, ys.chunks, ys.layout, n_trials, L->d_table, L->entry_bytes(),
                                L->d_bitmap, L->bm, c->catalog, 1, &out, cfg, s),
            "YLT kernel launch");
   tl.done();

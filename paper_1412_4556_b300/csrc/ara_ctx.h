@@ -95,6 +95,16 @@ struct ara_ctx {
   int4 *d_chunks = nullptr;         // id chunks + sentinel tail
   size_t cap_chunks = 0;
   bool packed = false;              // 6 ids of 21 bits per chunk
+  // compact id stream for YLT passes (ara_compact_yet): valid while
+  // compact_version == yet_version
+  int64_t compact_version = -1;
+  std::vector<int64_t> h_dcoff;     // chunk offsets (without flags)
+  int64_t *d_dcoff = nullptr;       // chunk offsets, bit 62 = difference-coded trial
+  size_t cap_dcoff = 0;
+  int4 *d_dchunks = nullptr;
+  size_t cap_dchunks = 0;
+  int64_t *d_cflag = nullptr;       // per-trial chunk count and flag (scratch)
+  size_t cap_cflag = 0;
   int32_t *d_raw = nullptr;         // staging for ids copied from the host
   size_t cap_raw = 0;
   float *d_ts = nullptr;
@@ -165,6 +175,18 @@ cudaError_t ensure(T **buf, size_t *cap, size_t count) {
 // Message into the calling thread's context-free error slot (read with
 // ara_last_error(NULL)); returns st.
 ara_status fail_free(ara_status st, const char *fmt, ...);
+
+// The id stream a YLT pass of G layers reads: the compact one when it is
+// current and G == 1 (measured on B300: 3% faster for one-layer passes,
+// 5-10% slower for multi-layer passes, whose gathers dominate and which run
+// without the L2 prefetch), else the stored-order chunks.
+struct YltStream {
+  const int64_t *coff;
+  const int4 *chunks;
+  int layout;               // as launch_ylt_group
+  const int64_t *h_coff;    // host copy of the chunk offsets (no flags)
+};
+YltStream ylt_stream(const ara_ctx *c, int G);
 
 ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s);
 // The device work of fold_layer for a layer whose buffers exist and whose

@@ -247,13 +247,15 @@ struct LayerOut {
   double *ylt;       // device output, one value per trial
 };
 
-// coff/chunks: the chunked YET layout written by launch_pad_ids (packed: 6
-// ids of 21 bits per chunk, else 4 plain ids); sentinel = catalog size (its
+// coff/chunks: the chunked YET layout written by launch_pad_ids (layout 1:
+// 6 ids of 21 bits per chunk, layout 0: 4 plain ids) or by the compact
+// builder (layout 2: per trial, 6 packed ids or 8 difference-coded ids, the
+// choice in bit 62 of the trial's offset); sentinel = catalog size (its
 // table entry is zero).  entry_bytes = 16 for FP64 layers (128-bit
 // fixed-point entries) or 8 for FP32-table layers (64-bit entries whose trial
 // sums stay below 2^64); G layers' tables interleaved (entry_bytes x G <= 32
 // bytes per event, one L2 sector) with the union of their bitmaps.
-cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
+cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, int layout, int64_t n_trials,
                              const void *table, int entry_bytes, const uint32_t *bitmap, BitmapLayout bm,
                              int32_t sentinel, int G, const LayerOut *outs, const YltLaunch &cfg,
                              cudaStream_t s);
@@ -262,7 +264,7 @@ cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packe
 // trials of mean_chunks 16-byte chunks and a (possibly interleaved) table of
 // table_bytes; fields of hint force the unroll (1/2), the lanes per trial
 // (16/32) or the L2 prefetch (0/1).  entry_bytes x G <= 32.
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int entry_bytes,
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, int layout, int entry_bytes,
                      int G, size_t table_bytes, YltShape hint, YltLaunch *out);
 
 // Up to four layers' tables and bitmaps for launch_interleave.
@@ -274,6 +276,20 @@ struct Bitmaps4 {
 };
 cudaError_t launch_interleave(const Tables4 &in, int entry_bytes, int G, int64_t entries, void *out,
                               const Bitmaps4 &bin, int32_t words, uint32_t *bout, cudaStream_t s);
+
+// Compact (sorted, difference-coded) id stream for YLT passes (compact.cu).
+constexpr int kCompactMaxTrial = 8192;  // longer trials keep the packed layout
+constexpr int64_t kCompactOffsetMask = ((int64_t)1 << 62) - 1;
+int4 delta_sentinel_chunk(int32_t sentinel);  // 8 empty slots after the sentinel id
+// Sort each trial's ids (6-per-chunk layout coff/chunks) into sorted (raw
+// CSR layout) and write count_flag[t] = chunk count | (1 << 62 when the
+// trial is difference-coded).
+cudaError_t launch_compact_sort(const int64_t *raw_off, const int64_t *coff, const int4 *chunks, int64_t n_trials,
+                                uint32_t *sorted, int64_t *count_flag, cudaStream_t s);
+// Write the compact stream at dcoff (offsets with the flag in bit 62), plus
+// kChunkTail tail chunks.
+cudaError_t launch_compact_encode(const int64_t *raw_off, const int64_t *coff, const int4 *chunks, int64_t n_trials,
+                                  const uint32_t *sorted, const int64_t *dcoff, int4 *dchunks, cudaStream_t s);
 
 // ELT ingest (ingest.cu): check the entries of n_elts ELTs (CSR by d_off,
 // device), group each ELT by fold bucket into s_ids / s_losses (same CSR) and

@@ -109,7 +109,8 @@ ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
     table = p->d_pair;
     bitmap = p->d_pair_bm;
   }
-  const double mean_chunks = (double)c->h_coff[(size_t)n] / (double)n;
+  const YltStream ys = ylt_stream(c, G);
+  const double mean_chunks = (double)ys.h_coff[(size_t)n] / (double)n;
   cudaEvent_t a = nullptr, b = nullptr;
   ARA_CUDA(c, cudaEventCreate(&a), "cudaEventCreate");
   cudaError_t e = cudaEventCreate(&b);
@@ -128,12 +129,12 @@ ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
       hint.unroll = unroll;
       hint.prefetch = prefetch;
       YltLaunch cfg;
-      e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, table_bytes, hint, &cfg);
+      e = plan_ylt(c->device, bm, mean_chunks, ys.layout, ps.eb, G, table_bytes, hint, &cfg);
       float ms = 1e30f;
       for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first run warms L2 and the clocks
         e = cudaEventRecord(a, p->cap);
         if (e == cudaSuccess)
-          e = launch_ylt_group(c->d_coff, c->d_chunks, c->packed, n, table, ps.eb, bitmap, bm, c->catalog, G,
+          e = launch_ylt_group(ys.coff, ys.chunks, ys.layout, n, table, ps.eb, bitmap, bm, c->catalog, G,
                                outs, cfg, p->cap);
         if (e == cudaSuccess) e = cudaEventRecord(b, p->cap);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
@@ -230,11 +231,12 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
       if (st) return bail(st);
     }
   }
-  const double mean_chunks = (double)c->h_coff[(size_t)n_trials] / (double)n_trials;
   for (const Pass &ps : passes) {
     const int G = (int)ps.idx.size();
+    const YltStream ys = ylt_stream(c, G);
+    const double mean_chunks = (double)ys.h_coff[(size_t)n_trials] / (double)n_trials;
     YltLaunch cfg;
-    e = plan_ylt(c->device, bm, mean_chunks, c->packed, ps.eb, G, ((size_t)c->catalog + 1) * (size_t)(ps.eb * G),
+    e = plan_ylt(c->device, bm, mean_chunks, ys.layout, ps.eb, G, ((size_t)c->catalog + 1) * (size_t)(ps.eb * G),
                  c->tuned[ps.eb == 8][G], &cfg);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "plan YLT launch"));
     p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch, ps.idx[0]});

@@ -98,6 +98,28 @@ __device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]
 // 32-byte load, i.e. one L2 sector for two layers) and predicated
 // add/add-with-carry, so occurrences whose bitmap bit is clear cost neither a
 // memory request nor register moves.
+// The 8 ids of a difference-coded chunk (see compact.cu): a 21-bit base and
+// seven 15-bit steps; a step of 0x7FFF marks an empty slot, read as the
+// sentinel id (table entry zero).
+__device__ __forceinline__ void delta_ids(int4 c, uint32_t zero_id, uint32_t (&id)[8]) {
+  const uint32_t x = (uint32_t)c.x, y = (uint32_t)c.y, z = (uint32_t)c.z, w = (uint32_t)c.w;
+  uint32_t d[8];
+  d[1] = __funnelshift_r(x, y, 21) & 0x7FFFu;
+  d[2] = (y >> 4) & 0x7FFFu;
+  d[3] = ((y >> 19) & 0x1FFFu) | ((z & 3u) << 13);
+  d[4] = (z >> 2) & 0x7FFFu;
+  d[5] = (z >> 17) & 0x7FFFu;
+  d[6] = w & 0x7FFFu;
+  d[7] = (w >> 15) & 0x7FFFu;
+  uint32_t cur = x & 0x1FFFFFu;
+  id[0] = cur;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    cur += d[k];
+    id[k] = d[k] == 0x7FFFu ? zero_id : cur;
+  }
+}
+
 // Accumulators of G layers: 128-bit for 16-byte entries, 64-bit for 8-byte.
 template <int EB, int G>
 struct Acc {
@@ -187,12 +209,17 @@ struct GroupOut {
 // one 128-bit accumulator per layer.  A warp sums 32 / LPT consecutive trials
 // side by side, LPT lanes per trial: fewer lanes idle in the last step of a
 // trial, and one group reduction and one epilogue serve 32 / LPT trials.
-template <int U, bool PACKED, int EB, int G, int LPT>
+template <int U, int LAYOUT, int EB, int G, int LPT>
 __global__ void __launch_bounds__(kYltThreads, 1)
 ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
                 int64_t n_trials, const void *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
-                int4 sent4, GroupOut<G> out, int do_prefetch) {
+                int4 sent4, int4 sentd, uint32_t zero_id, GroupOut<G> out, int do_prefetch) {
+  // LAYOUT 0: 4 plain ids per chunk; 1: 6 packed ids; 2: per trial either 6
+  // packed ids or 8 difference-coded ids (flag in bit 62 of its offset).
+  constexpr bool PACKED = LAYOUT >= 1;
+  constexpr int IDS = LAYOUT == 2 ? 8 : (PACKED ? 6 : 4);
+  constexpr int64_t OFF = LAYOUT == 2 ? kCompactOffsetMask : ~(int64_t)0;
   constexpr int TPW = 32 / LPT;  // trials per warp step
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
@@ -211,34 +238,36 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
 
   // Offsets of the next warp step's trials and the L2 prefetch range of the
   // step after it are loaded one step ahead, so no step waits on them.
-  int64_t pa = 0, pe = 0;  // chunk range of this lane's trial in the next step
+  int64_t pa = 0, pe = 0;  // chunk range of this lane's trial in the next step (flag kept in pa)
   if (t_begin + grp < t_end) {
     pa = coff[t_begin + grp];
-    pe = coff[t_begin + grp + 1];
+    pe = coff[t_begin + grp + 1] & OFF;
   }
   int64_t fa = 0, fb = 0;  // lane 0: chunk range prefetched at the top of the next step
   if (lane == 0 && t_begin < t_end) {
-    const int64_t a = coff[t_begin], b = coff[min(t_begin + TPW, t_end)];
+    const int64_t a = coff[t_begin] & OFF, b = coff[min(t_begin + TPW, t_end)] & OFF;
     if (b > a && do_prefetch) prefetch_l2(chunks + a, (uint32_t)((b - a) * 16), pol_ids);
     fa = b;
-    fb = coff[min(t_begin + 2 * TPW, t_end)];
+    fb = coff[min(t_begin + 2 * TPW, t_end)] & OFF;
   }
   for (int64_t t0 = t_begin; t0 < t_end; t0 += TPW) {
     const int64_t t = t0 + grp;
     const bool valid = t < t_end;
-    const int64_t p0 = pa;
-    const int nk = (int)(pe - pa);  // 16-byte chunks of trial t (0 if not valid)
+    const bool dfl = LAYOUT == 2 && ((pa >> 62) & 1);  // difference-coded trial
+    const int64_t p0 = pa & OFF;
+    const int nk = (int)(pe - p0);  // 16-byte chunks of trial t (0 if not valid)
     pa = pe = 0;
     if (t + TPW < t_end) {
       pa = coff[t + TPW];
-      pe = coff[t + TPW + 1];
+      pe = coff[t + TPW + 1] & OFF;
     }
     // While these trials are summed, the next ones' ids travel to L2.
     if (lane == 0) {
       if (fb > fa && do_prefetch) prefetch_l2(chunks + fa, (uint32_t)((fb - fa) * 16), pol_ids);
       fa = fb;
-      fb = coff[min(t0 + 3 * TPW, t_end)];
+      fb = coff[min(t0 + 3 * TPW, t_end)] & OFF;
     }
+    const int4 sentv = dfl ? sentd : sent4;
     int nk_max = nk;
     if constexpr (TPW > 1) nk_max = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)nk);
     const int4 *tp = chunks + p0;
@@ -255,7 +284,7 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
     int4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      v[u] = sent4;
+      v[u] = sentv;
       const int j = LPT * u + gl;
       if (j < nk) v[u] = ld_ids(tp + j, pol_ids);
     }
@@ -263,17 +292,29 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
       int4 vn[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        vn[u] = sent4;
+        vn[u] = sentv;
         const int j = base + LPT * (U + u) + gl;
         if (j < nk) vn[u] = ld_ids(tp + j, pol_ids);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (base + LPT * u >= nk_max) break;  // warp-uniform: the rest of this step is empty
-        uint32_t idv[PACKED ? 6 : 4];
-        chunk_ids<PACKED>(v[u], idv);
+        uint32_t idv[IDS];
+        if constexpr (LAYOUT == 2) {
+          if (dfl) {
+            delta_ids(v[u], zero_id, idv);
+          } else {
+            uint32_t id6[6];
+            chunk_ids<true>(v[u], id6);
 #pragma unroll
-        for (int i = 0; i < (PACKED ? 6 : 4); ++i) {
+            for (int i = 0; i < 6; ++i) idv[i] = id6[i];
+            idv[6] = idv[7] = zero_id;
+          }
+        } else {
+          chunk_ids<PACKED>(v[u], idv);
+        }
+#pragma unroll
+        for (int i = 0; i < IDS; ++i) {
           const uint32_t id = idv[i];
           const uint32_t word = s_bm[bitmap_word(id, bm_mul)];
           const uint32_t hit = __funnelshift_r(word, word, id) & 1u;  // bit id & 31
@@ -297,85 +338,94 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
   }
 }
 
-template <int U, bool PACKED, int EB, int G, int LPT>
+template <int U, int LAYOUT, int EB, int G, int LPT>
 static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
                             const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
                             const YltLaunch &cfg, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, PACKED, EB, G, LPT>,
+  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, LAYOUT, EB, G, LPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
   if (err != cudaSuccess) return err;
   int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
-  const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
+  const int4 sent4 = LAYOUT >= 1 ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
+  const int4 sentd = delta_sentinel_chunk(sentinel);
   GroupOut<G> go;
   for (int g = 0; g < G; ++g) go.l[g] = outs[g];
-  ylt_fp64_kernel<U, PACKED, EB, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
-      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sent4, go,
-      cfg.prefetch);
+  ylt_fp64_kernel<U, LAYOUT, EB, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
+      coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sent4, sentd,
+      (uint32_t)sentinel, go, cfg.prefetch);
   return cudaGetLastError();
 }
 
 // The kernel for (unroll, lanes per trial) as a function pointer and as a
-// launch, for one (PACKED, EB, G).
-template <bool PACKED, int EB, int G>
+// launch, for one (LAYOUT, EB, G).
+template <int LAYOUT, int EB, int G>
 struct YltVariants {
   static const void *fn(int unroll, int lpt) {
     if (lpt == 16)
-      return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, EB, G, 16>
-                         : (const void *)ylt_fp64_kernel<2, PACKED, EB, G, 16>;
-    return unroll == 1 ? (const void *)ylt_fp64_kernel<1, PACKED, EB, G, 32>
-                       : (const void *)ylt_fp64_kernel<2, PACKED, EB, G, 32>;
+      return unroll == 1 ? (const void *)ylt_fp64_kernel<1, LAYOUT, EB, G, 16>
+                         : (const void *)ylt_fp64_kernel<2, LAYOUT, EB, G, 16>;
+    return unroll == 1 ? (const void *)ylt_fp64_kernel<1, LAYOUT, EB, G, 32>
+                       : (const void *)ylt_fp64_kernel<2, LAYOUT, EB, G, 32>;
   }
   static cudaError_t launch(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
                             const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
                             const YltLaunch &cfg, cudaStream_t s) {
     if (cfg.lanes_per_trial == 16)
       return cfg.unroll == 1
-                 ? launch_u<1, PACKED, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
-                 : launch_u<2, PACKED, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+                 ? launch_u<1, LAYOUT, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
+                 : launch_u<2, LAYOUT, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
     return cfg.unroll == 1
-               ? launch_u<1, PACKED, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
-               : launch_u<2, PACKED, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+               ? launch_u<1, LAYOUT, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
+               : launch_u<2, LAYOUT, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
   }
 };
 
-// Dispatch on (packed, entry bytes, group size) -> F<PACKED, EB, G>.
-template <template <bool, int, int> class F, typename... A>
-static auto dispatch(bool packed, int eb, int G, A... a) {
-  if (eb == 16) {
-    if (G == 2) return packed ? F<true, 16, 2>::call(a...) : F<false, 16, 2>::call(a...);
-    return packed ? F<true, 16, 1>::call(a...) : F<false, 16, 1>::call(a...);
-  }
-  if (G == 4) return packed ? F<true, 8, 4>::call(a...) : F<false, 8, 4>::call(a...);
-  if (G == 2) return packed ? F<true, 8, 2>::call(a...) : F<false, 8, 2>::call(a...);
-  return packed ? F<true, 8, 1>::call(a...) : F<false, 8, 1>::call(a...);
+// Dispatch on (id layout, entry bytes, group size) -> F<LAYOUT, EB, G>.
+template <template <int, int, int> class F, int EB, int G, typename... A>
+static auto dispatch_layout(int layout, A... a) {
+  if (layout == 2) return F<2, EB, G>::call(a...);
+  if (layout == 1) return F<1, EB, G>::call(a...);
+  return F<0, EB, G>::call(a...);
 }
 
-template <bool PACKED, int EB, int G>
+template <template <int, int, int> class F, typename... A>
+static auto dispatch(int layout, int eb, int G, A... a) {
+  if (eb == 16) {
+    if (G == 2) return dispatch_layout<F, 16, 2>(layout, a...);
+    return dispatch_layout<F, 16, 1>(layout, a...);
+  }
+  if (G == 4) return dispatch_layout<F, 8, 4>(layout, a...);
+  if (G == 2) return dispatch_layout<F, 8, 2>(layout, a...);
+  return dispatch_layout<F, 8, 1>(layout, a...);
+}
+
+template <int LAYOUT, int EB, int G>
 struct LaunchF {
   static cudaError_t call(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
                           const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
                           const YltLaunch *cfg, cudaStream_t s) {
-    return YltVariants<PACKED, EB, G>::launch(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, *cfg, s);
+    return YltVariants<LAYOUT, EB, G>::launch(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, *cfg, s);
   }
 };
 
-template <bool PACKED, int EB, int G>
+template <int LAYOUT, int EB, int G>
 struct FnF {
-  static const void *call(int unroll, int lpt) { return YltVariants<PACKED, EB, G>::fn(unroll, lpt); }
+  static const void *call(int unroll, int lpt) { return YltVariants<LAYOUT, EB, G>::fn(unroll, lpt); }
 };
 
-cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, bool packed, int64_t n_trials,
+cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, int layout, int64_t n_trials,
                              const void *table, int entry_bytes, const uint32_t *bitmap, BitmapLayout bm,
                              int32_t sentinel, int G, const LayerOut *outs, const YltLaunch &cfg,
                              cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
   if (!(entry_bytes == 16 && (G == 1 || G == 2)) && !(entry_bytes == 8 && (G == 1 || G == 2 || G == 4)))
     return cudaErrorInvalidValue;
-  return dispatch<LaunchF>(packed, entry_bytes, G, coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
+  if (layout < 0 || layout > 2) return cudaErrorInvalidValue;
+  return dispatch<LaunchF>(layout, entry_bytes, G, coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
                            &cfg, s);
 }
 
-cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, bool packed, int entry_bytes,
+cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, int layout, int entry_bytes,
                      int G, size_t table_bytes, YltShape hint, YltLaunch *out) {
   if (!(entry_bytes == 16 && (G == 1 || G == 2)) && !(entry_bytes == 8 && (G == 1 || G == 2 || G == 4)))
     return cudaErrorInvalidValue;
@@ -413,7 +463,8 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, boo
   out->unroll = unroll;
   out->lanes_per_trial = lpt;
   out->prefetch = prefetch;
-  const void *fn = dispatch<FnF>(packed, entry_bytes, G, unroll, lpt);
+  if (layout < 0 || layout > 2) return cudaErrorInvalidValue;
+  const void *fn = dispatch<FnF>(layout, entry_bytes, G, unroll, lpt);
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
