@@ -126,16 +126,18 @@ ARA_API ara_status ara_load_yet(ara_ctx *ctx, int32_t catalog_size, int64_t n_tr
 
 /* Prepare the loaded YET for repeated pricing.  A trial's loss does not
  * depend on the order of its events (Algorithm 1 sums them; the engine sums
- * exactly), so one-layer YLT passes may read each trial's ids sorted and
- * stored as differences: 8 ids per 16 bytes instead of 6, a quarter fewer
- * bytes read from HBM by every later one-layer pass (ara_layer_ylt, and the
- * odd layer of ara_layers_ylt, plans and service batches; passes over
- * several layers keep the stored layout, which measured faster for them).  Trials longer than 8192 events, or whose sorted ids are far apart
- * (short trials over a large catalog), keep the stored layout.  Results are
- * bit for bit those of the stored layout; the Year Event Loss Table keeps
- * reading the stored (time) order.  Takes a few milliseconds and about 2
- * bytes per occurrence of device memory; a later ara_load_yet drops it.
- * No-op for catalogs above 2^21 - 1 events or when already prepared.
+ * exactly), so one-layer YLT passes may read each trial's ids reordered (so
+ * that every group of 8 ascends in small steps) and stored as differences:
+ * 8 ids per 16 bytes instead of 6, a quarter fewer bytes read from HBM by
+ * every later one-layer pass (ara_layer_ylt, and the odd layer of
+ * ara_layers_ylt, plans and service batches; passes over several layers keep
+ * the stored layout, which measured faster for them).  Trials whose ids are
+ * far apart (short trials over a large catalog) keep the stored layout.
+ * Results are bit for bit those of the stored layout; the Year Event Loss
+ * Table keeps reading the stored (time) order.  Takes a few milliseconds
+ * and about 2 bytes per occurrence of device memory; a later ara_load_yet
+ * drops it.  No-op for catalogs above 2^21 - 1 events or when already
+ * prepared.
  * Errors: ARA_E_STATE (no YET), ARA_E_NOMEM, ARA_E_CUDA. */
 ARA_API ara_status ara_compact_yet(ara_ctx *ctx);
 

@@ -715,33 +715,23 @@ ara_status ara_compact_yet(ara_ctx *c) {
   const int64_t n = c->n_trials, M = c->n_occ;
   cudaStream_t s = c->stream;
   ARA_CUDA(c, ensure(&c->d_raw, &c->cap_raw, (size_t)std::max<int64_t>(M, 1)), "compact YET scratch");
-  ARA_CUDA(c, ensure(&c->d_cflag, &c->cap_cflag, (size_t)std::max<int64_t>(n, 1)), "compact YET scratch");
-  ARA_CUDA(c, launch_compact_sort(c->d_offsets, c->d_coff, c->d_chunks, n, reinterpret_cast<uint32_t *>(c->d_raw),
-                                  c->d_cflag, s),
-           "sort trials");
-  std::vector<int64_t> cf((size_t)n);
-  if (n > 0)
-    ARA_CUDA(c, cudaMemcpyAsync(cf.data(), c->d_cflag, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
-             "copy chunk counts");
-  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
-  std::vector<int64_t> dcoff((size_t)n + 1), plain((size_t)n + 1);
-  int64_t run = 0;
-  for (int64_t t = 0; t < n; ++t) {
-    const int64_t v = cf[(size_t)t];
-    plain[(size_t)t] = run;
-    dcoff[(size_t)t] = run | (v & ((int64_t)1 << 62));
-    run += v & kCompactOffsetMask;
-  }
-  plain[(size_t)n] = run;
-  dcoff[(size_t)n] = run;
+  ARA_CUDA(c, ensure(&c->d_cflag, &c->cap_cflag, (size_t)n + 1 + kCompactScanScratch), "compact YET scratch");
   c->compact_version = -1;
   ARA_CUDA(c, ensure(&c->d_dcoff, &c->cap_dcoff, (size_t)n + 1), "compact YET offsets");
-  ARA_CUDA(c, ensure(&c->d_dchunks, &c->cap_dchunks, (size_t)run + kChunkTail), "compact YET chunks");
-  ARA_CUDA(c, cudaMemcpyAsync(c->d_dcoff, dcoff.data(), dcoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s),
-           "copy compact offsets");
+  ARA_CUDA(c, launch_compact_sort(c->d_offsets, c->d_coff, c->d_chunks, n, reinterpret_cast<uint32_t *>(c->d_raw),
+                                  c->d_cflag, s),
+           "reorder trials");
+  ARA_CUDA(c, launch_compact_scan(c->d_cflag, n, c->d_dcoff, c->d_cflag + n + 1, s), "scan chunk counts");
+  int64_t total = 0;
+  ARA_CUDA(c, cudaMemcpyAsync(&total, c->d_cflag + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy chunk total");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  ARA_CUDA(c, ensure(&c->d_dchunks, &c->cap_dchunks, (size_t)total + kChunkTail), "compact YET chunks");
   ARA_CUDA(c, launch_compact_encode(c->d_offsets, c->d_coff, c->d_chunks, n, reinterpret_cast<const uint32_t *>(c->d_raw),
                                     c->d_dcoff, c->d_dchunks, s),
            "encode compact YET");
+  std::vector<int64_t> plain((size_t)n + 1);
+  ARA_CUDA(c, cudaMemcpyAsync(plain.data(), c->d_cflag, plain.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+           "copy compact offsets");
   ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
   c->h_dcoff.swap(plain);
   c->compact_version = c->yet_version;

@@ -278,14 +278,19 @@ cudaError_t launch_interleave(const Tables4 &in, int entry_bytes, int G, int64_t
                               const Bitmaps4 &bin, int32_t words, uint32_t *bout, cudaStream_t s);
 
 // Compact (sorted, difference-coded) id stream for YLT passes (compact.cu).
-constexpr int kCompactMaxTrial = 8192;  // longer trials keep the packed layout
 constexpr int64_t kCompactOffsetMask = ((int64_t)1 << 62) - 1;
 int4 delta_sentinel_chunk(int32_t sentinel);  // 8 empty slots after the sentinel id
-// Sort each trial's ids (6-per-chunk layout coff/chunks) into sorted (raw
-// CSR layout) and write count_flag[t] = chunk count | (1 << 62 when the
-// trial is difference-coded).
+// Reorder each trial's ids (6-per-chunk layout coff/chunks) into sorted (raw
+// CSR layout) so that every group of 8 ascends, and write count_flag[t] =
+// chunk count | (1 << 62 when the trial is difference-coded).
 cudaError_t launch_compact_sort(const int64_t *raw_off, const int64_t *coff, const int4 *chunks, int64_t n_trials,
                                 uint32_t *sorted, int64_t *count_flag, cudaStream_t s);
+// Exclusive scan of count_flag (n_trials + 1 entries of room) into dcoff
+// (flag kept, n_trials + 1 entries) and, in place, the plain offsets; bsum
+// is scratch of kCompactScanScratch entries.
+constexpr int kCompactScanScratch = 1025;
+cudaError_t launch_compact_scan(int64_t *count_plain, int64_t n_trials, int64_t *dcoff, int64_t *bsum,
+                                cudaStream_t s);
 // Write the compact stream at dcoff (offsets with the flag in bit 62), plus
 // kChunkTail tail chunks.
 cudaError_t launch_compact_encode(const int64_t *raw_off, const int64_t *coff, const int4 *chunks, int64_t n_trials,

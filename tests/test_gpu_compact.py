@@ -41,9 +41,10 @@ def test_compact_stream_is_bit_identical(engine, catalog):
     sizes = [min(catalog, s) for s in (1, 300, 200_000, 7)]
     pool = _custom_pool(catalog, sizes, 21)
     hot = [0, catalog - 1, catalog // 2] + [int(x) for x in pool.ids[:50]]
-    # ragged lengths around every tile edge, trials longer than the sorted
-    # limit (8192 events), and very short trials (far-apart sorted ids)
-    lengths = LENGTHS * 3 + [8192, 8193, 20_000, 2, 3, 9, 17] * 3
+    # ragged lengths around every tile edge, trials around the shared-memory
+    # staging limit (1536 events) and longer (up to 20,000 events), and very
+    # short trials (far-apart sorted ids)
+    lengths = LENGTHS * 3 + [1535, 1536, 1537, 8192, 8193, 20_000, 2, 3, 9, 17] * 3
     yet = _custom_yet(catalog, lengths, catalog + 7, hot)
     engine.load_yet_from(yet)
     first = engine.load_pool(pool)
