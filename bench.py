@@ -199,7 +199,7 @@ def oracle_sample(w, budget_s: float = 12.0, threads=None, max_trials=None):
     n = w.yet.n_trials
     # Two probes separate the fixed cost (building the direct access tables)
     # from the per-trial cost; the sample is then sized to the time budget.
-    sizes = [min(n, 512), min(n, 2048)]
+    sizes = [min(n, 2048), min(n, 16384)]
     times = []
     for m in sizes:
         probe = np.sort(rng.choice(n, m, replace=False))
