@@ -144,7 +144,7 @@ ARA_API ara_status ara_compact_yet(ara_ctx *ctx);
 /* ------------------------------------------------- Event Loss Tables (ELT) */
 
 /* Append n_elts ELTs to the context's pool (Section III: ELT = {(E_i, l_i)}
- * plus financial terms FT1; "tens of thousands of event losses").  All
+ * plus financial terms FT1; an ELT typically holds 10^4-10^5 events).  All
  * arrays are host pointers.
  *   elt_offsets int64[n_elts+1]: ELT j owns positions [off[j], off[j+1]);
  *               off[0] == 0, nondecreasing (an empty ELT is allowed)

@@ -91,8 +91,8 @@ typedef struct {
   double *memo;          /* optional: combined ELT loss x(e) per event (R6) */
 } layer_t;
 
-/* Sec. IV-B: "direct access table" -- a dense array over event ids holding
- * the ELT's loss for present events and 0 elsewhere. */
+/* Sec. IV-B's direct access table of an ELT: a dense array over event ids
+ * holding the ELT's loss for present events and 0 elsewhere. */
 static int build_dats(layer_t *L, const int64_t *elt_off, const int32_t *elt_ids,
                       const double *elt_losses) {
   size_t n = (size_t)L->n_elts * (size_t)L->catalog;

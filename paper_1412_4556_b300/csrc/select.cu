@@ -1,6 +1,6 @@
-// PML and TVaR from a Year Loss Table (Section III: "risk metrics such as the
-// Probable Maximum Loss (PML) and the Tail Value-at-Risk (TVaR) ... can be
-// derived from the output of the analysis").
+// PML and TVaR from a Year Loss Table (Section III names both as risk
+// measures computed from the analysis' output; their definitions below are
+// the readings of the Introduction's and Section III's wording).
 //
 // For each return period r with k_r = floor(n / RP_r):
 //   PML_r  = the k_r-th largest trial loss
