@@ -73,8 +73,17 @@ def shard_seed(seed: int, rank: int) -> int:
     return S.sub_seed(seed, "rank", rank) if rank else seed
 
 
-def merge_shard_ylts(parts):
-    """Portfolio-wide YLT from the ranks' shards (rank order)."""
+def tail_size(n_per_rank: int, world: int, return_periods) -> int:
+    """Largest losses each trial shard sends for the portfolio-wide PML/TVaR:
+    floor(N_total / RP_min) (all of its own when that is more), since the
+    k largest of the whole YLT lie among every shard's k largest."""
+    n_total = n_per_rank * world
+    return max(1, min(n_per_rank, int(math.floor(n_total / min(return_periods)))))
+
+
+def merge_shard_tails(parts):
+    """The union of the ranks' tails (rank order), the input of
+    ara_pml_tvar_tail."""
     return np.concatenate([np.asarray(p, dtype=np.float64) for p in parts])
 
 
@@ -250,18 +259,22 @@ def run_engine(args):
     ylt_dev = torch.empty(N, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
 
-    gather_buf = None
+    gather_buf = tail_dev = None
+    k_tail = tail_size(N, world, rps)
     if world > 1:
-        gather_buf = torch.empty(N * world, dtype=torch.float64, device=dev)
+        tail_dev = torch.empty(k_tail, dtype=torch.float64, device=dev)
+        gather_buf = torch.empty(k_tail * world, dtype=torch.float64, device=dev)
 
     def step():
         L = eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
         eng.layer_ylt(L, out=ylt_dev)
         if world > 1:
+            # each shard sends its k_tail largest losses (not its whole YLT)
             import torch.distributed as dist
+            eng.ylt_tail(ylt_dev, k_tail, out=tail_dev)
             with torch.cuda.stream(stream):
-                dist.all_gather_into_tensor(gather_buf, ylt_dev)
-            res = eng.pml_tvar(gather_buf, rps) if rank == 0 else None
+                dist.all_gather_into_tensor(gather_buf, tail_dev)
+            res = eng.pml_tvar_tail(gather_buf, N * world, rps) if rank == 0 else None
         else:
             res = eng.pml_tvar(ylt_dev, rps)
         eng.release_layer(L)
@@ -337,7 +350,9 @@ def run_engine(args):
                                   "ara_compact_yet: 8 difference-coded ids per 16 bytes, each group of 8 ascending (prepared once "
                                   "before timing, %.1f ms)" % compact_ms),
                    "l2": "inputs larger than L2: the 2-2.7 GB chunked YET id stream is re-read from HBM every step",
-                   "parallelism": f"trial shards x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": (f"trial shards x{world}; each rank sends its {k_tail} largest trial losses "
+                                   "(ara_ylt_tail, NCCL all-gather) and rank 0 prices the union "
+                                   "(ara_pml_tvar_tail)") if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "ylt_fp64_kernel", "kernel_ms": ylt_avg_ms,
@@ -349,7 +364,9 @@ def run_engine(args):
         "pml": list(map(float, res[0])), "tvar": list(map(float, res[1])),
         "clocks": clocks.summary(),
         "e2e": e2e,
-        "gpu_launches": args.steps * (1 + 1 + 10),
+        # fold, YLT, selection (init + 8 passes + sum); with shards also the
+        # tail (selection + 3 kernels) and the selection over the union
+        "gpu_launches": args.steps * (1 + 1 + 10 + (13 if world > 1 else 0)),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

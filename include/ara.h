@@ -227,6 +227,35 @@ ARA_API ara_status ara_pml_tvar(ara_ctx *ctx, const double *ylt, int64_t n,
                         const double *return_periods, int32_t n_rp, double *pml_out,
                         double *tvar_out);
 
+/* The k largest of a YLT's n trial losses, for the exchange between trial
+ * shards (Section IV-C spreads one analysis' trials over several GPUs).  PML
+ * and TVaR at return period RP read only the floor(N / RP) largest of N
+ * losses, and the k largest of a union of shards lie in the union of each
+ * shard's k largest: shards that send their floor(N_total / RP_min) largest
+ * send all that ara_pml_tvar_tail needs, instead of whole YLTs.
+ *   ylt       double[n], host or device; finite and >= 0
+ *   k         1 <= k <= n
+ *   tail_out  double[k], host or device, caller-owned: the values above the
+ *             k-th largest value tau, in index order, then copies of tau
+ *             (k values in all; the same on every run)
+ * Errors: ARA_E_INVALID_ARG (sizes, NaN/negative/inf loss; tail_out is then
+ * unspecified), ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_ylt_tail(ara_ctx *ctx, const double *ylt, int64_t n, int64_t k, double *tail_out);
+
+/* PML and TVaR of a YLT of n_total trial losses from m values of it that
+ * include its floor(n_total / RP) largest for every return period given
+ * (for example the concatenated ara_ylt_tail outputs of its shards): the
+ * same definitions as ara_pml_tvar with k = floor(n_total / RP_r), and the
+ * same bits as ara_pml_tvar on the whole YLT (the tail sum is exact, on the
+ * fixed-point scale the whole YLT would use).
+ *   tail      double[m], host or device; finite and >= 0
+ *   n_total   trial count of the whole YLT, >= m
+ * Errors: ARA_E_INVALID_ARG (bad RP, floor(n_total / RP) above m,
+ * NaN/negative/inf value), ARA_E_NOMEM, ARA_E_CUDA. */
+ARA_API ara_status ara_pml_tvar_tail(ara_ctx *ctx, const double *tail, int64_t m, int64_t n_total,
+                                     const double *return_periods, int32_t n_rp, double *pml_out,
+                                     double *tvar_out);
+
 /* Year Loss Tables of several layers over the first n_trials trials
  * (Section III: a Program covers several Layers, a Portfolio several
  * Programs; each layer's YLT is Algorithm 1 for that layer).

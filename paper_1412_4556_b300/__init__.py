@@ -220,6 +220,30 @@ class Engine:
                              pml.ctypes.data, tvar.ctypes.data)
         return pml, tvar
 
+    def ylt_tail(self, ylt, k: int, out=None):
+        """The k largest values of a YLT (NumPy array or CUDA tensor): the
+        values above the k-th largest in index order, then copies of it.
+        ``out`` may be a float64 NumPy array or CUDA tensor of k values."""
+        p, keep = _arg(ylt, np.float64, "ylt")
+        if out is None:
+            out = np.empty(int(k), dtype=np.float64)
+        po, ko = _arg(out, np.float64, "out")
+        if ko is not out:
+            raise TypeError("out must be a contiguous float64 array or tensor")
+        _native.ara_ylt_tail(self.ctx, p, int(ylt.shape[0]), int(k), po)
+        return out
+
+    def pml_tvar_tail(self, tail, n_total: int, return_periods: Sequence[float]):
+        """PML and TVaR of a YLT of n_total trials from values of it that
+        include its floor(n_total / RP) largest (e.g. shards' ylt_tail)."""
+        p, keep = _arg(tail, np.float64, "tail")
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        pml = np.zeros(rps.shape[0])
+        tvar = np.zeros(rps.shape[0])
+        _native.ara_pml_tvar_tail(self.ctx, p, int(tail.shape[0]), int(n_total), rps.ctypes.data,
+                                  int(rps.shape[0]), pml.ctypes.data, tvar.ctypes.data)
+        return pml, tvar
+
     # ----------------------------------------------------------- measurement
     def set_kernel_timing(self, enable: bool = True) -> None:
         _native.ara_set_kernel_timing(self.ctx, enable)

@@ -74,6 +74,8 @@ PROTOTYPES = {
     "ara_layer_ylt": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "ara_pml_tvar": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp, _vp]),
     "ara_pml_tvar_noalloc": (_i32, [_vp, _i64, _vp, _i32, _vp, _vp, _vp]),
+    "ara_ylt_tail": (_i32, [_vp, _vp, _i64, _i64, _vp]),
+    "ara_pml_tvar_tail": (_i32, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp]),
     "ara_layers_ylt": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp]),
     "ara_pml_tvar_batch": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _vp, _vp]),
     "ara_set_kernel_timing": (_i32, [_vp, _i32]),
@@ -183,6 +185,16 @@ def ara_pml_tvar(ctx: int, ylt: int, n: int, return_periods: int, n_rp: int, pml
                  tvar_out: int) -> None:
     _check(ctx, lib.ara_pml_tvar(ctx, ylt or None, int(n), return_periods or None, int(n_rp),
                                  pml_out or None, tvar_out or None))
+
+
+def ara_ylt_tail(ctx: int, ylt: int, n: int, k: int, tail_out: int) -> None:
+    _check(ctx, lib.ara_ylt_tail(ctx, ylt or None, int(n), int(k), tail_out or None))
+
+
+def ara_pml_tvar_tail(ctx: int, tail: int, m: int, n_total: int, return_periods: int, n_rp: int,
+                      pml_out: int, tvar_out: int) -> None:
+    _check(ctx, lib.ara_pml_tvar_tail(ctx, tail or None, int(m), int(n_total), return_periods or None,
+                                      int(n_rp), pml_out or None, tvar_out or None))
 
 
 def ara_layers_ylt(ctx: int, n_layers: int, layers: int, n_trials: int, ylt_out: int,

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libara_b300.so")
-SOURCES = ["ara_api.cu", "fold.cu", "ylt.cu", "select.cu", "validate.cu", "noalloc.cu", "service.cu", "yelt.cu", "plan.cu", "ingest.cu", "compact.cu"]
+SOURCES = ["ara_api.cu", "fold.cu", "ylt.cu", "select.cu", "validate.cu", "noalloc.cu", "service.cu", "yelt.cu", "plan.cu", "ingest.cu", "compact.cu", "tail.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",

@@ -561,6 +561,8 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_sel_in);
   cudaFree(c->d_sel_ws);
   cudaFree(c->d_sel_out);
+  cudaFree(c->d_tail_scratch);
+  cudaFree(c->d_tail);
   cudaFree(c->d_sel_ws_batch);
   cudaFree(c->d_sel_out_batch);
   cudaFree(c->d_pair_table);
@@ -937,31 +939,30 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
   return ARA_OK;
 }
 
-ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *rps, int32_t n_rp,
-                        double *pml_out, double *tvar_out) {
-  ARA_ENTER(c);
-  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
-  if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps || !pml_out || !tvar_out)
-    return fail(c, ARA_E_INVALID_ARG, "need 1..%d return periods and output arrays", kMaxReturnPeriods);
-  int64_t k[kMaxReturnPeriods];
-  for (int32_t r = 0; r < n_rp; ++r) {
-    if (!(rps[r] >= 1.0)) return fail(c, ARA_E_INVALID_ARG, "return period %d must be >= 1", r);
-    const double kk = std::floor((double)n / rps[r]);
-    if (kk < 1.0) return fail(c, ARA_E_INVALID_ARG, "return period %g exceeds the %lld trials", rps[r], (long long)n);
-    k[r] = (int64_t)kk;
-  }
-  cudaStream_t s = c->stream;
-  const double *src = ylt;
+namespace {
+
+// Device input for the selection: ylt itself, or a copy of a host array.
+ara_status selection_input(ara_ctx *c, const double *ylt, int64_t n, const double **src) {
+  *src = ylt;
   if (!is_device_ptr(ylt)) {
     ARA_CUDA(c, ensure(&c->d_sel_in, &c->cap_sel_in, (size_t)n), "selection input buffer");
-    ARA_CUDA(c, cudaMemcpyAsync(c->d_sel_in, ylt, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s),
+    ARA_CUDA(c, cudaMemcpyAsync(c->d_sel_in, ylt, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
              "copy YLT");
-    src = c->d_sel_in;
+    *src = c->d_sel_in;
   }
+  return ARA_OK;
+}
+
+// PML/TVaR of m values at ranks k[0..n_rp), fixed-point scale of q_count values.
+ara_status pml_tvar_ranks(ara_ctx *c, const double *vals, int64_t m, const int64_t *k, int32_t n_rp,
+                          int64_t q_count, double *pml_out, double *tvar_out) {
+  cudaStream_t s = c->stream;
+  const double *src = nullptr;
+  ara_status st = selection_input(c, vals, m, &src);
+  if (st) return st;
   ARA_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
   TimedLaunch tl(c, ARA_TIMING_PML, s);
-  ARA_CUDA(c, launch_pml_tvar(src, n, k, n_rp, c->d_sel_ws, c->d_sel_out, c->d_err, c->device, s),
+  ARA_CUDA(c, launch_pml_tvar(src, m, k, n_rp, c->d_sel_ws, c->d_sel_out, c->d_err, c->device, s, q_count),
            "PML/TVaR kernels");
   tl.done();
   double out[2 * kMaxReturnPeriods];
@@ -976,6 +977,79 @@ ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *
     tvar_out[r] = out[n_rp + r];
   }
   return ARA_OK;
+}
+
+// k_r = floor(n / RP_r) for every return period, each in [1, k_max].
+ara_status ranks_of(ara_ctx *c, int64_t n, const double *rps, int32_t n_rp, int64_t k_max, int64_t *k) {
+  if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps)
+    return fail(c, ARA_E_INVALID_ARG, "need 1..%d return periods", kMaxReturnPeriods);
+  for (int32_t r = 0; r < n_rp; ++r) {
+    if (!(rps[r] >= 1.0)) return fail(c, ARA_E_INVALID_ARG, "return period %d must be >= 1", r);
+    const double kk = std::floor((double)n / rps[r]);
+    if (kk < 1.0) return fail(c, ARA_E_INVALID_ARG, "return period %g exceeds the %lld trials", rps[r], (long long)n);
+    if (kk > (double)k_max)
+      return fail(c, ARA_E_INVALID_ARG, "return period %g needs the %.0f largest losses; the tail holds %lld", rps[r],
+                  kk, (long long)k_max);
+    k[r] = (int64_t)kk;
+  }
+  return ARA_OK;
+}
+
+}  // namespace
+
+ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *rps, int32_t n_rp,
+                        double *pml_out, double *tvar_out) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
+  if (!pml_out || !tvar_out) return fail(c, ARA_E_INVALID_ARG, "NULL output array");
+  int64_t k[kMaxReturnPeriods];
+  ara_status st = ranks_of(c, n, rps, n_rp, n, k);
+  if (st) return st;
+  return pml_tvar_ranks(c, ylt, n, k, n_rp, n, pml_out, tvar_out);
+}
+
+ara_status ara_ylt_tail(ara_ctx *c, const double *ylt, int64_t n, int64_t k, double *tail_out) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
+  if (k < 1 || k > n) return fail(c, ARA_E_INVALID_ARG, "k = %lld outside [1, %lld]", (long long)k, (long long)n);
+  if (!tail_out) return fail(c, ARA_E_INVALID_ARG, "tail_out is NULL");
+  cudaStream_t s = c->stream;
+  const double *src = nullptr;
+  ara_status st = selection_input(c, ylt, n, &src);
+  if (st) return st;
+  const bool dev = is_device_ptr(tail_out);
+  double *dst = tail_out;
+  if (!dev) {
+    ARA_CUDA(c, ensure(&c->d_tail, &c->cap_tail, (size_t)k), "tail output buffer");
+    dst = c->d_tail;
+  }
+  ARA_CUDA(c, ensure(&c->d_tail_scratch, &c->cap_tail_scratch, (size_t)kTailScratch), "tail scratch");
+  ARA_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
+  // The selection's PML at rank k is the threshold tau (d_sel_out[0]).
+  ARA_CUDA(c, launch_pml_tvar(src, n, &k, 1, c->d_sel_ws, c->d_sel_out, c->d_err, c->device, s), "select tau");
+  ARA_CUDA(c, launch_ylt_tail(src, n, k, c->d_sel_out, c->d_tail_scratch, dst, s), "tail kernels");
+  if (!dev)
+    ARA_CUDA(c, cudaMemcpyAsync(tail_out, dst, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s), "copy tail");
+  unsigned int bad = 0;
+  ARA_CUDA(c, cudaMemcpyAsync(&bad, c->d_err, sizeof(bad), cudaMemcpyDeviceToHost, s), "copy flag");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (bad) return fail(c, ARA_E_INVALID_ARG, "trial losses must be finite and >= 0");
+  return ARA_OK;
+}
+
+ara_status ara_pml_tvar_tail(ara_ctx *c, const double *tail, int64_t m, int64_t n_total, const double *rps,
+                             int32_t n_rp, double *pml_out, double *tvar_out) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (m < 1 || !tail) return fail(c, ARA_E_INVALID_ARG, "need m >= 1 tail values");
+  if (n_total < m) return fail(c, ARA_E_INVALID_ARG, "n_total %lld < m %lld", (long long)n_total, (long long)m);
+  if (!pml_out || !tvar_out) return fail(c, ARA_E_INVALID_ARG, "NULL output array");
+  int64_t k[kMaxReturnPeriods];
+  ara_status st = ranks_of(c, n_total, rps, n_rp, m, k);
+  if (st) return st;
+  return pml_tvar_ranks(c, tail, m, k, n_rp, n_total, pml_out, tvar_out);
 }
 
 ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, int64_t n_trials,

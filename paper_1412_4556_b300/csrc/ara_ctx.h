@@ -131,6 +131,10 @@ struct ara_ctx {
   size_t cap_sel_ws_batch = 0;
   double *d_sel_out_batch = nullptr;
   size_t cap_sel_out_batch = 0;
+  int64_t *d_tail_scratch = nullptr;        // ara_ylt_tail: block counts
+  size_t cap_tail_scratch = 0;
+  double *d_tail = nullptr;                 // ara_ylt_tail: output for host callers
+  size_t cap_tail = 0;
   ulonglong2 *d_pair_table = nullptr;       // two layers' tables interleaved
   size_t cap_pair_table = 0;
   uint32_t *d_pair_bitmap = nullptr;        // union of their bitmaps

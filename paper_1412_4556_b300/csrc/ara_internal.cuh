@@ -332,11 +332,21 @@ constexpr size_t kSelectWorkspaceMax = 32 * 1024;
 // Record the message of a failed call that has no context (read back with
 // ara_last_error(NULL)).
 void set_context_free_error(const char *msg);
+// q_count (>= n when given) sets the fixed-point scale of the tail sums as
+// if that many values were summed: the tail form (ara_pml_tvar_tail) passes
+// the full YLT's trial count, so its sums use the scale the full YLT's would.
 cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp,
                             void *ws, double *out_pml_tvar /* device, 2*n_rp */,
-                            unsigned int *err_flag, int device, cudaStream_t s);
+                            unsigned int *err_flag, int device, cudaStream_t s, int64_t q_count = 0);
 cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, const int64_t *k,
                                   int n_rp, void *ws, double *out, unsigned int *err_flag,
-                                  int device, cudaStream_t s);
+                                  int device, cudaStream_t s, int64_t q_count = 0);
+
+// The k largest of n values (tail.cu): tau (device) is the k-th largest, as
+// the selection wrote it; out gets the values above tau in index order, then
+// copies of tau, k in all.  scratch holds kTailScratch entries.
+constexpr int kTailScratch = 1024;
+cudaError_t launch_ylt_tail(const double *y, int64_t n, int64_t k, const double *tau, int64_t *scratch,
+                            double *out, cudaStream_t s);
 
 }  // namespace ara

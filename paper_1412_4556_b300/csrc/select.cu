@@ -144,7 +144,7 @@ __device__ __forceinline__ int select_q(unsigned long long max_key, int64_t n) {
 
 // grid.y = return period index, grid.z = layer.
 __global__ void __launch_bounds__(kSelectThreads)
-select_sum_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, SelState *states,
+select_sum_kernel(const double *__restrict__ ylts, int64_t n, int64_t q_count, int n_rp, SelState *states,
                   double *outs) {
   const double *__restrict__ y = ylts + (size_t)blockIdx.z * (size_t)n;
   SelState *st = states + blockIdx.z;
@@ -156,7 +156,7 @@ select_sum_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, SelState
   const int tid = threadIdx.x;
   const unsigned long long tau = st->prefix[r];
   const unsigned long long max_key = st->max_key;
-  const int q = select_q(max_key, n);
+  const int q = select_q(max_key, q_count);
   U128 acc{0ull, 0ull};
   unsigned long long cnt = 0ull;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -215,7 +215,8 @@ select_sum_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, SelState
 
 cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, const int64_t *k,
                                   int n_rp, void *ws, double *out, unsigned int *err_flag,
-                                  int device, cudaStream_t s) {
+                                  int device, cudaStream_t s, int64_t q_count) {
+  if (q_count < n) q_count = n;
   SelState *st = reinterpret_cast<SelState *>(ws);
   KArgs ka;
   for (int i = 0; i < kMaxReturnPeriods; ++i) ka.k[i] = i < n_rp ? (long long)k[i] : 1;
@@ -238,13 +239,13 @@ cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, c
   int64_t bx = (blocks + n_rp - 1) / n_rp;
   if (bx < 1) bx = 1;
   select_sum_kernel<<<dim3((unsigned)bx, (unsigned)n_rp, (unsigned)n_layers), kSelectThreads, 0, s>>>(
-      ylts, n, n_rp, st, out);
+      ylts, n, q_count, n_rp, st, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pml_tvar(const double *ylt, int64_t n, const int64_t *k, int n_rp, void *ws,
-                            double *out, unsigned int *err_flag, int device, cudaStream_t s) {
-  return launch_pml_tvar_batch(ylt, 1, n, k, n_rp, ws, out, err_flag, device, s);
+                            double *out, unsigned int *err_flag, int device, cudaStream_t s, int64_t q_count) {
+  return launch_pml_tvar_batch(ylt, 1, n, k, n_rp, ws, out, err_flag, device, s, q_count);
 }
 
 }  // namespace ara

@@ -1,7 +1,9 @@
-"""Host logic of the multi-GPU path on CPU: two gloo ranks each price their own
-block of trials (as bench.py does under torchrun), all-gather the shard YLTs
-and derive the portfolio-wide PML/TVaR on rank 0.  The oracle stands in for
-the device kernels, so this runs without a GPU."""
+"""Host logic of the multi-GPU path on CPU: gloo ranks each price their own
+block of trials (as bench.py does under torchrun), all-gather their largest
+losses (bench.tail_size of them, as ara_ylt_tail sends) and derive the
+portfolio-wide PML/TVaR on rank 0.  The oracle and NumPy stand in for the
+device kernels, so this runs without a GPU: PML/TVaR of the union padded
+with zero losses to the whole trial count equal those of the whole YLT."""
 import os
 import socket
 
@@ -33,38 +35,46 @@ def _worker(rank, world, port, out):
     import oracle
     w = _shard(rank)
     ylt, _ = oracle.layer_ylt(w.yet, w.pool, w.layers[0], threads=1)
-    t = torch.from_numpy(ylt)
+    import bench
+    k = bench.tail_size(ylt.size, world, RPS)
+    t = torch.from_numpy(np.sort(ylt)[-k:].copy())  # this shard's k largest
     parts = [torch.empty_like(t) for _ in range(world)]
     dist.all_gather(parts, t)
     if rank == 0:
-        import bench
-        merged = bench.merge_shard_ylts([p.numpy() for p in parts])
-        pml, tvar = oracle.pml_tvar(merged, [10.0, 30.0])
-        out.put((merged, pml, tvar))
+        union = bench.merge_shard_tails([p.numpy() for p in parts])
+        n_total = ylt.size * world
+        padded = np.concatenate([union, np.zeros(n_total - union.size)])
+        pml, tvar = oracle.pml_tvar(padded, RPS)
+        out.put((union, pml, tvar))
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_two_rank_shards_gather_and_merge():
-    world = 2
+RPS = [10.0, 30.0]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_shards_exchange_tails_and_merge(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    merged, pml, tvar = q.get(timeout=120)
+    union, pml, tvar = q.get(timeout=120)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
+    import bench
     import oracle
     ref = []
     for r in range(world):
         w = _shard(r)
         ref.append(oracle.layer_ylt(w.yet, w.pool, w.layers[0], threads=1)[0])
     ref = np.concatenate(ref)
-    np.testing.assert_array_equal(merged, ref)
-    pml_r, tvar_r = oracle.pml_tvar(ref, [10.0, 30.0])
+    k = bench.tail_size(ref.size // world, world, RPS)
+    assert union.size == k * world and k == min(ref.size // world, ref.size // 10)
+    pml_r, tvar_r = oracle.pml_tvar(ref, RPS)
     np.testing.assert_array_equal(pml, pml_r)
     np.testing.assert_array_equal(tvar, tvar_r)
     # the ranks priced different trials
