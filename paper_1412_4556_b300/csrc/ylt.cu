@@ -101,6 +101,7 @@ __device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]
 // The 8 ids of a difference-coded chunk (see compact.cu): a 21-bit base and
 // seven 15-bit steps; a step of 0x7FFF marks an empty slot, read as the
 // sentinel id (table entry zero).
+template <bool FULL>
 __device__ __forceinline__ void delta_ids(int4 c, uint32_t zero_id, uint32_t (&id)[8]) {
   const uint32_t x = (uint32_t)c.x, y = (uint32_t)c.y, z = (uint32_t)c.z, w = (uint32_t)c.w;
   uint32_t d[8];
@@ -116,7 +117,7 @@ __device__ __forceinline__ void delta_ids(int4 c, uint32_t zero_id, uint32_t (&i
 #pragma unroll
   for (int k = 1; k < 8; ++k) {
     cur += d[k];
-    id[k] = d[k] == 0x7FFFu ? zero_id : cur;
+    id[k] = FULL || d[k] != 0x7FFFu ? cur : zero_id;  // FULL: a chunk that is not a trial's last
   }
 }
 
@@ -268,8 +269,11 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
       fb = coff[min(t0 + 3 * TPW, t_end)] & OFF;
     }
     const int4 sentv = dfl ? sentd : sent4;
-    int nk_max = nk;
-    if constexpr (TPW > 1) nk_max = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)nk);
+    int nk_max = nk, nk_min = nk;
+    if constexpr (TPW > 1) {
+      nk_max = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)nk);
+      if constexpr (LAYOUT == 2) nk_min = (int)__reduce_min_sync(0xFFFFFFFFu, (unsigned)nk);
+    }
     const int4 *tp = chunks + p0;
     Acc<EB, G> acc;
 #pragma unroll
@@ -302,7 +306,11 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
         uint32_t idv[IDS];
         if constexpr (LAYOUT == 2) {
           if (dfl) {
-            delta_ids(v[u], zero_id, idv);
+            // warp-uniform: no lane holds the last chunk of its trial, so no slot is empty
+            if (base + LPT * (u + 1) < nk_min)
+              delta_ids<true>(v[u], zero_id, idv);
+            else
+              delta_ids<false>(v[u], zero_id, idv);
           } else {
             uint32_t id6[6];
             chunk_ids<true>(v[u], id6);
