@@ -93,11 +93,6 @@ __device__ __forceinline__ void chunk_ids(int4 c, uint32_t (&id)[PACKED ? 6 : 4]
   }
 }
 
-// Adds the table entries of `id` for G layers (16 bytes each, interleaved)
-// to the accumulators when `hit` is set: a predicated gather (G = 2 is one
-// 32-byte load, i.e. one L2 sector for two layers) and predicated
-// add/add-with-carry, so occurrences whose bitmap bit is clear cost neither a
-// memory request nor register moves.
 // The 8 ids of a difference-coded chunk (see compact.cu): a 21-bit base and
 // seven 15-bit steps; a step of 0x7FFF marks an empty slot, read as the
 // sentinel id (table entry zero).
