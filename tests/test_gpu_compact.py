@@ -99,3 +99,32 @@ def test_compact_is_a_no_op_for_wide_catalogs(engine):
     ref = engine.layer_ylt(h)
     engine.compact_yet()
     np.testing.assert_array_equal(engine.layer_ylt(h), ref)
+
+
+def test_service_on_a_compacted_yet(engine):
+    """Service batches price one-layer passes from the compact stream and
+    multi-layer passes from the stored layout; every result equals the same
+    request priced on the stored layout."""
+    from paper_1412_4556_b300 import ARA_FP32_TABLE, ARA_FP64, Service
+    w = S.batched(n_layers=1, n_trials=20_000, lam=300.0, catalog_size=300_000, n_pool=24)
+    reqs = S.service_requests(n_requests=16, rate_per_s=1000.0, n_pool=24, trial_choices=(2_000, 20_000))
+    rps = (10.0, 100.0)
+
+    def run(compact):
+        engine.load_yet_from(w.yet)
+        if compact:
+            engine.compact_yet()
+        first = engine.load_pool(w.pool)
+        with Service(engine, rps, slots=2, max_batch=4) as svc:
+            ts = [svc.submit([first + j for j in rq.layer.elts], rq.layer.occ_ret, rq.layer.occ_lim,
+                             rq.layer.agg_ret, rq.layer.agg_lim, rq.n_trials,
+                             precision=ARA_FP32_TABLE if i % 2 else ARA_FP64, want_ylt=True)
+                  for i, rq in enumerate(reqs)]
+            return [svc.wait(t) for t in ts]
+
+    stored, compacted = run(False), run(True)
+    for a, b in zip(stored, compacted):
+        assert a.ok and b.ok
+        np.testing.assert_array_equal(b.ylt.view(np.uint64), a.ylt.view(np.uint64))
+        np.testing.assert_array_equal(b.pml, a.pml)
+        np.testing.assert_array_equal(b.tvar, a.tvar)
