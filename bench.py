@@ -199,36 +199,61 @@ def ncu_traffic_per_launch(occurrences: int):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(w, budget_s: float = 12.0, threads=None, max_trials=None):
-    """Time the FP64 oracle (literal Algorithm 1) on a bounded trial sample."""
+def sample_yet(yet, sel):
+    """A YET of the trials sel (ascending indices) of yet, in CSR form."""
+    lens = yet.offsets[sel + 1] - yet.offsets[sel]
+    off = np.zeros(sel.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    src = np.arange(off[-1], dtype=np.int64) + np.repeat(yet.offsets[sel] - off[:-1], lens)
+    return S.YET(yet.catalog_size, off, yet.ids[src], None)
+
+
+def _time_oracle(w, sel, threads):
+    """Seconds of one oracle call (literal Algorithm 1) on the trials sel and
+    their occurrence count.  A sample of a tenth of the trials or less is
+    priced as a YET of its own (built before the clock starts), so the
+    oracle's per-call pass over its input covers the sample, not the whole
+    YET; a larger one goes through the oracle's trial selection."""
     import oracle
-    threads = threads or os.cpu_count() or 1
     layer = w.layers[0]
-    rng = np.random.default_rng(5)
-    n = w.yet.n_trials
-    # Two probes separate the fixed cost (building the direct access tables)
-    # from the per-trial cost; the sample is then sized to the time budget.
-    sizes = [min(n, 2048), min(n, 16384)]
-    times = []
-    for m in sizes:
-        probe = np.sort(rng.choice(n, m, replace=False))
+    occ = int((w.yet.offsets[sel + 1] - w.yet.offsets[sel]).sum())
+    if sel.size * 10 <= w.yet.n_trials:
+        y = sample_yet(w.yet, sel)
         t0 = time.perf_counter()
-        oracle.layer_ylt(w.yet, w.pool, layer, trials=probe, mode="literal", threads=threads)
-        times.append(time.perf_counter() - t0)
+        oracle.layer_ylt(y, w.pool, layer, mode="literal", threads=threads)
+    else:
+        t0 = time.perf_counter()
+        oracle.layer_ylt(w.yet, w.pool, layer, trials=sel, mode="literal", threads=threads)
+    return time.perf_counter() - t0, occ
+
+
+def oracle_cost_model(w, threads, rng):
+    """(fixed seconds per call, seconds per trial) of the oracle on this host,
+    from two probes of 2,048 and 16,384 trials."""
+    n = w.yet.n_trials
+    sizes = [min(n, 2048), min(n, 16384)]
+    times = [_time_oracle(w, np.sort(rng.choice(n, m, replace=False)), threads)[0] for m in sizes]
     if sizes[1] > sizes[0]:
-        per_trial = max((times[1] - times[0]) / (sizes[1] - sizes[0]), 1e-7)
+        per_trial = max((times[1] - times[0]) / (sizes[1] - sizes[0]), 1e-8)
         fixed = max(times[0] - sizes[0] * per_trial, 0.0)
     else:
-        per_trial, fixed = max(times[1] / max(sizes[1], 1), 1e-7), 0.0
-    k = int(min(n, max(sizes[1], (budget_s - fixed) / per_trial)))
+        per_trial, fixed = max(times[1] / max(sizes[1], 1), 1e-8), 0.0
+    return fixed, per_trial
+
+
+def oracle_sample(w, budget_s: float = 12.0, threads=None, model=None, rng=None):
+    """Time the FP64 oracle (literal Algorithm 1) on a bounded trial sample
+    sized to about budget_s seconds."""
+    threads = threads or os.cpu_count() or 1
+    rng = rng or np.random.default_rng(5)
+    n = w.yet.n_trials
+    fixed, per_trial = model or oracle_cost_model(w, threads, rng)
+    k = int(min(n, max(256, (budget_s - fixed) / per_trial)))
     sel = np.sort(rng.choice(n, k, replace=False))
-    occ = int(np.diff(w.yet.offsets)[sel].sum())
-    t0 = time.perf_counter()
-    oracle.layer_ylt(w.yet, w.pool, layer, trials=sel, mode="literal", threads=threads)
-    dt = time.perf_counter() - t0
+    dt, occ = _time_oracle(w, sel, threads)
     return {"value": occ / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{k} of {n} trials ({occ} trial-events), literal Algorithm 1 "
-                      f"(16 direct-access-table lookups per event), {dt:.1f} s including the "
+                      f"(16 direct-access-table lookups per event), {dt:.2f} s including the "
                       f"table build"}
 
 
@@ -732,13 +757,18 @@ def run_reference(args):
         return
     w = S.paper_scale(n_trials=args.trials)
     M = w.yet.n_occurrences
-    per = max(2.0, min(args.cpu_budget, 150.0 / max(args.steps + args.warmup, 1)))
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(5)
+    model = oracle_cost_model(w, threads, rng)
+    # Each timed step prices a fresh trial sample sized so that the whole run
+    # stays within a few minutes; warm-up steps price 256 trials.
+    per = max(0.25, min(args.cpu_budget, 150.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
-        oracle_sample(w, budget_s=per / 4)
+        oracle_sample(w, budget_s=0.0, threads=threads, model=model, rng=rng)
     vals, samples = [], []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        r = oracle_sample(w, budget_s=per)
+        r = oracle_sample(w, budget_s=per, threads=threads, model=model, rng=rng)
         vals.append(r["value"])
         samples.append(r)
     wall = time.perf_counter() - t_all
@@ -749,8 +779,10 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
         "config": {"workload": WORKLOAD, "n_trials_per_gpu": w.yet.n_trials, "occurrences_per_gpu": M,
-                   "note": "each step times the oracle on a bounded trial sample; ms_per_step is "
-                           "extrapolated to the full workload from the measured rate"},
+                   "note": "each step times the oracle on a fresh bounded trial sample (about "
+                           f"{per:.2f} s of it, so that the run ends within minutes; the oracle's fixed "
+                           "cost per call, its table build, weighs more in short samples); "
+                           "ms_per_step is extrapolated to the full workload from the median rate"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[-1]["cores"], "kind": "oracle",
                          "sample": samples[-1]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
