@@ -271,15 +271,19 @@ def paper_full():
 
 def test_paper_scale_full_size_sampled(paper_full):
     """1,000,000 trials x Poisson(1000) events (~1e9 occurrences), 16 ELTs, in
-    the launch configuration the benchmark times; the oracle checks a sample
-    of trials one by one, plus properties that hold at any size."""
+    the launch configuration the benchmark times (compact id stream; the
+    stored layout gives the same bits); the oracle checks a sample of trials
+    one by one, plus properties that hold at any size."""
     from paper_1412_4556_b300 import Engine
     w = paper_full
     layer = w.layers[0]
     with Engine(0) as e:
         (L,) = load_workload(e, w)
+        stored = e.layer_ylt(L)
+        e.compact_yet()  # the benchmark prices from the compact id stream
         g = e.layer_ylt(L)
         pml_g, tvar_g = e.pml_tvar(g, w.return_periods)
+    np.testing.assert_array_equal(g.view(np.uint64), stored.view(np.uint64))
     assert g.shape == (1_000_000,)
     assert np.all(g >= 0) and np.all(g <= layer.agg_lim)
     counts = np.diff(w.yet.offsets)
