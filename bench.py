@@ -751,6 +751,127 @@ def run_service(args):
 
 
 # ------------------------------------------------------------ oracle arm
+YELT_WORKLOAD = ("paper-scale Year Event Loss Table, FP64: the paper-scale YET and layer; step = "
+                 "ara_define_layer + ara_layer_yelt (every occurrence's increment and each trial's "
+                 "largest, device outputs) + ara_rpl_report (AEP/OEP return period losses, RP "
+                 "100/250/500)")
+
+
+def run_yelt(args):
+    """Year Event Loss Table and RPL reports (per-occurrence output): each
+    rank prices its own trials (weak scaling, no exchange)."""
+    import torch
+    from paper_1412_4556_b300 import ARA_TIMING_YELT, Engine
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(dev)
+    w = S.paper_scale(seed=shard_seed(S.DEFAULT_SEED, rank), n_trials=args.trials)
+    layer = w.layers[0]
+    rps = w.return_periods
+    M, N, C = w.yet.n_occurrences, w.yet.n_trials, w.yet.catalog_size
+    stream = torch.cuda.Stream(device=dev)
+    eng = Engine(local, stream=stream)
+    eng.load_yet_from(w.yet)
+    first = eng.load_pool(w.pool)
+    handles = [first + j for j in layer.elts]
+    yelt = torch.empty(M, dtype=torch.float64, device=dev)
+    occ_max = torch.empty(N, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def define():
+        return eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
+
+    def step():
+        L = define()
+        eng.layer_yelt(L, out=yelt, occ_max=occ_max, stream=stream)
+        rep = eng.rpl_report(L, rps)
+        eng.release_layer(L)
+        return rep
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        clocks.wait_first_sample()
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        t_start = time.monotonic()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rep = step()
+        ev1.record(stream)
+        barrier()
+        t_end = time.monotonic()
+        # the YELT kernel alone (with its per-occurrence output), for the roofline
+        L = define()
+        eng.layer_yelt(L, out=yelt, occ_max=occ_max, stream=stream)
+        eng.set_kernel_timing(True)
+        for _ in range(args.steps):
+            eng.layer_yelt(L, out=yelt, occ_max=occ_max, stream=stream)
+        n_k, k_ms = eng.kernel_timing(ARA_TIMING_YELT)
+        eng.set_kernel_timing(True)
+        for _ in range(args.steps):
+            eng.rpl_report(L, rps)
+        n_r, r_ms = eng.kernel_timing(ARA_TIMING_YELT)
+        eng.set_kernel_timing(False)
+        eng.release_layer(L)
+        torch.cuda.synchronize()
+        time.sleep(0.3)
+        clocks.mark(t_start, t_end)
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    kern_ms = k_ms / max(n_k, 1)
+    # ids read, increments written, per-trial maxima written, chunk and raw
+    # offsets read, one FP64 table read
+    alg_bytes = 4 * M + 8 * M + 8 * N + 16 * (N + 1) + 8 * C
+    peak, peak_kind = measured_hbm_peak()
+    eng.close()
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    line = {
+        "metric": "YELT trial-events/s (per-occurrence increments + AEP/OEP report)",
+        "value": M * world / (ms_step / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": YELT_WORKLOAD, "n_trials_per_gpu": N, "occurrences_per_gpu": M,
+                   "yelt_bytes_per_step": 8 * M,
+                   "l2": "inputs larger than L2: the 2.67 GB id stream and the 8 GB YELT pass through HBM "
+                         "every step"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "yelt_kernel",
+                     "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_kind": peak_kind, "frac_of_nominal_8000_gbs": achieved / 8000.0},
+        "breakdown_ms": {"yelt_kernel_with_output": kern_ms,
+                         "rpl_report_yelt_kernel": r_ms / max(n_r, 1)},
+        "rpl": {k: v.tolist() for k, v in rep.items()},
+        "clocks": clocks.summary(),
+        "gpu_launches": args.steps * (1 + 1 + 1 + 10),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -797,9 +918,10 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
-    ap.add_argument("--workload", choices=["paper", "batched", "mixed", "service"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "batched", "mixed", "service", "yelt"], default="paper",
                     help="paper: the single-layer paper-scale step (default); batched: 64 layers; "
-                         "mixed: 64 FP32-table layers; service: the pricing-request stream")
+                         "mixed: 64 FP32-table layers; service: the pricing-request stream; "
+                         "yelt: the Year Event Loss Table and RPL report")
     ap.add_argument("--requests", type=int, default=2000, help="service: requests in the stream")
     ap.add_argument("--rate", type=float, default=50.0, help="service: Poisson arrival rate per s")
     ap.add_argument("--slots", type=int, default=4, help="service: batches in flight")
@@ -820,6 +942,8 @@ def main():
         run_batched(args)
     elif args.workload == "service":
         run_service(args)
+    elif args.workload == "yelt":
+        run_yelt(args)
     else:
         run_engine(args)
 

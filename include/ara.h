@@ -69,6 +69,7 @@ typedef int32_t ara_status;
 #define ARA_TIMING_YLT 0  /* the per-trial gather/sum kernel */
 #define ARA_TIMING_FOLD 1 /* the per-layer ELT fold (pre-pass) kernel */
 #define ARA_TIMING_PML 2  /* the PML/TVaR selection kernels, summed */
+#define ARA_TIMING_YELT 3 /* the Year Event Loss Table kernel (ara_layer_yelt, ara_rpl_report) */
 
 /* ------------------------------------------------------------------ setup */
 

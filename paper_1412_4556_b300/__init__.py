@@ -19,11 +19,11 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 
 from . import _native
-from ._native import (ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_FOLD, ARA_TIMING_PML, ARA_TIMING_YLT,
-                      AraError)
+from ._native import (ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_FOLD, ARA_TIMING_PML, ARA_TIMING_YELT,
+                      ARA_TIMING_YLT, AraError)
 
 __all__ = ["Engine", "Plan", "Service", "ServiceResult", "AraError", "ARA_FP64", "ARA_FP32_TABLE",
-           "ARA_TIMING_YLT", "ARA_TIMING_FOLD", "ARA_TIMING_PML"]
+           "ARA_TIMING_YLT", "ARA_TIMING_FOLD", "ARA_TIMING_PML", "ARA_TIMING_YELT"]
 
 
 def _is_tensor(a) -> bool:

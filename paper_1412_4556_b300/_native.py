@@ -20,6 +20,7 @@ ARA_FP32_TABLE = 1
 ARA_TIMING_YLT = 0
 ARA_TIMING_FOLD = 1
 ARA_TIMING_PML = 2
+ARA_TIMING_YELT = 3
 
 STATUS_NAMES = {
     0: "ARA_OK", -1: "ARA_E_INVALID_ARG", -2: "ARA_E_EVENT_RANGE", -3: "ARA_E_DUP_EVENT",

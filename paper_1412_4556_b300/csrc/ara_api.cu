@@ -1123,9 +1123,11 @@ ara_status ara_layer_yelt(ara_ctx *c, int32_t layer, int64_t n_trials, double *y
     odst = c->d_ylt_stage;
   }
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, nullptr};
+  TimedLaunch tl(c, ARA_TIMING_YELT, s);
   ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table,
                           L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, ydst, odst, c->device, s),
            "YELT kernel launch");
+  tl.done();
   if (yelt_out && !ydev)
     ARA_CUDA(c, cudaMemcpyAsync(yelt_out, ydst, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, s),
              "copy YELT");
@@ -1160,10 +1162,12 @@ ara_status ara_rpl_report(ara_ctx *c, int32_t layer, int64_t n_trials, const dou
   // [0, n): trial losses (AEP); [n, 2n): largest increment per trial (OEP)
   ARA_CUDA(c, ensure(&c->d_sel_in, &c->cap_sel_in, 2 * (size_t)n_trials), "report buffer");
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, c->d_sel_in};
+  TimedLaunch tl(c, ARA_TIMING_YELT, s);
   ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table,
                           L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, nullptr, c->d_sel_in + n_trials,
                           c->device, s),
            "YELT kernel launch");
+  tl.done();
   ARA_CUDA(c, ensure(&c->d_sel_ws_batch, &c->cap_sel_ws_batch, 2 * select_workspace_bytes(kMaxReturnPeriods)),
            "selection workspace");
   ARA_CUDA(c, ensure(&c->d_sel_out_batch, &c->cap_sel_out_batch, 4 * (size_t)n_rp), "selection output");
@@ -1253,7 +1257,7 @@ ara_status ara_set_kernel_timing(ara_ctx *c, int32_t enable) {
 
 ara_status ara_kernel_timing(ara_ctx *c, int32_t channel, int64_t *launches, double *total_ms) {
   ARA_ENTER(c);
-  if (channel < 0 || channel > 2 || !launches || !total_ms)
+  if (channel < 0 || channel > ARA_TIMING_YELT || !launches || !total_ms)
     return fail(c, ARA_E_INVALID_ARG, "bad timing channel or NULL output");
   TimingChannel &ch = c->chan[channel];
   for (auto &ev : ch.events) {

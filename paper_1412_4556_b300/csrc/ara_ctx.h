@@ -144,7 +144,7 @@ struct ara_ctx {
   unsigned int *d_err = nullptr;            // PML/TVaR input check flag
   // timing
   bool timing = false;
-  TimingChannel chan[3];
+  TimingChannel chan[4];
   // pricing service that owns the context while attached (service.cu)
   ara_service *service = nullptr;
   // live pricing plans (plan.cu), destroyed with the context

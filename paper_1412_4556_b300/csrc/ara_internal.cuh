@@ -166,6 +166,22 @@ __device__ __forceinline__ double from_fixed_int(U128 a, int q) {
                                           (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// from_fixed_int for an integer of at most 53 significant bits (every single
+// table entry: to_fixed keeps one binary64 mantissa), which converts without
+// rounding: the same bits as from_fixed_int, with no rounding logic and no
+// branches on the common path.
+__device__ __forceinline__ double from_fixed_exact(U128 a, int q) {
+  const bool h = a.hi != 0ull;
+  const int lzh = __clzll((long long)a.hi), lzl = __clzll((long long)a.lo);
+  const int lz = h ? lzh : 64 + lzl;
+  // the 64 bits from the leading one down ((lo >> (63 - lzh)) >> 1 is lo >> (64 - lzh), 0 for lzh = 0)
+  const unsigned long long top = h ? (a.hi << lzh) | ((a.lo >> (63 - lzh)) >> 1) : a.lo << (lzl & 63);
+  const int biased = 127 - lz + q + 1023;
+  if ((a.hi | a.lo) == 0ull) return 0.0;
+  if (biased <= 0 || biased >= 2047) return from_fixed(a, q);
+  return __longlong_as_double((long long)(((unsigned long long)biased << 52) | ((top >> 11) & 0xFFFFFFFFFFFFFull)));
+}
+
 // a >= b for 128-bit unsigned integers.
 __device__ __forceinline__ bool ge128(U128 a, U128 b) {
   return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);

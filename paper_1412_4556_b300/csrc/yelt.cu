@@ -108,6 +108,9 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
   const int64_t t_begin = n_trials * w / n_warps;
   const int64_t t_end = n_trials * (w + 1) / n_warps;
   const bool exact = L.af.exact != 0;
+  // AggR + AggL on the grid, saturated (an unreachable limit stays unreachable)
+  U128 ret_lim = add(L.af.ret, L.af.lim);
+  if (!ge128(ret_lim, L.af.ret)) ret_lim = U128{~0ull, ~0ull};
 
   for (int64_t t = t_begin; t < t_end; ++t) {
     const int64_t p0 = coff[t];
@@ -115,7 +118,8 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
     const int64_t r0 = raw_off[t];
     const int64_t nr = raw_off[t + 1] - r0;  // occurrences of trial t
     U128 carry{0ull, 0ull};                  // running sum before this step
-    double best = 0.0;                       // largest increment seen by this lane
+    unsigned long long best = 0ull;          // largest increment seen by this lane, as bits
+                                             // (increments are >= 0: bits order like values)
     for (int base = 0; base < nk; base += 32) {
       const int j = base + lane;
       const int4 v = j < nk ? chunks[p0 + j] : sent4;
@@ -145,9 +149,36 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       const U128 step_total = shfl_u128(incl, 31);
       // running sum before this lane's first id: carry + exclusive prefix
       U128 P = sub128(add(carry, incl), tot);
+      const int64_t k0 = (int64_t)j * IDS;  // index of id[0] within the trial
+      const int64_t left = nr - k0;          // this lane's ids that are occurrences (may be <= 0)
+      const int valid = left < IDS ? (int)(left > 0 ? left : 0) : IDS;
+      double *const out = yelt ? yelt + r0 + k0 : nullptr;
+      // Fast path (warp-uniform): every lane's chunk lies wholly below the
+      // retention (a stays 0), wholly beyond the exhausted limit (a stays
+      // AggL), or wholly inside the layer (a_k = P_k - AggR, so each
+      // increment is the occurrence's own entry, exactly).
+      bool inside = false;
+      bool fast = false;
+      if (exact) {
+        const U128 P1 = add(P, tot);
+        inside = ge128(P, L.af.ret) && ge128(ret_lim, P1);
+        fast = __all_sync(0xFFFFFFFFu, inside || ge128(L.af.ret, P1) || ge128(P, ret_lim));
+      }
+      if (fast) {
+#pragma unroll
+        for (int i = 0; i < IDS; ++i) {
+          const double inc = inside ? from_fixed_exact(x[i], L.q) : 0.0;
+          if (i < valid) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(inc);
+            best = b > best ? b : best;
+            if (out) out[i] = inc;
+          }
+        }
+        carry = add(carry, step_total);
+        continue;
+      }
       U128 a_fx = exact ? clamp_fixed(P, L.af) : U128{0ull, 0ull};
       double a_fp = exact ? 0.0 : clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
-      const int64_t k0 = (int64_t)j * IDS;  // index of id[0] within the trial
 #pragma unroll
       for (int i = 0; i < IDS; ++i) {
         P = add(P, x[i]);
@@ -161,17 +192,21 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
           inc = __dsub_rn(a, a_fp);
           a_fp = a;
         }
-        if (k0 + i < nr) {
-          best = fmax(best, inc);
-          if (yelt) yelt[r0 + k0 + i] = inc;
+        if (i < valid) {
+          const unsigned long long b = (unsigned long long)__double_as_longlong(inc);
+          best = b > best ? b : best;
+          if (out) out[i] = inc;
         }
       }
       carry = add(carry, step_total);
     }
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) best = fmax(best, __shfl_xor_sync(0xFFFFFFFFu, best, m));
+    for (int m = 16; m > 0; m >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, best, m);
+      best = o > best ? o : best;
+    }
     if (lane == 0) {
-      if (occ_max) occ_max[t] = best;
+      if (occ_max) occ_max[t] = __longlong_as_double((long long)best);
       if (L.ylt) L.ylt[t] = trial_loss(carry, L.q, L.af, L.agg_ret, L.agg_lim);
     }
   }
