@@ -91,7 +91,9 @@ __device__ __forceinline__ void chunk_ids_y(int4 c, uint32_t (&id)[PACKED ? 6 : 
   }
 }
 
-template <bool PACKED, int EB>
+// OUT: the per-occurrence increments are written (else only the trial
+// maxima and losses, as for the return period report).
+template <bool PACKED, int EB, bool OUT>
 __global__ void __launch_bounds__(kYltThreads, 1)
 yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
             const int64_t *__restrict__ raw_off, int64_t n_trials, const void *__restrict__ table,
@@ -120,6 +122,7 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
     U128 carry{0ull, 0ull};                  // running sum before this step
     unsigned long long best = 0ull;          // largest increment seen by this lane, as bits
                                              // (increments are >= 0: bits order like values)
+    U128 best_fx{0ull, 0ull};                // !OUT: largest entry of the steps inside the layer
     for (int base = 0; base < nk; base += 32) {
       const int j = base + lane;
       const int4 v = j < nk ? chunks[p0 + j] : sent4;
@@ -152,7 +155,7 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       const int64_t k0 = (int64_t)j * IDS;  // index of id[0] within the trial
       const int64_t left = nr - k0;          // this lane's ids that are occurrences (may be <= 0)
       const int valid = left < IDS ? (int)(left > 0 ? left : 0) : IDS;
-      double *const out = yelt ? yelt + r0 + k0 : nullptr;
+      double *const out = OUT ? yelt + r0 + k0 : nullptr;
       // Fast path (warp-uniform): every lane's chunk lies wholly below the
       // retention (a stays 0), wholly beyond the exhausted limit (a stays
       // AggL), or wholly inside the layer (a_k = P_k - AggR, so each
@@ -164,14 +167,44 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         inside = ge128(P, L.af.ret) && ge128(ret_lim, P1);
         fast = __all_sync(0xFFFFFFFFu, inside || ge128(L.af.ret, P1) || ge128(P, ret_lim));
       }
+      if (!OUT && fast) {
+        // Inside the layer an increment is its entry, and the conversion is
+        // monotone: keep the largest entry, convert it once per trial.
+        if (inside) {
+#pragma unroll
+          for (int i = 0; i < IDS; ++i)
+            if (i < valid && ge128(x[i], best_fx)) best_fx = x[i];
+        }
+        carry = add(carry, step_total);
+        continue;
+      }
       if (fast) {
+        double inc[IDS];
 #pragma unroll
         for (int i = 0; i < IDS; ++i) {
-          const double inc = inside ? from_fixed_exact(x[i], L.q) : 0.0;
-          if (i < valid) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(inc);
-            best = b > best ? b : best;
-            if (out) out[i] = inc;
+          inc[i] = inside ? from_fixed_exact(x[i], L.q) : 0.0;
+          const unsigned long long b = (unsigned long long)__double_as_longlong(inc[i]);
+          if (i < valid) best = b > best ? b : best;
+        }
+        if (OUT) {
+          if (valid == IDS) {
+            // 16-byte stores where the pair is aligned (the parity of r0 is the
+            // same for every lane), so a warp writes half as many sectors
+            if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0u) {
+#pragma unroll
+              for (int i = 0; i + 1 < IDS; i += 2)
+                *reinterpret_cast<double2 *>(out + i) = make_double2(inc[i], inc[i + 1]);
+            } else {
+              out[0] = inc[0];
+#pragma unroll
+              for (int i = 1; i + 1 < IDS; i += 2)
+                *reinterpret_cast<double2 *>(out + i) = make_double2(inc[i], inc[i + 1]);
+              out[IDS - 1] = inc[IDS - 1];
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < IDS; ++i)
+              if (i < valid) out[i] = inc[i];
           }
         }
         carry = add(carry, step_total);
@@ -195,10 +228,14 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         if (i < valid) {
           const unsigned long long b = (unsigned long long)__double_as_longlong(inc);
           best = b > best ? b : best;
-          if (out) out[i] = inc;
+          if (OUT) out[i] = inc;
         }
       }
       carry = add(carry, step_total);
+    }
+    if (!OUT) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(from_fixed_exact(best_fx, L.q));
+      best = b > best ? b : best;
     }
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
@@ -214,17 +251,17 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
 
 }  // namespace
 
-template <bool PACKED, int EB>
+template <bool PACKED, int EB, bool OUT>
 static cudaError_t launch_yelt_t(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, int64_t n_trials,
                                  const void *table, const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel,
                                  const LayerOut &L, double *yelt, double *occ_max, int sms, cudaStream_t s) {
   const size_t smem = (size_t)bm.words * 4u;
-  cudaError_t err = cudaFuncSetAttribute(yelt_kernel<PACKED, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t err = cudaFuncSetAttribute(yelt_kernel<PACKED, EB, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
   int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
   const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
-  yelt_kernel<PACKED, EB><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table,
+  yelt_kernel<PACKED, EB, OUT><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table,
                                                          reinterpret_cast<const uint4 *>(bitmap), bm.words / 4,
                                                          bm.mul, sent4, L, yelt, occ_max);
   return cudaGetLastError();
@@ -238,15 +275,16 @@ cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *
   int sms = 148;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
-  if (entry_bytes == 16)
-    return packed ? launch_yelt_t<true, 16>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
-                                            occ_max, sms, s)
-                  : launch_yelt_t<false, 16>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
-                                             occ_max, sms, s);
-  return packed ? launch_yelt_t<true, 8>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
-                                         occ_max, sms, s)
-                : launch_yelt_t<false, 8>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt,
-                                          occ_max, sms, s);
+  const bool out = yelt != nullptr;
+#define ARA_YELT_LAUNCH(P, E, O)                                                                             \
+  launch_yelt_t<P, E, O>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt, occ_max, sms, s)
+  if (entry_bytes == 16) {
+    if (packed) return out ? ARA_YELT_LAUNCH(true, 16, true) : ARA_YELT_LAUNCH(true, 16, false);
+    return out ? ARA_YELT_LAUNCH(false, 16, true) : ARA_YELT_LAUNCH(false, 16, false);
+  }
+  if (packed) return out ? ARA_YELT_LAUNCH(true, 8, true) : ARA_YELT_LAUNCH(true, 8, false);
+  return out ? ARA_YELT_LAUNCH(false, 8, true) : ARA_YELT_LAUNCH(false, 8, false);
+#undef ARA_YELT_LAUNCH
 }
 
 }  // namespace ara
