@@ -562,6 +562,8 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_sel_ws);
   cudaFree(c->d_sel_out);
   cudaFree(c->d_tail_scratch);
+  cudaFree(c->d_evt64);
+  cudaFree(c->d_evt64_inexact);
   cudaFree(c->d_tail);
   cudaFree(c->d_sel_ws_batch);
   cudaFree(c->d_sel_out_batch);
@@ -1123,9 +1125,22 @@ ara_status ara_layer_yelt(ara_ctx *c, int32_t layer, int64_t n_trials, double *y
     odst = c->d_ylt_stage;
   }
   const LayerOut out{L->q, L->agg_fx, L->agg_ret, L->agg_lim, nullptr};
+  if (ydst) {
+    // The layer's table in binary64 (the event table), with a flag set when
+    // some value is not exactly on the table's grid: in-layer increments are
+    // then read from it instead of converted one by one.
+    ARA_CUDA(c, ensure(&c->d_evt64, &c->cap_evt64, (size_t)c->catalog + 1), "binary64 event table");
+    ARA_CUDA(c, ensure(&c->d_evt64_inexact, &c->cap_evt64_inexact, 1), "binary64 event table flag");
+    ARA_CUDA(c, cudaMemsetAsync(c->d_evt64 + c->catalog, 0, sizeof(double), s), "cudaMemsetAsync");
+    ARA_CUDA(c, cudaMemsetAsync(c->d_evt64_inexact, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
+    ARA_CUDA(c, launch_fold(L->d_desc, (int)L->elts.size(), c->catalog, L->occ_ret, L->occ_lim, L->q, nullptr,
+                            nullptr, L->bm, L->precision == ARA_FP32_TABLE, c->d_evt64, s, c->d_evt64_inexact),
+             "binary64 event table");
+  }
   TimedLaunch tl(c, ARA_TIMING_YELT, s);
   ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table,
-                          L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, ydst, odst, c->device, s),
+                          L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, ydst, odst, c->device, s,
+                          ydst ? c->d_evt64 : nullptr, c->d_evt64_inexact),
            "YELT kernel launch");
   tl.done();
   if (yelt_out && !ydev)

@@ -131,6 +131,10 @@ struct ara_ctx {
   size_t cap_sel_ws_batch = 0;
   double *d_sel_out_batch = nullptr;
   size_t cap_sel_out_batch = 0;
+  double *d_evt64 = nullptr;                // ara_layer_yelt: the layer's table in binary64
+  size_t cap_evt64 = 0;
+  unsigned int *d_evt64_inexact = nullptr;  // set when that table is not exact
+  size_t cap_evt64_inexact = 0;
   int64_t *d_tail_scratch = nullptr;        // ara_ylt_tail: block counts
   size_t cap_tail_scratch = 0;
   double *d_tail = nullptr;                 // ara_ylt_tail: output for host callers

@@ -234,9 +234,13 @@ __device__ __forceinline__ U128 warp_sum_u128(U128 v) {
 
 // --------------------------------------------------------- launchers
 // Each returns cudaSuccess or the launch error.
+// f64_out (nullable) gets every event's binary64 value; with inexact given,
+// zeros are written as +0 and inexact is set when some value is not exactly
+// on the fixed-point grid of q.
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
                         double occ_lim, int q, void *table, uint32_t *bitmap,
-                        BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s);
+                        BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s,
+                        unsigned int *inexact = nullptr);
 
 struct YltLaunch {
   int blocks;
@@ -334,10 +338,14 @@ cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const floa
 // Year Event Loss Table of one layer: per-occurrence increments into
 // yelt[raw_off[t] + k] (nullable), each trial's largest increment into
 // occ_max[t] (nullable), and the trial loss into L.ylt[t] (nullable).
+// table64 (nullable, catalog + 1 values) is the layer's table in binary64,
+// used when *inexact (device) is 0: then it holds exactly the table's
+// values and an in-layer increment is read instead of converted.
 cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
                         int64_t n_trials, const void *table, int entry_bytes, const uint32_t *bitmap,
                         BitmapLayout bm, int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max,
-                        int device, cudaStream_t s);
+                        int device, cudaStream_t s, const double *table64 = nullptr,
+                        const unsigned int *inexact = nullptr);
 
 // PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes
 // per layer; the batch form reads n_layers YLTs of n values each (layer-major)

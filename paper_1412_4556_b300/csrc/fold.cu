@@ -45,7 +45,7 @@ template <bool FP32>
 __global__ void __launch_bounds__(kFoldThreads)
 fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
             double occ_lim, int q, void *__restrict__ table, uint32_t *__restrict__ bitmap,
-            uint32_t bm_mul, double *__restrict__ f64_out) {
+            uint32_t bm_mul, double *__restrict__ f64_out, unsigned int *__restrict__ inexact) {
   using Real = typename std::conditional<FP32, float, double>::type;
   __shared__ Real x[kFoldEventsPerCta];
   __shared__ int32_t seg[kMaxLayerElts + 1];    // prefix sums of slice lengths
@@ -122,6 +122,11 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
                         __double2float_rn(occ_lim));
     else
       o = fmin(fmax(__dsub_rn(x[i], occ_ret), 0.0), occ_lim);
+    if (inexact) {
+      o = o == 0.0 ? 0.0 : o;  // +0: what the conversion of a zero entry gives
+      const U128 v = to_fixed(o, q);
+      if (__double_as_longlong(from_fixed_exact(v, q)) != __double_as_longlong(o)) atomicOr(inexact, 1u);
+    }
     if (f64_out) f64_out[e] = o;
     if (table) {
       const U128 v = to_fixed(o, q);
@@ -138,15 +143,15 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
 
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
                         double occ_lim, int q, void *table, uint32_t *bitmap,
-                        BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s) {
+                        BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s, unsigned int *inexact) {
   if (catalog <= 0) return cudaSuccess;
   const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
   if (fp32)
     fold_kernel<true><<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
-                                                       table, bitmap, bm.mul, f64_out);
+                                                       table, bitmap, bm.mul, f64_out, inexact);
   else
     fold_kernel<false><<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
-                                                        table, bitmap, bm.mul, f64_out);
+                                                        table, bitmap, bm.mul, f64_out, inexact);
   return cudaGetLastError();
 }
 

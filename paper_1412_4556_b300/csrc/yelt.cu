@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kYltThreads, 1)
 yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
             const int64_t *__restrict__ raw_off, int64_t n_trials, const void *__restrict__ table,
             const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul, int4 sent4, LayerOut L,
-            double *__restrict__ yelt, double *__restrict__ occ_max) {
+            double *__restrict__ yelt, double *__restrict__ occ_max, const double *__restrict__ table64,
+            const unsigned int *__restrict__ inexact) {
   constexpr int IDS = PACKED ? 6 : 4;
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
@@ -110,6 +111,8 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
   const int64_t t_begin = n_trials * w / n_warps;
   const int64_t t_end = n_trials * (w + 1) / n_warps;
   const bool exact = L.af.exact != 0;
+  // the binary64 table holds exactly the entries' values: read increments from it
+  const bool use64 = OUT && table64 != nullptr && *inexact == 0u;
   // AggR + AggL on the grid, saturated (an unreachable limit stays unreachable)
   U128 ret_lim = add(L.af.ret, L.af.lim);
   if (!ge128(ret_lim, L.af.ret)) ret_lim = U128{~0ull, ~0ull};
@@ -180,9 +183,20 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       }
       if (fast) {
         double inc[IDS];
+        if (use64) {
+#pragma unroll
+          for (int i = 0; i < IDS; ++i) {
+            inc[i] = 0.0;
+            const uint32_t nz = inside && (x[i].lo | x[i].hi) != 0ull ? 1u : 0u;
+            asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                "@p ld.global.nc.f64 %0, [%2];\n\t}"
+                : "+d"(inc[i])
+                : "r"(nz), "l"(table64 + id[i]));
+          }
+        }
 #pragma unroll
         for (int i = 0; i < IDS; ++i) {
-          inc[i] = inside ? from_fixed_exact(x[i], L.q) : 0.0;
+          if (!use64) inc[i] = inside ? from_fixed_exact(x[i], L.q) : 0.0;
           const unsigned long long b = (unsigned long long)__double_as_longlong(inc[i]);
           if (i < valid) best = b > best ? b : best;
         }
@@ -254,7 +268,8 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
 template <bool PACKED, int EB, bool OUT>
 static cudaError_t launch_yelt_t(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, int64_t n_trials,
                                  const void *table, const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel,
-                                 const LayerOut &L, double *yelt, double *occ_max, int sms, cudaStream_t s) {
+                                 const LayerOut &L, double *yelt, double *occ_max, int sms, cudaStream_t s,
+                                 const double *table64, const unsigned int *inexact) {
   const size_t smem = (size_t)bm.words * 4u;
   cudaError_t err = cudaFuncSetAttribute(yelt_kernel<PACKED, EB, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -263,21 +278,22 @@ static cudaError_t launch_yelt_t(const int64_t *coff, const int4 *chunks, const 
   const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
   yelt_kernel<PACKED, EB, OUT><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table,
                                                          reinterpret_cast<const uint4 *>(bitmap), bm.words / 4,
-                                                         bm.mul, sent4, L, yelt, occ_max);
+                                                         bm.mul, sent4, L, yelt, occ_max, table64, inexact);
   return cudaGetLastError();
 }
 
 cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
                         int64_t n_trials, const void *table, int entry_bytes, const uint32_t *bitmap,
                         BitmapLayout bm, int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max,
-                        int device, cudaStream_t s) {
+                        int device, cudaStream_t s, const double *table64, const unsigned int *inexact) {
   if (n_trials <= 0) return cudaSuccess;
   int sms = 148;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
   const bool out = yelt != nullptr;
 #define ARA_YELT_LAUNCH(P, E, O)                                                                             \
-  launch_yelt_t<P, E, O>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt, occ_max, sms, s)
+  launch_yelt_t<P, E, O>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt, occ_max, sms, s, \
+                         table64, inexact)
   if (entry_bytes == 16) {
     if (packed) return out ? ARA_YELT_LAUNCH(true, 16, true) : ARA_YELT_LAUNCH(true, 16, false);
     return out ? ARA_YELT_LAUNCH(false, 16, true) : ARA_YELT_LAUNCH(false, 16, false);

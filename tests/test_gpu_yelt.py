@@ -197,3 +197,56 @@ def test_paper_scale_full_size_sampled():
     sy = np.sort(ylt)[::-1]
     for r, p in zip(w.return_periods, rep["aep"]):
         assert p == sy[int(math.floor(ylt.size / r)) - 1]
+
+
+def _inside_increments_check(yelt, table, yet):
+    """Every increment is 0, or exactly the occurrence's event-table value
+    (its running sum stayed inside the layer), or one of at most two per
+    trial where the running sum crossed AggR or AggR + AggL."""
+    v = table[yet.ids]
+    same = (yelt == 0.0) | (yelt.view(np.uint64) == v.view(np.uint64))
+    trial_of = np.repeat(np.arange(yet.n_trials), np.diff(yet.offsets))
+    other = np.bincount(trial_of[~same], minlength=yet.n_trials)
+    assert other.max() <= 2
+    return int(np.count_nonzero(same & (yelt != 0.0)))
+
+
+def test_inside_increments_are_the_event_table_values(engine):
+    """The binary64 reading of in-layer increments (the event table, used
+    when every table value is exactly on the grid) gives the bits the
+    fixed-point difference gives."""
+    w = S.paper_scale(n_trials=5_000, lam=200.0, catalog_size=200_000)
+    L = w.layers[0]
+    engine.load_yet_from(w.yet)
+    first = engine.load_pool(w.pool)
+    h = engine.define_layer([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, 1.5e8)
+    inc, occ_max = engine.layer_yelt(h)
+    inside = _inside_increments_check(inc, engine.event_table(h), w.yet)
+    assert inside > 100_000
+    o_inc, out_off, o_max, _, pre = oracle.layer_yelt(w.yet, w.pool, S.Layer(L.elts, L.occ_ret, L.occ_lim,
+                                                                               L.agg_ret, 1.5e8))
+    assert_yelt_parity(inc, occ_max, o_inc, out_off, o_max, pre, FP64_REL, what="paper-shaped")
+
+
+def test_tiny_losses_take_the_conversion_path(engine):
+    """Losses far below the table's grid (rounded into the fixed-point
+    table) make the binary64 table inexact: increments are then converted
+    from the fixed-point entries, still within the parity bound."""
+    catalog = 50_000
+    pool = _custom_pool(catalog, [5_000, 20_000], 11, ded=[0.0, 0.0], lim=[1e12, 1e12])
+    pool.losses[:2_500] *= 1e-25  # their last bits fall below the grid the large losses set
+    yet = _custom_yet(catalog, LENGTHS * 4, 5)
+    layer = S.Layer([0, 1], 0.0, math.inf, 1e3, 1e12)
+    engine.load_yet_from(yet)
+    first = engine.load_pool(pool)
+    h = engine.define_layer([first, first + 1], layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
+    inc, occ_max = engine.layer_yelt(h)
+    o_inc, out_off, o_max, _, pre = oracle.layer_yelt(yet, pool, layer)
+    assert_yelt_parity(inc, occ_max, o_inc, out_off, o_max, pre, FP64_REL, what="tiny losses")
+    # events whose only loss is tiny are rounded in the fixed-point table, and
+    # their increments follow the fixed-point sums, not the binary64 values
+    tab = engine.event_table(h)
+    tiny = (tab > 0.0) & (tab < 1e-15)
+    hit = tiny[yet.ids] & (inc != 0.0)
+    assert hit.sum() > 100
+    assert np.any(inc[hit].view(np.uint64) != tab[yet.ids][hit].view(np.uint64))
