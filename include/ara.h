@@ -174,12 +174,12 @@ ARA_API ara_status ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int64_t *el
  *                        may not appear twice.  n_elts >= 1.
  *   occ_ret, occ_lim     FT2: occurrence retention and limit, applied to
  *                        each event's loss combined across the ELTs
- *   agg_ret, agg_lim     FT3: aggregate retention and limit, applied to the
- *                        cumulative sum of occurrence-net losses of a trial
+ *   agg_ret, agg_lim     FT3: aggregate retention and limit, on a trial's
+ *                        running total of occurrence-net losses
  *   precision            ARA_FP64, or ARA_FP32_TABLE: losses and terms are
  *                        rounded to binary32 and the ELT combination and
- *                        occurrence terms run in binary32 (Section IV-B,
- *                        "single precision when possible"); the trial sum
+ *                        occurrence terms run in binary32 (Section IV-B uses
+ *                        binary32 arithmetic wherever it can); the trial sum
  *                        and aggregate terms keep full precision
  *   layer_out (out)      the layer handle
  * Retentions must be finite and >= 0, limits >= 0 (+inf allowed).  The

@@ -17,7 +17,7 @@
 // bit of the zero-skip bitmap, and (optionally) the FP64 value.  FP64 layers
 // store round(o / 2^q) as a 128-bit integer (exact for every value the grid
 // can hold).  Reduced-precision layers run the same steps in binary32 (the
-// paper's "single precision when possible", Section IV-B) and store 64-bit
+// paper's choice of binary32 wherever it can, Section IV-B) and store 64-bit
 // entries on a grid chosen so that no trial sum reaches 2^64: half the table
 // bytes; rounding to that grid moves a trial sum by less than its length x
 // 2^(q-1), far below the binary32 rounding of the values themselves.

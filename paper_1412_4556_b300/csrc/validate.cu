@@ -1,7 +1,7 @@
 // Device-side ingest of a freshly copied YET: every event id must lie in the
-// catalog (Section III: ids are drawn from the catalogue of events), and
-// time-stamps, when given, must be finite and ascending within each trial
-// (Section III: each trial is ordered by ascending time-stamp).  Violations
+// catalog (Section III: a trial's events come from the event catalogue), and
+// time-stamps, when given, must be finite and nondecreasing within each
+// trial (Section III: a trial lists its events in time order).  Violations
 // are counted; the host turns a nonzero count into a status code, so a bad
 // input never reaches a kernel that would index with it.
 #include "ara_internal.cuh"
