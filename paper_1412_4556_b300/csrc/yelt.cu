@@ -8,11 +8,12 @@
 //     inc_k = a_k - a_{k-1},   a_0 = 0             (YELT entry of occurrence k)
 // and the trial loss is a_n (the YLT entry).
 //
-// B300 design: one warp per trial walks the trial's 16-byte id chunks in
-// order, 32 chunks per step.  Each lane gathers its chunk's table entries
-// (zero-skip bitmap in shared memory, as in the YLT kernel), forms their
-// prefix sums, and the warp turns the lane totals into an exclusive scan with
-// shuffles: a segmented scan whose segments are the trials.  The running
+// B300 design: 16 lanes per trial walk the trial's 16-byte id chunks in
+// order, 16 chunks per step, two trials side by side in a warp.  Each lane
+// gathers its chunk's table entries (zero-skip bitmap in shared memory, as
+// in the YLT kernel), forms their prefix sums, and the 16 lanes turn their
+// totals into an exclusive scan with shuffles: a segmented scan whose
+// segments are the trials.  The running
 // sums are 128-bit fixed-point integers, so every P_k is exact; when the
 // aggregate terms lie on the table's grid the clamps and differences are
 // exact integers too and each increment is rounded to binary64 once.
@@ -59,17 +60,20 @@ __device__ __forceinline__ double clamp_fp64(U128 P, int q, double agg_ret, doub
   return fmin(fmax(__dsub_rn(from_fixed(P, q), agg_ret), 0.0), agg_lim);
 }
 
+// Shuffles within groups of W consecutive lanes.
+template <int W>
 __device__ __forceinline__ U128 shfl_up_u128(U128 v, int d) {
   U128 r;
-  r.lo = __shfl_up_sync(0xFFFFFFFFu, v.lo, d);
-  r.hi = __shfl_up_sync(0xFFFFFFFFu, v.hi, d);
+  r.lo = __shfl_up_sync(0xFFFFFFFFu, v.lo, d, W);
+  r.hi = __shfl_up_sync(0xFFFFFFFFu, v.hi, d, W);
   return r;
 }
 
+template <int W>
 __device__ __forceinline__ U128 shfl_u128(U128 v, int src) {
   U128 r;
-  r.lo = __shfl_sync(0xFFFFFFFFu, v.lo, src);
-  r.hi = __shfl_sync(0xFFFFFFFFu, v.hi, src);
+  r.lo = __shfl_sync(0xFFFFFFFFu, v.lo, src, W);
+  r.hi = __shfl_sync(0xFFFFFFFFu, v.hi, src, W);
   return r;
 }
 
@@ -93,6 +97,8 @@ __device__ __forceinline__ void chunk_ids_y(int4 c, uint32_t (&id)[PACKED ? 6 : 
 
 // OUT: the per-occurrence increments are written (else only the trial
 // maxima and losses, as for the return period report).
+constexpr int kLanes = 16;                    // lanes per trial
+constexpr int kTrialsPerWarp = 32 / kLanes;   // trials a warp walks side by side
 template <bool PACKED, int EB, bool OUT>
 __global__ void __launch_bounds__(kYltThreads, 1)
 yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
@@ -106,6 +112,8 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
   __syncthreads();
   const uint32_t *s_bm = reinterpret_cast<const uint32_t *>(s_bm4);
   const int lane = threadIdx.x & 31;
+  const int grp = lane / kLanes;  // which of the warp's trials this lane works on
+  const int gl = lane % kLanes;   // lane within that trial's group
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t t_begin = n_trials * w / n_warps;
@@ -117,17 +125,21 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
   U128 ret_lim = add(L.af.ret, L.af.lim);
   if (!ge128(ret_lim, L.af.ret)) ret_lim = U128{~0ull, ~0ull};
 
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    const int64_t p0 = coff[t];
-    const int nk = (int)(coff[t + 1] - p0);
-    const int64_t r0 = raw_off[t];
-    const int64_t nr = raw_off[t + 1] - r0;  // occurrences of trial t
+  for (int64_t t0 = t_begin; t0 < t_end; t0 += kTrialsPerWarp) {
+    const int64_t t = t0 + grp;
+    const bool valid_t = t < t_end;
+    const int64_t p0 = valid_t ? coff[t] : 0;
+    const int nk = valid_t ? (int)(coff[t + 1] - p0) : 0;
+    const int64_t r0 = valid_t ? raw_off[t] : 0;
+    const int64_t nr = valid_t ? raw_off[t + 1] - r0 : 0;  // occurrences of trial t
+    int nk_max = nk;
+    if constexpr (kTrialsPerWarp > 1) nk_max = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)nk);
     U128 carry{0ull, 0ull};                  // running sum before this step
     unsigned long long best = 0ull;          // largest increment seen by this lane, as bits
                                              // (increments are >= 0: bits order like values)
     U128 best_fx{0ull, 0ull};                // !OUT: largest entry of the steps inside the layer
-    for (int base = 0; base < nk; base += 32) {
-      const int j = base + lane;
+    for (int base = 0; base < nk_max; base += kLanes) {
+      const int j = base + gl;
       const int4 v = j < nk ? chunks[p0 + j] : sent4;
       uint32_t id[IDS];
       chunk_ids_y<PACKED>(v, id);
@@ -145,14 +157,14 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         }
         tot = add(tot, x[i]);
       }
-      // inclusive scan of the lane totals across the warp
+      // inclusive scan of the lane totals across the trial's lanes
       U128 incl = tot;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const U128 o = shfl_up_u128(incl, d);
-        if (lane >= d) incl = add(incl, o);
+      for (int d = 1; d < kLanes; d <<= 1) {
+        const U128 o = shfl_up_u128<kLanes>(incl, d);
+        if (gl >= d) incl = add(incl, o);
       }
-      const U128 step_total = shfl_u128(incl, 31);
+      const U128 step_total = shfl_u128<kLanes>(incl, kLanes - 1);
       // running sum before this lane's first id: carry + exclusive prefix
       U128 P = sub128(add(carry, incl), tot);
       const int64_t k0 = (int64_t)j * IDS;  // index of id[0] within the trial
@@ -203,7 +215,7 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         if (OUT) {
           if (valid == IDS) {
             // 16-byte stores where the pair is aligned (the parity of r0 is the
-            // same for every lane), so a warp writes half as many sectors
+            // same for every lane of a trial), so a warp writes half as many sectors
             if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0u) {
 #pragma unroll
               for (int i = 0; i + 1 < IDS; i += 2)
@@ -252,11 +264,11 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       best = b > best ? b : best;
     }
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
+    for (int m = kLanes / 2; m > 0; m >>= 1) {
       const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, best, m);
       best = o > best ? o : best;
     }
-    if (lane == 0) {
+    if (gl == 0 && valid_t) {
       if (occ_max) occ_max[t] = __longlong_as_double((long long)best);
       if (L.ylt) L.ylt[t] = trial_loss(carry, L.q, L.af, L.agg_ret, L.agg_lim);
     }
