@@ -8,10 +8,11 @@
 //     inc_k = a_k - a_{k-1},   a_0 = 0             (YELT entry of occurrence k)
 // and the trial loss is a_n (the YLT entry).
 //
-// B300 design: 16 lanes per trial walk the trial's 16-byte id chunks in
-// order, 16 chunks per step, two trials side by side in a warp.  Each lane
+// B300 design: 16 lanes per trial (8 for the report variant) walk the
+// trial's 16-byte id chunks in order, one chunk per lane per step, two (four)
+// trials side by side in a warp.  Each lane
 // gathers its chunk's table entries (zero-skip bitmap in shared memory, as
-// in the YLT kernel), forms their prefix sums, and the 16 lanes turn their
+// in the YLT kernel), forms their prefix sums, and the trial's lanes turn their
 // totals into an exclusive scan with shuffles: a segmented scan whose
 // segments are the trials.  The running
 // sums are 128-bit fixed-point integers, so every P_k is exact; when the
@@ -97,8 +98,6 @@ __device__ __forceinline__ void chunk_ids_y(int4 c, uint32_t (&id)[PACKED ? 6 : 
 
 // OUT: the per-occurrence increments are written (else only the trial
 // maxima and losses, as for the return period report).
-constexpr int kLanes = 16;                    // lanes per trial
-constexpr int kTrialsPerWarp = 32 / kLanes;   // trials a warp walks side by side
 template <bool PACKED, int EB, bool OUT>
 __global__ void __launch_bounds__(kYltThreads, 1)
 yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
@@ -107,6 +106,9 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
             double *__restrict__ yelt, double *__restrict__ occ_max, const double *__restrict__ table64,
             const unsigned int *__restrict__ inexact) {
   constexpr int IDS = PACKED ? 6 : 4;
+  // lanes per trial (measured: 16 with per-occurrence output, 8 without)
+  constexpr int kLanes = OUT ? 16 : 8;
+  constexpr int kTrialsPerWarp = 32 / kLanes;  // trials a warp walks side by side
   extern __shared__ uint4 s_bm4[];
   for (int i = threadIdx.x; i < bm_words4; i += blockDim.x) s_bm4[i] = bitmap4[i];
   __syncthreads();
