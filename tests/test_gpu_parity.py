@@ -304,7 +304,8 @@ def test_paper_scale_full_size_sampled(paper_full):
 @pytest.mark.parametrize("catalog", [(1 << 21) - 1, 1 << 21])
 def test_packing_boundary_catalogs(engine, catalog):
     """The largest catalog whose ids (and the sentinel) pack into 21 bits, and
-    the smallest that does not: both layouts give the oracle's YLT."""
+    the smallest that does not: both layouts give the oracle's YLT, and so
+    does the compact stream of the first."""
     pool = _custom_pool(catalog, [40_000, 25_000, 5], 8)
     hot = [0, catalog - 1, catalog - 2] + [int(x) for x in pool.ids[:20]]
     yet = _custom_yet(catalog, LENGTHS * 4, 17, hot)
@@ -313,7 +314,12 @@ def test_packing_boundary_catalogs(engine, catalog):
     lay = S.Layer([0, 1, 2], 1e3, 5e6, 1e4, 1e8)
     L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret, lay.agg_lim)
     o, pre = oracle.layer_ylt(yet, pool, lay, mode="memo")
-    assert_fp64_parity(engine.layer_ylt(L), o, pre)
+    y = engine.layer_ylt(L)
+    assert_fp64_parity(y, o, pre)
+    # the difference code's 21-bit bases and 8192-id buckets reach the top id
+    # (a no-op for the plain layout of the larger catalog)
+    engine.compact_yet()
+    np.testing.assert_array_equal(engine.layer_ylt(L).view(np.uint64), y.view(np.uint64))
 
 
 def test_layer_with_the_most_elts(engine):
