@@ -453,6 +453,23 @@ BATCHED = ("batched layers, FP64: the paper-scale YET (1,000,000 trials x Poisso
            "[1e7,1e9]; RP 100/250/500")
 
 
+def batched_roofline(M, N, C, layers, table_bytes_per_event, ylt_ms, passes):
+    """Roofline of the YLT passes of a many-layer step against the
+    algorithmic minimum of the step: the YET read once (4 B per occurrence)
+    plus each layer's table (table_bytes_per_event per catalog event), YLT
+    (8 B per trial) and trial offsets."""
+    alg = 4 * M + layers * (table_bytes_per_event * C + 8 * N) + 8 * (N + 1)
+    achieved = alg / (ylt_ms / 1e3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "ylt_fp64_kernel (%d grouped passes)" % passes, "kernel_ms": ylt_ms,
+            "algorithmic_bytes_per_step": alg, "peak_kind": peak_kind,
+            "frac_of_nominal_8000_gbs": achieved / 8000.0,
+            "note": "the algorithmic minimum reads the YET once for all layers; the passes re-read it once "
+                    "per pass and gather one 32-byte sector per occurrence any of a pass's layers needs, "
+                    "which bounds them (L1TEX, not HBM)"}
+
+
 def run_batched(args):
     """Config-2 step: define 64 layers (ELT folds), price them in pairs in one
     call (ara_layers_ylt), PML/TVaR for all (ara_pml_tvar_batch).  Also times
@@ -583,6 +600,7 @@ def run_batched(args):
                             "value": G * M / (ms_p / 1e3),
                             "step": "64 x ara_define_layer + 64 x ara_layer_ylt + ara_pml_tvar_batch"},
         "speedup_vs_plain": ms_p / ms_g,
+        "roofline": batched_roofline(M, N, w.yet.catalog_size, G, 4 if mixed else 8, ylt_b, len(passes)),
         "clocks": clocks.summary(),
     }
     if mixed:
