@@ -152,6 +152,28 @@ def test_neutral_terms_reduce_to_segmented_sum():
         np.testing.assert_array_equal(ylt, pre)
 
 
+def test_mean_trial_loss_with_neutral_layer_terms_is_poisson_mean_times_catalog_mean():
+    """Statistical sanity on the tiny workload: with neutral occurrence and
+    aggregate terms a trial's loss sums about Poisson(100) uniform draws of
+    the per-event combined ELT loss C, so the mean over 1,000 trials lies
+    within a few standard errors of 100 x mean(C) (C computed here with
+    NumPy from the ELTs, not by the oracle)."""
+    import ara_synth as S
+    w = S.tiny()
+    pool = w.pool
+    layer = Layer(w.layers[0].elts, 0.0, math.inf, 0.0, math.inf)
+    c = np.zeros(w.yet.catalog_size)
+    for j in layer.elts:
+        a, b = pool.offsets[j], pool.offsets[j + 1]
+        c[pool.ids[a:b]] += np.minimum(np.maximum(pool.losses[a:b] - pool.deductibles[j], 0.0), pool.limits[j])
+    ylt, _ = oracle.layer_ylt(w.yet, pool, layer)
+    expect = 100.0 * c.mean()
+    stderr = math.sqrt(100.0 * np.mean(c * c) / ylt.size)
+    assert abs(ylt.mean() - expect) < 5.0 * stderr, (ylt.mean(), expect, stderr)
+    # and the draws themselves average lambda per trial
+    assert abs(np.diff(w.yet.offsets).mean() - 100.0) < 5.0 * math.sqrt(100.0 / ylt.size)
+
+
 def test_literal_and_memo_modes_are_bit_identical():
     yet, pool, layer = _random_instance(2)
     a, pa = oracle.layer_ylt(yet, pool, layer, mode="literal", threads=3)
