@@ -292,7 +292,9 @@ ARA_API ara_status ara_pml_tvar_batch(ara_ctx *ctx, const double *ylt, int32_t n
  *   occ_max_out  double[n_trials], host or device; NULL if not wanted
  *   cuda_stream  stream for this call, or NULL for the context's stream
  * FP64 layers: the running sums are exact integers on the layer's grid; each
- * entry is rounded once.  Errors as ara_layer_ylt. */
+ * entry is rounded once.  With yelt_out, the context keeps (catalog_size + 1)
+ * doubles of device scratch for the layer's table in binary64, rebuilt by
+ * each call.  Errors as ara_layer_ylt. */
 ARA_API ara_status ara_layer_yelt(ara_ctx *ctx, int32_t layer, int64_t n_trials, double *yelt_out,
                                   double *occ_max_out, void *cuda_stream);
 
