@@ -106,27 +106,36 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // Pick the next digit of every return period in parallel: thread i holds
-  // the count of digit 255 - i (descending), a block-wide inclusive scan
-  // gives the counts of keys above each digit, and the one thread whose
-  // range contains rank k_rem records the digit.
+  // Pick the next digit of every return period: the merged counts come into
+  // shared memory at once, then two return periods at a time (256 threads
+  // each) thread i holds the count of digit 255 - i (descending), a scan over
+  // its 256 threads gives the counts of keys above each digit, and the one
+  // thread whose range contains rank k_rem records the digit.
   __shared__ long long s_warp[kSelectThreads / 32];
+  __shared__ long long s_krem[kMaxReturnPeriods];
   const int lane = tid & 31, wid = tid >> 5;
-  for (int r = 0; r < n_rp; ++r) {
-    const long long k_rem = st->k_rem[r];
-    const long long h = tid < 256 ? (long long)__ldcg(&st->hist[r][255 - tid]) : 0;
+  unsigned int *cnt = &sh[0][0];  // the block's histogram is merged: reuse its space
+  for (int i = tid; i < n_rp * 256; i += blockDim.x) cnt[i] = __ldcg(&st->hist[0][0] + i);
+  if (tid < n_rp) s_krem[tid] = st->k_rem[tid];
+  __syncthreads();
+  const int half = tid >> 8, b = tid & 255;
+  for (int r0 = 0; r0 < n_rp; r0 += 2) {
+    const int r = r0 + half;
+    const bool act = r < n_rp;
+    const long long k_rem = act ? s_krem[r] : 0;
+    const long long h = act ? (long long)cnt[r * 256 + 255 - b] : 0;
     long long incl = h;
     for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += y;
+      const long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
     }
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
-    for (int w = 0; w < wid; ++w) incl += s_warp[w];
+    for (int w = half * 8; w < wid; ++w) incl += s_warp[w];
     const long long excl = incl - h;
-    if (tid < 256 && excl < k_rem && k_rem <= incl) {
+    if (act && excl < k_rem && k_rem <= incl) {
       st->k_rem[r] = k_rem - excl;
-      st->prefix[r] = s_prefix[r] | ((unsigned long long)(255 - tid) << shift);
+      st->prefix[r] = s_prefix[r] | ((unsigned long long)(255 - b) << shift);
     }
     __syncthreads();
   }
