@@ -39,6 +39,10 @@ __device__ __forceinline__ float elt_terms32(double loss, double deductible, dou
                __double2float_rn(limit));
 }
 
+// ELT entries staged in shared memory per round (a bucket of a typical layer
+// fits in one round).
+constexpr int kStage = 1024;
+
 // FP32 = true: combine and apply occurrence terms in binary32 (the table then
 // holds binary32 values, exactly representable in the fixed-point grid).
 template <bool FP32>
@@ -48,10 +52,13 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
             uint32_t bm_mul, double *__restrict__ f64_out, unsigned int *__restrict__ inexact) {
   using Real = typename std::conditional<FP32, float, double>::type;
   __shared__ Real x[kFoldEventsPerCta];
-  __shared__ int32_t seg[kMaxLayerElts + 1];    // prefix sums of slice lengths
-  __shared__ int32_t first[kMaxLayerElts];      // slice start inside ELT j
-  __shared__ uint16_t st_off[kFoldStage];
-  __shared__ Real st_val[kFoldStage];
+  __shared__ uint16_t st_off[kStage];
+  __shared__ Real st_val[kStage];
+  // sized by the layer (n_elts + 1 and n_elts entries), so that a CTA of a
+  // typical layer needs little shared memory and the whole grid is resident
+  extern __shared__ int32_t s_dyn[];
+  int32_t *seg = s_dyn;                // prefix sums of slice lengths
+  int32_t *first = s_dyn + n_elts + 1;  // slice start inside ELT j
 
   const int tid = threadIdx.x;
   const int b = blockIdx.x;
@@ -76,8 +83,8 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
   __syncthreads();
   const int32_t total = seg[n_elts];
 
-  for (int32_t base = 0; base < total; base += kFoldStage) {
-    const int32_t end = min(total, base + kFoldStage);
+  for (int32_t base = 0; base < total; base += kStage) {
+    const int32_t end = min(total, base + kStage);
     for (int32_t f = base + tid; f < end; f += kFoldThreads) {
       int lo = 0, hi = n_elts;  // find j with seg[j] <= f < seg[j+1]
       while (hi - lo > 1) {
@@ -146,12 +153,13 @@ cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, doub
                         BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s, unsigned int *inexact) {
   if (catalog <= 0) return cudaSuccess;
   const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
+  const size_t dyn = (2 * (size_t)n_elts + 1) * sizeof(int32_t);  // at most 8 KB (kMaxLayerElts)
   if (fp32)
-    fold_kernel<true><<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
-                                                       table, bitmap, bm.mul, f64_out, inexact);
+    fold_kernel<true><<<blocks, kFoldThreads, dyn, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
+                                                         table, bitmap, bm.mul, f64_out, inexact);
   else
-    fold_kernel<false><<<blocks, kFoldThreads, 0, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
-                                                        table, bitmap, bm.mul, f64_out, inexact);
+    fold_kernel<false><<<blocks, kFoldThreads, dyn, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
+                                                          table, bitmap, bm.mul, f64_out, inexact);
   return cudaGetLastError();
 }
 
