@@ -523,6 +523,9 @@ ara_status ara_create(ara_ctx **out, int device) {
   c->device = device;
   e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+  for (cudaEvent_t &ev : c->load_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_sel_ws, select_workspace_bytes(kMaxReturnPeriods));
@@ -544,6 +547,7 @@ void ara_destroy(ara_ctx *c) {
   while (!c->plans.empty()) ara_plan_destroy(c->plans.back());
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (auto &L : c->layers) free_layer(L);
   for (auto &B : c->pool) free_buffers(B);
   for (void *p : c->elt_blocks) cudaFree(p);
@@ -554,6 +558,7 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_dchunks);
   cudaFree(c->d_cflag);
   cudaFree(c->d_raw);
+  cudaFreeHost(c->h_off_stage);
   cudaFree(c->d_ts);
   cudaFree(c->d_ylt_stage);
   cudaFree(c->d_yelt_stage);
@@ -576,6 +581,9 @@ void ara_destroy(ara_ctx *c) {
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);
     }
+  for (cudaEvent_t ev : c->load_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   cudaGetLastError();
   delete c;
@@ -617,22 +625,48 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
     return fail(c, ARA_E_INVALID_ARG, "event_ids is NULL but offsets hold %lld events", (long long)M_claimed);
   // The ids go to a staging buffer the loaded YET does not use, so a failed
   // check below still leaves the previous YET loaded.
+  // Host ids are copied in up to kLoadPieces pieces on the copy stream; the
+  // trials a piece completes are chunked while the later pieces are copied.
+  // The first piece starts now, the others once the offsets are checked.
   const bool dev_ids = M_claimed > 0 && is_device_ptr(ids);
+  int np = 0;      // pieces of the host id copy (0: none)
+  int issued = 0;  // pieces whose copy has been issued
+  int64_t step = 0;
+  auto piece_end = [&](int i) { return i + 1 == np ? M_claimed : step * (i + 1); };
+  auto issue_piece = [&](int i) {
+    ++issued;
+    return cudaMemcpyAsync(c->d_raw + step * i, ids + step * i, (size_t)(piece_end(i) - step * i) * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, c->copy_stream);
+  };
+  // Errors below wait for the id copies before returning (the caller may free ids).
+  auto wait_copies = [&]() {
+    if (issued > 0) cudaStreamSynchronize(c->copy_stream);
+  };
   if (M_claimed > 0 && !dev_ids) {
     ARA_CUDA(c, ensure(&c->d_raw, &c->cap_raw, (size_t)M_claimed), "allocate YET buffers");
-    ARA_CUDA(c, cudaMemcpyAsync(c->d_raw, ids, (size_t)M_claimed * sizeof(int32_t), cudaMemcpyHostToDevice, s),
-             "copy event_ids");
+    ARA_CUDA(c, cudaEventRecord(c->load_ev[kLoadPieces], s), "cudaEventRecord");
+    ARA_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->load_ev[kLoadPieces], 0), "cudaStreamWaitEvent");
+    np = (int)std::min<int64_t>(kLoadPieces, std::max<int64_t>(1, M_claimed >> kLoadPieceShift));
+    step = M_claimed / np;
+    const cudaError_t e = issue_piece(0);
+    if (e != cudaSuccess) {
+      wait_copies();
+      return cuda_fail(c, e, "copy event_ids");
+    }
   }
   std::vector<int64_t> h((size_t)n_trials + 1);
   if (dev_off) {
-    ARA_CUDA(c, cudaMemcpyAsync(h.data(), offsets, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
-             "copy trial_offsets");
-    ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    cudaError_t e = cudaMemcpyAsync(h.data(), offsets, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      wait_copies();
+      return cuda_fail(c, e, "copy trial_offsets");
+    }
   } else {
     std::memcpy(h.data(), offsets, h.size() * sizeof(int64_t));
   }
-  // Errors below wait for the id copy before returning (the caller may free ids).
   auto fail_sync = [&](ara_status st, const char *msg) {
+    wait_copies();
     cudaStreamSynchronize(s);
     cudaGetLastError();
     return fail(c, st, "%s", msg);
@@ -677,24 +711,60 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
   if (e == cudaSuccess) e = ensure(&c->d_chunks, &c->cap_chunks, (size_t)Mc + kChunkTail);
   if (e == cudaSuccess && ts) e = ensure(&c->d_ts, &c->cap_ts, (size_t)std::max<int64_t>(M, 1));
   if (e != cudaSuccess) {
+    wait_copies();
     cudaStreamSynchronize(s);
     return cuda_fail(c, e, "allocate YET buffers");
   }
-  e = cudaMemcpyAsync(c->d_offsets, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->d_coff, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  if (np > 0) {
+    // The offsets go between the first id piece and the second, from pinned
+    // memory, so that neither they nor the chunking wait for the whole id copy.
+    const size_t n1 = (size_t)n_trials + 1;
+    e = ensure_pinned(&c->h_off_stage, &c->cap_off_stage, 2 * n1);
+    if (e == cudaSuccess) {
+      std::memcpy(c->h_off_stage, h.data(), n1 * sizeof(int64_t));
+      std::memcpy(c->h_off_stage + n1, hp.data(), n1 * sizeof(int64_t));
+      e = cudaMemcpyAsync(c->d_offsets, c->h_off_stage, n1 * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          c->copy_stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_coff, c->h_off_stage + n1, n1 * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          c->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->load_ev[0], c->copy_stream);
+    for (int i = 1; i < np && e == cudaSuccess; ++i) {
+      e = issue_piece(i);
+      if (e == cudaSuccess) e = cudaEventRecord(c->load_ev[i], c->copy_stream);
+    }
+  } else {
+    e = cudaMemcpyAsync(c->d_offsets, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_coff, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  }
   const int32_t *src = (M > 0 && !dev_ids) ? c->d_raw : ids;
   if (e == cudaSuccess && ts && M > 0)
     e = cudaMemcpyAsync(c->d_ts, ts, (size_t)M * sizeof(float), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, 2 * sizeof(unsigned long long), s);
-  if (e == cudaSuccess)
-    e = launch_pad_ids(src, c->d_offsets, c->d_coff, n_trials, c->d_chunks, catalog, packed,
-                       c->d_counter, s);
+  // Piece i completes the trials whose ids end at or before piece_end(i).
+  int64_t t_done = 0;
+  for (int i = 0; i < std::max(np, 1) && e == cudaSuccess; ++i) {
+    const bool last = i + 1 >= np;
+    int64_t t_next = n_trials;
+    if (np > 0) {
+      e = cudaStreamWaitEvent(s, c->load_ev[i], 0);
+      if (!last) t_next = std::upper_bound(h.begin() + 1, h.end(), piece_end(i)) - (h.begin() + 1);
+    }
+    if (e == cudaSuccess && (t_next > t_done || last))
+      e = launch_pad_ids_range(src, c->d_offsets, c->d_coff, t_done, t_next, last, c->d_chunks, catalog,
+                               packed, c->d_counter, s);
+    t_done = t_next;
+  }
   if (e == cudaSuccess && ts) e = launch_check_ts(c->d_offsets, n_trials, c->d_ts, c->d_counter + 1, s);
   unsigned long long bad[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_counter, sizeof(bad), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "load YET");
+  if (e != cudaSuccess) {
+    wait_copies();
+    return cuda_fail(c, e, "load YET");
+  }
   if (bad[0]) return fail(c, ARA_E_EVENT_RANGE, "%llu event ids lie outside [0, %d)", bad[0], catalog);
   if (bad[1])
     return fail(c, ARA_E_INVALID_ARG,

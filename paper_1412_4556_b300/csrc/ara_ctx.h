@@ -9,6 +9,7 @@
 
 #include "ara.h"
 #include "ara_internal.cuh"
+#include "yet_load.cuh"
 
 namespace ara {
 
@@ -77,6 +78,10 @@ struct ara_ctx {
   int device = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
+  // host-to-device YET id copies run here, in pieces, each followed by an
+  // event; load_ev[kLoadPieces] orders the copies after the work on stream
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t load_ev[ara::kLoadPieces + 1] = {};
   std::string err;
   // YET
   int64_t yet_version = 0;
@@ -107,6 +112,8 @@ struct ara_ctx {
   size_t cap_cflag = 0;
   int32_t *d_raw = nullptr;         // staging for ids copied from the host
   size_t cap_raw = 0;
+  int64_t *h_off_stage = nullptr;   // pinned: raw then chunk offsets, copied between id pieces
+  size_t cap_off_stage = 0;
   float *d_ts = nullptr;
   size_t cap_ts = 0;
   bool has_ts = false;
@@ -176,6 +183,19 @@ cudaError_t ensure(T **buf, size_t *cap, size_t count) {
   *buf = nullptr;
   *cap = 0;
   cudaError_t e = cudaMalloc((void **)buf, (count > 0 ? count : 1) * sizeof(T));
+  if (e == cudaSuccess) *cap = count > 0 ? count : 1;
+  return e;
+}
+
+// The same for pinned host memory (page-locked, so copies from it are
+// asynchronous).
+template <typename T>
+cudaError_t ensure_pinned(T **buf, size_t *cap, size_t count) {
+  if (*cap >= count && *buf) return cudaSuccess;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMallocHost((void **)buf, (count > 0 ? count : 1) * sizeof(T));
   if (e == cudaSuccess) *cap = count > 0 ? count : 1;
   return e;
 }

@@ -87,17 +87,6 @@ struct Slot {
   size_t cap_h_desc = 0;
 };
 
-template <typename T>
-cudaError_t ensure_pinned(T **buf, size_t *cap, size_t count) {
-  if (*cap >= count && *buf) return cudaSuccess;
-  if (*buf) cudaFreeHost(*buf);
-  *buf = nullptr;
-  *cap = 0;
-  cudaError_t e = cudaMallocHost((void **)buf, std::max<size_t>(count, 1) * sizeof(T));
-  if (e == cudaSuccess) *cap = std::max<size_t>(count, 1);
-  return e;
-}
-
 void free_slot(Slot &sl) {
   if (sl.s) {
     cudaStreamSynchronize(sl.s);

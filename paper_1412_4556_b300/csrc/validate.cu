@@ -5,6 +5,7 @@
 // are counted; the host turns a nonzero count into a status code, so a bad
 // input never reaches a kernel that would index with it.
 #include "ara_internal.cuh"
+#include "yet_load.cuh"
 
 namespace ara {
 
@@ -36,7 +37,8 @@ __global__ void check_ts_kernel(const int64_t *__restrict__ offsets, int64_t n_t
 // sentinel id (= catalog size, whose table entry is zero), so every chunk
 // belongs to exactly one trial.  Ids outside the catalog are counted and
 // replaced by the sentinel, so no later kernel indexes with them.  One warp
-// per trial, one chunk per lane.
+// per trial, one chunk per lane; one launch covers the trials [t0, t1), and
+// the launch of the last range also writes the tail.
 __device__ __forceinline__ int32_t ingest_id(const int32_t *src, int64_t i, int64_t n,
                                              int32_t catalog, unsigned long long &bad) {
   if (i >= n) return catalog;
@@ -50,15 +52,15 @@ __device__ __forceinline__ int32_t ingest_id(const int32_t *src, int64_t i, int6
 
 template <bool PACKED>
 __global__ void pad_ids_kernel(const int32_t *__restrict__ src, const int64_t *__restrict__ off,
-                               const int64_t *__restrict__ coff, int64_t n_trials,
-                               int4 *__restrict__ dst, int32_t catalog,
+                               const int64_t *__restrict__ coff, int64_t t0, int64_t t1,
+                               bool write_tail, int4 *__restrict__ dst, int32_t catalog,
                                unsigned long long *bad_count) {
   constexpr int IPC = PACKED ? 6 : 4;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   unsigned long long bad = 0;
-  for (int64_t t = w0; t < n_trials; t += warps) {
+  for (int64_t t = t0 + w0; t < t1; t += warps) {
     const int64_t s = off[t], n = off[t + 1] - s;
     const int64_t c0 = coff[t], nc = coff[t + 1] - c0;
     for (int64_t j = lane; j < nc; j += 32) {
@@ -68,25 +70,31 @@ __global__ void pad_ids_kernel(const int32_t *__restrict__ src, const int64_t *_
       dst[c0 + j] = PACKED ? pack6(v) : make_int4(v[0], v[1], v[2], v[3]);
     }
   }
-  if (w0 == 0 && lane < kChunkTail) {
+  if (write_tail && w0 == 0 && lane < kChunkTail) {
     int32_t v[6] = {catalog, catalog, catalog, catalog, catalog, catalog};
-    dst[coff[n_trials] + lane] = PACKED ? pack6(v) : make_int4(catalog, catalog, catalog, catalog);
+    dst[coff[t1] + lane] = PACKED ? pack6(v) : make_int4(catalog, catalog, catalog, catalog);
   }
   for (int m = 16; m > 0; m >>= 1) bad += __shfl_xor_sync(0xFFFFFFFFu, bad, m);
   if (lane == 0 && bad) atomicAdd(bad_count, bad);
 }
 
-cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *coff,
-                           int64_t n_trials, int4 *dst, int32_t catalog, bool packed,
-                           unsigned long long *bad_count, cudaStream_t s) {
-  int64_t blocks = (n_trials + 7) / 8;
+cudaError_t launch_pad_ids_range(const int32_t *src, const int64_t *off, const int64_t *coff,
+                                 int64_t t0, int64_t t1, bool last, int4 *dst, int32_t catalog,
+                                 bool packed, unsigned long long *bad_count, cudaStream_t s) {
+  int64_t blocks = (t1 - t0 + 7) / 8;
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
   if (packed)
-    pad_ids_kernel<true><<<(int)blocks, 256, 0, s>>>(src, off, coff, n_trials, dst, catalog, bad_count);
+    pad_ids_kernel<true><<<(int)blocks, 256, 0, s>>>(src, off, coff, t0, t1, last, dst, catalog, bad_count);
   else
-    pad_ids_kernel<false><<<(int)blocks, 256, 0, s>>>(src, off, coff, n_trials, dst, catalog, bad_count);
+    pad_ids_kernel<false><<<(int)blocks, 256, 0, s>>>(src, off, coff, t0, t1, last, dst, catalog, bad_count);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pad_ids(const int32_t *src, const int64_t *off, const int64_t *coff,
+                           int64_t n_trials, int4 *dst, int32_t catalog, bool packed,
+                           unsigned long long *bad_count, cudaStream_t s) {
+  return launch_pad_ids_range(src, off, coff, 0, n_trials, true, dst, catalog, packed, bad_count, s);
 }
 
 cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const float *ts,

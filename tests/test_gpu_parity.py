@@ -367,3 +367,65 @@ def test_rejected_yet_keeps_the_previous_one(engine):
     assert ei.value.name == "ARA_E_STATE"
     engine.load_yet_from(w.yet)
     np.testing.assert_array_equal(engine.layer_ylt(L), ref)
+
+
+def _split_at(lengths, pos, n_empty):
+    """Split the trial that holds id position pos so that a trial ends exactly
+    there, and put n_empty empty trials at the cut (the total is unchanged)."""
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    t = int(np.searchsorted(off, pos, side="right")) - 1
+    if off[t] == pos:
+        return lengths[:t] + [0] * n_empty + lengths[t:]
+    a = pos - int(off[t])
+    return lengths[:t] + [a] + [0] * n_empty + [lengths[t] - a] + lengths[t + 1:]
+
+
+@pytest.mark.parametrize("catalog", [2_000_000, 5_000_000])
+def test_host_ids_load_in_pieces(engine, catalog):
+    """Host ids of several times 2^24 entries are copied in pieces, and the
+    trials each piece completes are chunked while the later pieces copy.  A
+    trial spanning several pieces, trials that end exactly at a piece
+    boundary with empty trials there, and empty trials at both ends give the
+    bits of the same ids loaded from device memory (one chunking launch) and
+    the oracle's YLT on sampled trials; a bad id in the first or the last
+    piece is found."""
+    import torch
+    from paper_1412_4556_b300 import AraError
+    rng = np.random.default_rng(31)
+    # the long trial covers the first pieces whole (they complete no trial)
+    lengths = [0, 0, (1 << 26) + 4_999] + [int(x) for x in rng.poisson(1000, 80_000)] + [0]
+    M = sum(lengths)
+    pieces = min(8, M >> 24)
+    assert pieces == 8
+    step = M // pieces
+    lengths = _split_at(lengths, 5 * step, 3)
+    lengths = _split_at(lengths, 6 * step, 1)
+    assert sum(lengths) == M
+    yet = _custom_yet(catalog, lengths, 41, hot=[0, catalog - 1])
+    pool = _custom_pool(catalog, [50_000, 30_000, 20_000], 5)
+    lay = S.Layer([0, 1, 2], 1e3, 5e6, 1e4, 1e9)
+    dev = torch.device("cuda", 0)
+    engine.load_yet(catalog, torch.from_numpy(yet.offsets).to(dev), torch.from_numpy(yet.ids).to(dev))
+    first = engine.load_pool(pool)
+    L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret, lay.agg_lim)
+    ref = engine.layer_ylt(L)
+    h_ids = torch.from_numpy(yet.ids).pin_memory()
+    engine.load_yet(catalog, yet.offsets, h_ids.numpy())
+    y = engine.layer_ylt(L)
+    np.testing.assert_array_equal(y.view(np.uint64), ref.view(np.uint64))
+    off = yet.offsets
+    around = np.concatenate([np.searchsorted(off, b * step, side="right") + np.arange(-3, 3)
+                             for b in range(1, pieces)])
+    sel = np.unique(np.concatenate([around, [0, 1, 2, off.size - 2, int(np.argmax(np.diff(off)))],
+                                    rng.choice(y.size, 300, replace=False)]))
+    sel = sel[(sel >= 0) & (sel < y.size)]
+    o, pre = oracle.layer_ylt(yet, pool, lay, trials=sel, mode="memo")
+    assert_fp64_parity(y[sel], o, pre)
+    for pos in (0, M - 1):
+        ids = yet.ids.copy()
+        ids[pos] = catalog
+        with pytest.raises(AraError) as ei:
+            engine.load_yet(catalog, yet.offsets, ids)
+        assert ei.value.name == "ARA_E_EVENT_RANGE"
+    engine.load_yet(catalog, yet.offsets, h_ids.numpy())
+    np.testing.assert_array_equal(engine.layer_ylt(L).view(np.uint64), ref.view(np.uint64))
