@@ -24,24 +24,59 @@ namespace ara {
 
 namespace {
 
-__device__ __forceinline__ ulonglong2 gather_or_zero(const ulonglong2 *p, uint32_t hit) {
+// L2 policies: the id chunks (read once) and the increments (written once)
+// pass through L2 marked evict-first, the table gathers evict-last, so that
+// the stream does not push the layer's table out of L2 (measured on the
+// paper-scale YET: 4.68 -> 3.94 ms with per-occurrence output).
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ ulonglong2 gather_or_zero(const ulonglong2 *p, uint32_t hit, unsigned long long pol) {
   unsigned long long a = 0ull, b = 0ull;
   asm("{\n\t.reg .pred p;\n\t"
       "setp.ne.u32 p, %2, 0;\n\t"
-      "@p ld.global.nc.v2.u64 {%0, %1}, [%3];\n\t}"
+      "@p ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
       : "+l"(a), "+l"(b)
-      : "r"(hit), "l"(p));
+      : "r"(hit), "l"(p), "l"(pol));
   return make_ulonglong2(a, b);
 }
 
-__device__ __forceinline__ unsigned long long gather_or_zero8(const unsigned long long *p, uint32_t hit) {
+__device__ __forceinline__ unsigned long long gather_or_zero8(const unsigned long long *p, uint32_t hit,
+                                                              unsigned long long pol) {
   unsigned long long a = 0ull;
   asm("{\n\t.reg .pred p;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "@p ld.global.nc.u64 %0, [%2];\n\t}"
+      "@p ld.global.nc.L2::cache_hint.u64 %0, [%2], %3;\n\t}"
       : "+l"(a)
-      : "r"(hit), "l"(p));
+      : "r"(hit), "l"(p), "l"(pol));
   return a;
+}
+
+__device__ __forceinline__ int4 ld_chunk(const int4 *p, unsigned long long pol) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ void st_out2(double *p, double a, double b, unsigned long long pol) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(a), "d"(b),
+               "l"(pol)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_out(double *p, double a, unsigned long long pol) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(a), "l"(pol) : "memory");
 }
 
 __device__ __forceinline__ U128 add(U128 a, U128 b) {
@@ -121,6 +156,8 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
   const int64_t t_begin = n_trials * w / n_warps;
   const int64_t t_end = n_trials * (w + 1) / n_warps;
   const bool exact = L.af.exact != 0;
+  const unsigned long long pol_stream = l2_evict_first();
+  const unsigned long long pol_tab = l2_evict_last();
   // the binary64 table holds exactly the entries' values: read increments from it
   const bool use64 = OUT && table64 != nullptr && *inexact == 0u;
   // AggR + AggL on the grid, saturated (an unreachable limit stays unreachable)
@@ -142,15 +179,15 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
     U128 best_fx{0ull, 0ull};                // !OUT: largest entry of the steps inside the layer
     // The report variant loads the next step's chunk a step ahead (measured:
     // faster without output, slower with it).
-    int4 vnext = !OUT && gl < nk ? chunks[p0 + gl] : sent4;
+    int4 vnext = !OUT && gl < nk ? ld_chunk(chunks + p0 + gl, pol_stream) : sent4;
     for (int base = 0; base < nk_max; base += kLanes) {
       const int j = base + gl;
       int4 v;
       if constexpr (OUT) {
-        v = j < nk ? chunks[p0 + j] : sent4;
+        v = j < nk ? ld_chunk(chunks + p0 + j, pol_stream) : sent4;
       } else {
         v = vnext;
-        vnext = j + kLanes < nk ? chunks[p0 + j + kLanes] : sent4;
+        vnext = j + kLanes < nk ? ld_chunk(chunks + p0 + j + kLanes, pol_stream) : sent4;
       }
       uint32_t id[IDS];
       chunk_ids_y<PACKED>(v, id);
@@ -161,10 +198,10 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         const uint32_t word = s_bm[bitmap_word(id[i], bm_mul)];
         const uint32_t hit = __funnelshift_r(word, word, id[i]) & 1u;
         if constexpr (EB == 16) {
-          const ulonglong2 e = gather_or_zero(static_cast<const ulonglong2 *>(table) + id[i], hit);
+          const ulonglong2 e = gather_or_zero(static_cast<const ulonglong2 *>(table) + id[i], hit, pol_tab);
           x[i] = U128{e.x, e.y};
         } else {
-          x[i] = U128{gather_or_zero8(static_cast<const unsigned long long *>(table) + id[i], hit), 0ull};
+          x[i] = U128{gather_or_zero8(static_cast<const unsigned long long *>(table) + id[i], hit, pol_tab), 0ull};
         }
         tot = add(tot, x[i]);
       }
@@ -229,19 +266,17 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
             // same for every lane of a trial), so a warp writes half as many sectors
             if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0u) {
 #pragma unroll
-              for (int i = 0; i + 1 < IDS; i += 2)
-                *reinterpret_cast<double2 *>(out + i) = make_double2(inc[i], inc[i + 1]);
+              for (int i = 0; i + 1 < IDS; i += 2) st_out2(out + i, inc[i], inc[i + 1], pol_stream);
             } else {
-              out[0] = inc[0];
+              st_out(out, inc[0], pol_stream);
 #pragma unroll
-              for (int i = 1; i + 1 < IDS; i += 2)
-                *reinterpret_cast<double2 *>(out + i) = make_double2(inc[i], inc[i + 1]);
-              out[IDS - 1] = inc[IDS - 1];
+              for (int i = 1; i + 1 < IDS; i += 2) st_out2(out + i, inc[i], inc[i + 1], pol_stream);
+              st_out(out + IDS - 1, inc[IDS - 1], pol_stream);
             }
           } else {
 #pragma unroll
             for (int i = 0; i < IDS; ++i)
-              if (i < valid) out[i] = inc[i];
+              if (i < valid) st_out(out + i, inc[i], pol_stream);
           }
         }
         carry = add(carry, step_total);
@@ -265,7 +300,7 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         if (i < valid) {
           const unsigned long long b = (unsigned long long)__double_as_longlong(inc);
           best = b > best ? b : best;
-          if (OUT) out[i] = inc;
+          if (OUT) st_out(out + i, inc, pol_stream);
         }
       }
       carry = add(carry, step_total);
