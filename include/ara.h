@@ -120,7 +120,11 @@ ARA_API ara_status ara_set_stream(ara_ctx *ctx, void *cuda_stream);
  * loaded; once the copy has started (it replaces the previous YET in place,
  * since it can be several GB), a failure leaves the context with no YET.
  * Layers already defined are re-folded against the new YET on their next
- * use. */
+ * use.  The call returns when the YET is on the device (the caller may then
+ * free its arrays).  Host ids go up in pieces of at least 2^24 ids on a copy
+ * stream of the context's, each piece's completed trials being laid out
+ * while later pieces copy; from pinned host memory the copies run
+ * asynchronously to the host's checks of the offsets. */
 ARA_API ara_status ara_load_yet(ara_ctx *ctx, int32_t catalog_size, int64_t n_trials,
                         const int64_t *trial_offsets, const int32_t *event_ids,
                         const float *timestamps);
