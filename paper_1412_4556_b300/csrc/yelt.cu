@@ -232,11 +232,13 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       }
       if (!OUT && fast) {
         // Inside the layer an increment is its entry, and the conversion is
-        // monotone: keep the largest entry, convert it once per trial.
+        // monotone: keep the largest entry, convert it once per trial.  Slots
+        // past the trial's end hold the sentinel (entry 0), which cannot
+        // raise a maximum, so only the stores need the slot count.
         if (inside) {
 #pragma unroll
           for (int i = 0; i < IDS; ++i)
-            if (i < valid && ge128(x[i], best_fx)) best_fx = x[i];
+            if (ge128(x[i], best_fx)) best_fx = x[i];
         }
         carry = add(carry, step_total);
         continue;
@@ -258,7 +260,7 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         for (int i = 0; i < IDS; ++i) {
           if (!use64) inc[i] = inside ? from_fixed_exact(x[i], L.q) : 0.0;
           const unsigned long long b = (unsigned long long)__double_as_longlong(inc[i]);
-          if (i < valid) best = b > best ? b : best;
+          best = b > best ? b : best;
         }
         if (OUT) {
           if (valid == IDS) {
