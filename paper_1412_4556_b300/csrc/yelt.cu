@@ -75,6 +75,13 @@ __device__ __forceinline__ void st_out2(double *p, double a, double b, unsigned 
                : "memory");
 }
 
+// 32 bytes at a 32-byte aligned address (256-bit store, sm_100 and later).
+__device__ __forceinline__ void st_out4(double *p, double a, double b, double c, double d, unsigned long long pol) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f64 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "d"(a),
+               "d"(b), "d"(c), "d"(d), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ void st_out(double *p, double a, unsigned long long pol) {
   asm volatile("st.global.L1::no_allocate.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(a), "l"(pol) : "memory");
 }
@@ -264,9 +271,20 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         }
         if (OUT) {
           if (valid == IDS) {
-            // 16-byte stores where the pair is aligned (the parity of r0 is the
-            // same for every lane of a trial), so a warp writes half as many sectors
-            if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0u) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(out);
+            if (IDS == 6 && (a & 15u) == 0u) {
+              // 48 bytes a lane: a 32-byte store on the lane's 32-byte aligned
+              // part and a 16-byte store on the rest (which part comes first
+              // alternates from lane to lane; selects keep the warp converged)
+              const bool lo32 = (a & 31u) == 0u;
+              double *p4 = lo32 ? out : out + 2;
+              double *p2 = lo32 ? out + 4 : out;
+              st_out4(p4, lo32 ? inc[0] : inc[2], lo32 ? inc[1] : inc[3], lo32 ? inc[2] : inc[4],
+                      lo32 ? inc[3] : inc[5], pol_stream);
+              st_out2(p2, lo32 ? inc[4] : inc[0], lo32 ? inc[5] : inc[1], pol_stream);
+            } else if ((a & 15u) == 0u) {
+              // 16-byte stores where the pair is aligned (the parity of r0 is the
+              // same for every lane of a trial), so a warp writes half as many sectors
 #pragma unroll
               for (int i = 0; i + 1 < IDS; i += 2) st_out2(out + i, inc[i], inc[i + 1], pol_stream);
             } else {
