@@ -569,6 +569,7 @@ void ara_destroy(ara_ctx *c) {
   cudaFree(c->d_tail_scratch);
   cudaFree(c->d_evt64);
   cudaFree(c->d_evt64_inexact);
+  cudaFree(c->d_yelt_comb);
   cudaFree(c->d_tail);
   cudaFree(c->d_sel_ws_batch);
   cudaFree(c->d_sel_out_batch);
@@ -1206,11 +1207,17 @@ ara_status ara_layer_yelt(ara_ctx *c, int32_t layer, int64_t n_trials, double *y
     ARA_CUDA(c, launch_fold(L->d_desc, (int)L->elts.size(), c->catalog, L->occ_ret, L->occ_lim, L->q, nullptr,
                             nullptr, L->bm, L->precision == ARA_FP32_TABLE, c->d_evt64, s, c->d_evt64_inexact),
              "binary64 event table");
+    // ... interleaved with the layer's entries, so the kernel's one gather per
+    // occurrence brings both
+    ARA_CUDA(c, ensure(&c->d_yelt_comb, &c->cap_yelt_comb, ((size_t)c->catalog + 1) * (L->entry_bytes() == 16 ? 2 : 1)),
+             "YELT event table");
+    ARA_CUDA(c, launch_yelt_comb(L->d_table, L->entry_bytes(), c->d_evt64, (int64_t)c->catalog + 1, c->d_yelt_comb, s),
+             "YELT event table");
   }
   TimedLaunch tl(c, ARA_TIMING_YELT, s);
   ARA_CUDA(c, launch_yelt(c->d_coff, c->d_chunks, c->d_offsets, c->packed, n_trials, L->d_table,
                           L->entry_bytes(), L->d_bitmap, L->bm, c->catalog, out, ydst, odst, c->device, s,
-                          ydst ? c->d_evt64 : nullptr, c->d_evt64_inexact),
+                          ydst ? c->d_yelt_comb : nullptr, c->d_evt64_inexact),
            "YELT kernel launch");
   tl.done();
   if (yelt_out && !ydev)

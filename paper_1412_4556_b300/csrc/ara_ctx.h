@@ -139,6 +139,8 @@ struct ara_ctx {
   double *d_sel_out_batch = nullptr;
   size_t cap_sel_out_batch = 0;
   double *d_evt64 = nullptr;                // ara_layer_yelt: the layer's table in binary64
+  ulonglong2 *d_yelt_comb = nullptr;  // the YELT's interleaved entry + binary64 table
+  size_t cap_yelt_comb = 0;
   size_t cap_evt64 = 0;
   unsigned int *d_evt64_inexact = nullptr;  // set when that table is not exact
   size_t cap_evt64_inexact = 0;

@@ -338,14 +338,21 @@ cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const floa
 // Year Event Loss Table of one layer: per-occurrence increments into
 // yelt[raw_off[t] + k] (nullable), each trial's largest increment into
 // occ_max[t] (nullable), and the trial loss into L.ylt[t] (nullable).
-// table64 (nullable, catalog + 1 values) is the layer's table in binary64,
-// used when *inexact (device) is 0: then it holds exactly the table's
-// values and an in-layer increment is read instead of converted.
+// With yelt, comb (required) is the layer's table with each event's binary64
+// value interleaved (launch_yelt_comb), so one gather brings both; while
+// *inexact (device) is 0 the binary64 values are exactly the entries' and an
+// in-layer increment is read instead of converted.
 cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
                         int64_t n_trials, const void *table, int entry_bytes, const uint32_t *bitmap,
                         BitmapLayout bm, int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max,
-                        int device, cudaStream_t s, const double *table64 = nullptr,
+                        int device, cudaStream_t s, const ulonglong2 *comb = nullptr,
                         const unsigned int *inexact = nullptr);
+
+// Interleave n_events table entries (entry_bytes 16 or 8) with their binary64
+// values table64[e]: comb holds {lo, hi} {value, 0} per event for 16-byte
+// entries (32 bytes: one sector) and {entry, value} for 8-byte entries.
+cudaError_t launch_yelt_comb(const void *table, int entry_bytes, const double *table64, int64_t n_events,
+                             ulonglong2 *comb, cudaStream_t s);
 
 // PML/TVaR on the device.  ws must hold select_workspace_bytes(n_rp) bytes
 // per layer; the batch form reads n_layers YLTs of n values each (layer-major)

@@ -61,6 +61,41 @@ __device__ __forceinline__ unsigned long long gather_or_zero8(const unsigned lon
   return a;
 }
 
+// A table entry as a 128-bit integer (zero without a load when hit is 0).
+template <int EB>
+__device__ __forceinline__ U128 entry_or_zero(const void *table, uint32_t id, uint32_t hit, unsigned long long pol) {
+  if constexpr (EB == 16) {
+    const ulonglong2 e = gather_or_zero(static_cast<const ulonglong2 *>(table) + id, hit, pol);
+    return U128{e.x, e.y};
+  } else {
+    return U128{gather_or_zero8(static_cast<const unsigned long long *>(table) + id, hit, pol), 0ull};
+  }
+}
+
+// An entry and its binary64 value from the interleaved table: one 32-byte
+// (16-byte entries) or 16-byte (8-byte entries) load, zero when hit is 0.
+template <int EB>
+__device__ __forceinline__ void gather_comb(const ulonglong2 *comb, uint32_t id, uint32_t hit, unsigned long long pol,
+                                            U128 &e, unsigned long long &f64) {
+  unsigned long long a = 0ull, b = 0ull, c = 0ull, d = 0ull;
+  if constexpr (EB == 16) {
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%5], %6;\n\t}"
+        : "+l"(a), "+l"(b), "+l"(c), "+l"(d)
+        : "r"(hit), "l"(comb + 2 * (size_t)id), "l"(pol));
+    e = U128{a, b};
+    f64 = c;
+  } else {
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%3], %4;\n\t}"
+        : "+l"(a), "+l"(b)
+        : "r"(hit), "l"(comb + id), "l"(pol));
+    e = U128{a, 0ull};
+    f64 = b;
+  }
+  (void)d;
+}
+
 __device__ __forceinline__ int4 ld_chunk(const int4 *p, unsigned long long pol) {
   int4 v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
@@ -145,7 +180,7 @@ __global__ void __launch_bounds__(kYltThreads, 1)
 yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
             const int64_t *__restrict__ raw_off, int64_t n_trials, const void *__restrict__ table,
             const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul, int4 sent4, LayerOut L,
-            double *__restrict__ yelt, double *__restrict__ occ_max, const double *__restrict__ table64,
+            double *__restrict__ yelt, double *__restrict__ occ_max, const ulonglong2 *__restrict__ comb,
             const unsigned int *__restrict__ inexact) {
   constexpr int IDS = PACKED ? 6 : 4;
   // lanes per trial (measured: 16 with per-occurrence output, 8 without)
@@ -165,8 +200,8 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
   const bool exact = L.af.exact != 0;
   const unsigned long long pol_stream = l2_evict_first();
   const unsigned long long pol_tab = l2_evict_last();
-  // the binary64 table holds exactly the entries' values: read increments from it
-  const bool use64 = OUT && table64 != nullptr && *inexact == 0u;
+  // the binary64 values hold exactly the entries' values: read increments from them
+  const bool use64 = OUT && *inexact == 0u;
   // AggR + AggL on the grid, saturated (an unreachable limit stays unreachable)
   U128 ret_lim = add(L.af.ret, L.af.lim);
   if (!ge128(ret_lim, L.af.ret)) ret_lim = U128{~0ull, ~0ull};
@@ -198,20 +233,34 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       }
       uint32_t id[IDS];
       chunk_ids_y<PACKED>(v, id);
-      U128 x[IDS];
+      // Without output the entries stay in registers; with output only their
+      // binary64 values do (the per-occurrence path, rare, gathers an entry
+      // again: the line is still in L2).
+      U128 x[OUT ? 1 : IDS];
+      unsigned long long f[OUT ? IDS : 1];
+      uint32_t hits = 0u;
       U128 tot{0ull, 0ull};
 #pragma unroll
       for (int i = 0; i < IDS; ++i) {
         const uint32_t word = s_bm[bitmap_word(id[i], bm_mul)];
         const uint32_t hit = __funnelshift_r(word, word, id[i]) & 1u;
-        if constexpr (EB == 16) {
-          const ulonglong2 e = gather_or_zero(static_cast<const ulonglong2 *>(table) + id[i], hit, pol_tab);
-          x[i] = U128{e.x, e.y};
+        if constexpr (OUT) {
+          hits |= hit << i;
+          U128 e;
+          gather_comb<EB>(comb, id[i], hit, pol_tab, e, f[i]);
+          tot = add(tot, e);
         } else {
-          x[i] = U128{gather_or_zero8(static_cast<const unsigned long long *>(table) + id[i], hit, pol_tab), 0ull};
+          x[i] = entry_or_zero<EB>(table, id[i], hit, pol_tab);
+          tot = add(tot, x[i]);
         }
-        tot = add(tot, x[i]);
       }
+      // entry i of this lane's chunk (with output: gathered again)
+      auto entry = [&](int i) -> U128 {
+        if constexpr (OUT)
+          return entry_or_zero<EB>(table, id[i], (hits >> i) & 1u, pol_tab);
+        else
+          return x[i];
+      };
       // inclusive scan of the lane totals across the trial's lanes
       U128 incl = tot;
 #pragma unroll
@@ -237,35 +286,33 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
         inside = ge128(P, L.af.ret) && ge128(ret_lim, P1);
         fast = __all_sync(0xFFFFFFFFu, inside || ge128(L.af.ret, P1) || ge128(P, ret_lim));
       }
-      if (!OUT && fast) {
-        // Inside the layer an increment is its entry, and the conversion is
-        // monotone: keep the largest entry, convert it once per trial.  Slots
-        // past the trial's end hold the sentinel (entry 0), which cannot
-        // raise a maximum, so only the stores need the slot count.
-        if (inside) {
+      if constexpr (!OUT) {
+        if (fast) {
+          // Inside the layer an increment is its entry, and the conversion is
+          // monotone: keep the largest entry, convert it once per trial.  Slots
+          // past the trial's end hold the sentinel (entry 0), which cannot
+          // raise a maximum, so only the stores need the slot count.
+          if (inside) {
 #pragma unroll
-          for (int i = 0; i < IDS; ++i)
-            if (ge128(x[i], best_fx)) best_fx = x[i];
+            for (int i = 0; i < IDS; ++i)
+              if (ge128(x[i], best_fx)) best_fx = x[i];
+          }
+          carry = add(carry, step_total);
+          continue;
         }
-        carry = add(carry, step_total);
-        continue;
       }
       if (fast) {
         double inc[IDS];
-        if (use64) {
-#pragma unroll
-          for (int i = 0; i < IDS; ++i) {
-            inc[i] = 0.0;
-            const uint32_t nz = inside && (x[i].lo | x[i].hi) != 0ull ? 1u : 0u;
-            asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-                "@p ld.global.nc.f64 %0, [%2];\n\t}"
-                : "+d"(inc[i])
-                : "r"(nz), "l"(table64 + id[i]));
-          }
-        }
 #pragma unroll
         for (int i = 0; i < IDS; ++i) {
-          if (!use64) inc[i] = inside ? from_fixed_exact(x[i], L.q) : 0.0;
+          if constexpr (OUT) {
+            if (use64)
+              inc[i] = inside ? __longlong_as_double((long long)f[i]) : 0.0;
+            else
+              inc[i] = inside ? from_fixed_exact(entry(i), L.q) : 0.0;
+          } else {
+            inc[i] = inside ? from_fixed_exact(x[i], L.q) : 0.0;
+          }
           const unsigned long long b = (unsigned long long)__double_as_longlong(inc[i]);
           best = b > best ? b : best;
         }
@@ -306,7 +353,7 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       double a_fp = exact ? 0.0 : clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
 #pragma unroll
       for (int i = 0; i < IDS; ++i) {
-        P = add(P, x[i]);
+        P = add(P, entry(i));
         double inc;
         if (exact) {
           const U128 a = clamp_fixed(P, L.af);
@@ -347,7 +394,7 @@ template <bool PACKED, int EB, bool OUT>
 static cudaError_t launch_yelt_t(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, int64_t n_trials,
                                  const void *table, const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel,
                                  const LayerOut &L, double *yelt, double *occ_max, int sms, cudaStream_t s,
-                                 const double *table64, const unsigned int *inexact) {
+                                 const ulonglong2 *comb, const unsigned int *inexact) {
   const size_t smem = (size_t)bm.words * 4u;
   cudaError_t err = cudaFuncSetAttribute(yelt_kernel<PACKED, EB, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -356,22 +403,23 @@ static cudaError_t launch_yelt_t(const int64_t *coff, const int4 *chunks, const 
   const int4 sent4 = PACKED ? pack6(sv) : make_int4(sentinel, sentinel, sentinel, sentinel);
   yelt_kernel<PACKED, EB, OUT><<<sms, kYltThreads, smem, s>>>(coff, chunks, raw_off, n_trials, table,
                                                          reinterpret_cast<const uint4 *>(bitmap), bm.words / 4,
-                                                         bm.mul, sent4, L, yelt, occ_max, table64, inexact);
+                                                         bm.mul, sent4, L, yelt, occ_max, comb, inexact);
   return cudaGetLastError();
 }
 
 cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *raw_off, bool packed,
                         int64_t n_trials, const void *table, int entry_bytes, const uint32_t *bitmap,
                         BitmapLayout bm, int32_t sentinel, const LayerOut &L, double *yelt, double *occ_max,
-                        int device, cudaStream_t s, const double *table64, const unsigned int *inexact) {
+                        int device, cudaStream_t s, const ulonglong2 *comb, const unsigned int *inexact) {
   if (n_trials <= 0) return cudaSuccess;
+  if (yelt != nullptr && (comb == nullptr || inexact == nullptr)) return cudaErrorInvalidValue;
   int sms = 148;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
   const bool out = yelt != nullptr;
 #define ARA_YELT_LAUNCH(P, E, O)                                                                             \
   launch_yelt_t<P, E, O>(coff, chunks, raw_off, n_trials, table, bitmap, bm, sentinel, L, yelt, occ_max, sms, s, \
-                         table64, inexact)
+                         comb, inexact)
   if (entry_bytes == 16) {
     if (packed) return out ? ARA_YELT_LAUNCH(true, 16, true) : ARA_YELT_LAUNCH(true, 16, false);
     return out ? ARA_YELT_LAUNCH(false, 16, true) : ARA_YELT_LAUNCH(false, 16, false);
@@ -379,6 +427,33 @@ cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *
   if (packed) return out ? ARA_YELT_LAUNCH(true, 8, true) : ARA_YELT_LAUNCH(true, 8, false);
   return out ? ARA_YELT_LAUNCH(false, 8, true) : ARA_YELT_LAUNCH(false, 8, false);
 #undef ARA_YELT_LAUNCH
+}
+
+namespace {
+
+__global__ void yelt_comb_kernel(const void *__restrict__ table, int entry_bytes, const double *__restrict__ table64,
+                                 int64_t n, ulonglong2 *__restrict__ comb) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long f = (unsigned long long)__double_as_longlong(table64[e]);
+    if (entry_bytes == 16) {
+      comb[2 * e] = static_cast<const ulonglong2 *>(table)[e];
+      comb[2 * e + 1] = make_ulonglong2(f, 0ull);
+    } else {
+      comb[e] = make_ulonglong2(static_cast<const unsigned long long *>(table)[e], f);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_yelt_comb(const void *table, int entry_bytes, const double *table64, int64_t n_events,
+                             ulonglong2 *comb, cudaStream_t s) {
+  if (n_events <= 0) return cudaSuccess;
+  if (entry_bytes != 16 && entry_bytes != 8) return cudaErrorInvalidValue;
+  int64_t blocks = (n_events + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  yelt_comb_kernel<<<(int)blocks, 256, 0, s>>>(table, entry_bytes, table64, n_events, comb);
+  return cudaGetLastError();
 }
 
 }  // namespace ara
