@@ -17,7 +17,11 @@
 // segments are the trials.  The running
 // sums are 128-bit fixed-point integers, so every P_k is exact; when the
 // aggregate terms lie on the table's grid the clamps and differences are
-// exact integers too and each increment is rounded to binary64 once.
+// exact integers too and each increment is rounded to binary64 once.  With
+// per-occurrence output the entries are gathered from a copy of the table
+// holding each event's binary64 value beside its entry (one 32-byte sector
+// for FP64 layers), so an increment inside the layer is read, not converted,
+// and needs no second gather.
 #include "ara_internal.cuh"
 
 namespace ara {
