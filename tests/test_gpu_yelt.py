@@ -95,9 +95,12 @@ def test_ragged_trials_and_catalogs(engine, catalog):
         np.testing.assert_array_equal(m41, occ_max[:n])
 
 
-def test_fp32_table_layer(engine):
+@pytest.mark.parametrize("catalog", [200_000, 3_000_000])
+def test_fp32_table_layer(engine, catalog):
+    """FP32-table layers (8-byte entries, 16-byte interleaved entries with
+    output), with packed (catalog < 2^21) and plain id chunks."""
     from paper_1412_4556_b300 import ARA_FP32_TABLE
-    w = S.batched(n_layers=3, n_trials=3_000, lam=200.0, catalog_size=200_000, n_pool=30)
+    w = S.batched(n_layers=3, n_trials=3_000, lam=200.0, catalog_size=catalog, n_pool=30)
     engine.load_yet_from(w.yet)
     first = engine.load_pool(w.pool)
     for lay in w.layers:
