@@ -232,6 +232,20 @@ ARA_API ara_status ara_pml_tvar(ara_ctx *ctx, const double *ylt, int64_t n,
                         const double *return_periods, int32_t n_rp, double *pml_out,
                         double *tvar_out);
 
+/* ara_pml_tvar queued on the context's stream, for a caller that keeps the
+ * results on the device (pricing layer after layer without waiting for each):
+ *   ylt             double[n], DEVICE memory; finite and >= 0
+ *   return_periods  double[n_rp], host; as for ara_pml_tvar
+ *   out             double[2 * n_rp], DEVICE memory: PML_0..PML_{n_rp-1}, then
+ *                   TVaR_0..TVaR_{n_rp-1}, written in the stream's order
+ * Returns once the work is queued: the host does not wait.  Same definitions
+ * and bits as ara_pml_tvar.  Losses that fail the check (NaN, negative or
+ * infinite) cannot be reported by the return status: every output is then a
+ * quiet NaN.  Errors found on the host: ARA_E_INVALID_ARG (bad RP, host
+ * pointers), ARA_E_CUDA. */
+ARA_API ara_status ara_pml_tvar_async(ara_ctx *ctx, const double *ylt, int64_t n,
+                                      const double *return_periods, int32_t n_rp, double *out);
+
 /* The k largest of a YLT's n trial losses, for the exchange between trial
  * shards (Section IV-C spreads one analysis' trials over several GPUs).  PML
  * and TVaR at return period RP read only the floor(N / RP) largest of N

@@ -220,6 +220,20 @@ class Engine:
                              pml.ctypes.data, tvar.ctypes.data)
         return pml, tvar
 
+    def pml_tvar_async(self, ylt, return_periods: Sequence[float], out):
+        """PML and TVaR of a CUDA-tensor YLT queued on the engine's stream
+        without waiting: ``out`` (a CUDA float64 tensor of 2 * len(return_periods)
+        values) receives the PMLs, then the TVaRs, in stream order (quiet NaNs
+        when the losses fail their check)."""
+        p, keep = _arg(ylt, np.float64, "ylt")
+        po, ko = _arg(out, np.float64, "out")
+        if keep is not ylt or ko is not out:
+            # a temporary copy could be freed before the queued work reads it
+            raise TypeError("ylt and out must be contiguous float64 CUDA tensors")
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        _native.ara_pml_tvar_async(self.ctx, p, int(ylt.shape[0]), rps.ctypes.data, int(rps.shape[0]), po)
+        return out
+
     def ylt_tail(self, ylt, k: int, out=None):
         """The k largest values of a YLT (NumPy array or CUDA tensor): the
         values above the k-th largest in index order, then copies of it.

@@ -74,6 +74,7 @@ PROTOTYPES = {
     "ara_layer_event_table": (_i32, [_vp, _i32, _vp]),
     "ara_layer_ylt": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "ara_pml_tvar": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp, _vp]),
+    "ara_pml_tvar_async": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp]),
     "ara_pml_tvar_noalloc": (_i32, [_vp, _i64, _vp, _i32, _vp, _vp, _vp]),
     "ara_ylt_tail": (_i32, [_vp, _vp, _i64, _i64, _vp]),
     "ara_pml_tvar_tail": (_i32, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp]),
@@ -186,6 +187,10 @@ def ara_pml_tvar(ctx: int, ylt: int, n: int, return_periods: int, n_rp: int, pml
                  tvar_out: int) -> None:
     _check(ctx, lib.ara_pml_tvar(ctx, ylt or None, int(n), return_periods or None, int(n_rp),
                                  pml_out or None, tvar_out or None))
+
+
+def ara_pml_tvar_async(ctx: int, ylt: int, n: int, return_periods: int, n_rp: int, out: int) -> None:
+    _check(ctx, lib.ara_pml_tvar_async(ctx, ylt or None, int(n), return_periods or None, int(n_rp), out or None))
 
 
 def ara_ylt_tail(ctx: int, ylt: int, n: int, k: int, tail_out: int) -> None:

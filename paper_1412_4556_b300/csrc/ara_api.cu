@@ -1082,6 +1082,48 @@ ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *
   return pml_tvar_ranks(c, ylt, n, k, n_rp, n, pml_out, tvar_out);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The queued form's results: the selection's outputs, or quiet NaNs when the
+// losses failed their check (which the synchronous form reports as a status).
+__global__ void pml_tvar_out_kernel(const double *__restrict__ sel_out, const unsigned int *__restrict__ err, int n,
+                                    double *__restrict__ out) {
+  const int i = threadIdx.x;
+  if (i < n) out[i] = *err ? __longlong_as_double(0x7FF8000000000000LL) : sel_out[i];
+}
+
+cudaError_t launch_pml_tvar_out(const double *sel_out, const unsigned int *err, int n, double *out, cudaStream_t s) {
+  pml_tvar_out_kernel<<<1, 2 * kMaxReturnPeriods, 0, s>>>(sel_out, err, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+ara_status ara_pml_tvar_async(ara_ctx *c, const double *ylt, int64_t n, const double *rps, int32_t n_rp,
+                              double *out) {
+  ARA_ENTER(c);
+  ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
+  if (!out) return fail(c, ARA_E_INVALID_ARG, "NULL output array");
+  if (!is_device_ptr(ylt) || !is_device_ptr(out))
+    return fail(c, ARA_E_INVALID_ARG, "ylt and out must be device memory");
+  int64_t k[kMaxReturnPeriods];
+  ara_status st = ranks_of(c, n, rps, n_rp, n, k);
+  if (st) return st;
+  cudaStream_t s = c->stream;
+  ARA_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), s), "cudaMemsetAsync");
+  TimedLaunch tl(c, ARA_TIMING_PML, s);
+  ARA_CUDA(c, launch_pml_tvar(ylt, n, k, n_rp, c->d_sel_ws, c->d_sel_out, c->d_err, c->device, s, n),
+           "PML/TVaR kernels");
+  tl.done();
+  ARA_CUDA(c, launch_pml_tvar_out(c->d_sel_out, c->d_err, 2 * n_rp, out, s), "PML/TVaR output");
+  return ARA_OK;
+}
+
 ara_status ara_ylt_tail(ara_ctx *c, const double *ylt, int64_t n, int64_t k, double *tail_out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");

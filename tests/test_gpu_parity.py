@@ -429,3 +429,48 @@ def test_host_ids_load_in_pieces(engine, catalog):
         assert ei.value.name == "ARA_E_EVENT_RANGE"
     engine.load_yet(catalog, yet.offsets, h_ids.numpy())
     np.testing.assert_array_equal(engine.layer_ylt(L).view(np.uint64), ref.view(np.uint64))
+
+
+def test_pml_tvar_queued_matches_the_synchronous_form(engine):
+    """ara_pml_tvar_async: several selections queued back to back on the
+    engine's stream give the bits of ara_pml_tvar; losses that fail the check
+    give NaN outputs; host pointers are refused."""
+    import torch
+    from paper_1412_4556_b300 import AraError
+    w = S.tiny()
+    rps = [10.0, 50.0, 100.0]
+    (L,) = load_workload(engine, w)
+    dev = torch.device("cuda", 0)
+    base = torch.from_numpy(engine.layer_ylt(L)).to(dev)
+    ylts = [base, base * 0.5, torch.flip(base, [0]), base[:777].contiguous()]
+    outs = [torch.full((2 * len(rps),), -1.0, dtype=torch.float64, device=dev) for _ in ylts]
+    torch.cuda.synchronize()
+    for y, o in zip(ylts, outs):
+        engine.pml_tvar_async(y, rps, o)
+    torch.cuda.synchronize()
+    for y, o in zip(ylts, outs):
+        pml, tvar = engine.pml_tvar(y.cpu().numpy(), rps)
+        got = o.cpu().numpy()
+        np.testing.assert_array_equal(got[:3].view(np.uint64), pml.view(np.uint64))
+        np.testing.assert_array_equal(got[3:].view(np.uint64), tvar.view(np.uint64))
+    for bad_value in (float("nan"), -1.0, float("inf")):
+        bad = base.clone()
+        bad[5] = bad_value
+        o = torch.zeros(2 * len(rps), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()  # the engine's stream is not torch's
+        engine.pml_tvar_async(bad, rps, o)
+        torch.cuda.synchronize()
+        assert torch.isnan(o).all()
+    # the next queued call is not affected by the failed one
+    o = torch.zeros(2 * len(rps), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    engine.pml_tvar_async(base, rps, o)
+    torch.cuda.synchronize()
+    pml, _ = engine.pml_tvar(base.cpu().numpy(), rps)
+    np.testing.assert_array_equal(o.cpu().numpy()[:3], pml)
+    with pytest.raises(AraError) as ei:
+        engine.pml_tvar_async(base.cpu().numpy(), rps, o)
+    assert ei.value.name == "ARA_E_INVALID_ARG"
+    with pytest.raises(AraError) as ei:
+        engine.pml_tvar_async(base, [1e9], o)
+    assert ei.value.name == "ARA_E_INVALID_ARG"
