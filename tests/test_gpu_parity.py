@@ -413,6 +413,10 @@ def test_host_ids_load_in_pieces(engine, catalog):
     engine.load_yet(catalog, yet.offsets, h_ids.numpy())
     y = engine.layer_ylt(L)
     np.testing.assert_array_equal(y.view(np.uint64), ref.view(np.uint64))
+    # device offsets with host ids: the pieces are sized from the offsets' last
+    # entry, read back before the first piece starts
+    engine.load_yet(catalog, torch.from_numpy(yet.offsets).to(dev), h_ids.numpy())
+    np.testing.assert_array_equal(engine.layer_ylt(L).view(np.uint64), ref.view(np.uint64))
     off = yet.offsets
     around = np.concatenate([np.searchsorted(off, b * step, side="right") + np.arange(-3, 3)
                              for b in range(1, pieces)])
