@@ -405,7 +405,9 @@ def test_host_ids_load_in_pieces(engine, catalog):
     pool = _custom_pool(catalog, [50_000, 30_000, 20_000], 5)
     lay = S.Layer([0, 1, 2], 1e3, 5e6, 1e4, 1e9)
     dev = torch.device("cuda", 0)
-    engine.load_yet(catalog, torch.from_numpy(yet.offsets).to(dev), torch.from_numpy(yet.ids).to(dev))
+    d_off, d_ids = torch.from_numpy(yet.offsets).to(dev), torch.from_numpy(yet.ids).to(dev)
+    torch.cuda.synchronize()  # the engine's stream is not torch's
+    engine.load_yet(catalog, d_off, d_ids)
     first = engine.load_pool(pool)
     L = engine.define_layer([first + j for j in lay.elts], lay.occ_ret, lay.occ_lim, lay.agg_ret, lay.agg_lim)
     ref = engine.layer_ylt(L)
@@ -415,7 +417,7 @@ def test_host_ids_load_in_pieces(engine, catalog):
     np.testing.assert_array_equal(y.view(np.uint64), ref.view(np.uint64))
     # device offsets with host ids: the pieces are sized from the offsets' last
     # entry, read back before the first piece starts
-    engine.load_yet(catalog, torch.from_numpy(yet.offsets).to(dev), h_ids.numpy())
+    engine.load_yet(catalog, d_off, h_ids.numpy())
     np.testing.assert_array_equal(engine.layer_ylt(L).view(np.uint64), ref.view(np.uint64))
     off = yet.offsets
     around = np.concatenate([np.searchsorted(off, b * step, side="right") + np.arange(-3, 3)
