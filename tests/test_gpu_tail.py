@@ -79,6 +79,7 @@ def test_tail_edges_and_device_buffers(engine):
     check_tail(zeros, 10, engine.ylt_tail(zeros, 10))
     d = torch.from_numpy(y).cuda()
     out = torch.empty(500, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # the engine's stream is not torch's
     engine.ylt_tail(d, 500, out=out)
     torch.cuda.synchronize()
     host = out.cpu().numpy()
