@@ -174,26 +174,27 @@ def measured_hbm_peak():
         return 6400.0, "fallback"
 
 
-def kernel_source_digest() -> str:
+def kernel_source_digest(kernel_file: str = "ylt.cu") -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("ylt.cu", "ara_internal.cuh"):
+    for f in (kernel_file, "ara_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1412_4556_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch(occurrences: int):
-    """DRAM bytes per YLT launch from the committed ncu summary, scaled to this
+def ncu_traffic_per_launch(occurrences: int, profile: str = "ylt_fp64_kernel_paper_scale.md",
+                           kernel_file: str = "ylt.cu"):
+    """DRAM bytes per launch from a committed ncu summary, scaled to this
     launch by occurrences; None when the kernel changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "ylt_fp64_kernel_paper_scale.md")
+    p = os.path.join(ROOT, "profiles", profile)
     try:
         text = open(p).read()
     except OSError:
         return None
     m = re.search(r"kernel_digest:\s*([0-9a-f]+)", text)
     b = re.search(r"dram_bytes_per_occurrence:\s*([0-9.eE+-]+)", text)
-    if not m or not b or m.group(1) != kernel_source_digest():
+    if not m or not b or m.group(1) != kernel_source_digest(kernel_file):
         return None
     return float(b.group(1)) * occurrences
 
@@ -888,14 +889,18 @@ def run_yelt(args):
                    "l2": "inputs larger than L2: the 2.67 GB id stream and the 8 GB YELT pass through HBM "
                          "every step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "yelt_kernel",
+                     "frac": achieved / peak,
+                     "traffic": ncu_traffic_per_launch(M, "yelt_kernel_paper_scale.md", "yelt.cu"),
+                     "kernel": "yelt_kernel",
                      "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_kind": peak_kind, "frac_of_nominal_8000_gbs": achieved / 8000.0},
         "breakdown_ms": {"yelt_kernel_with_output": kern_ms,
                          "rpl_report_yelt_kernel": r_ms / max(n_r, 1)},
         "rpl": {k: v.tolist() for k, v in rep.items()},
         "clocks": clocks.summary(),
-        "gpu_launches": args.steps * (1 + 1 + 1 + 10),
+        # fold; binary64 fold, interleave, YELT kernel; report pass and the
+        # AEP/OEP selection (init + 8 passes + sum)
+        "gpu_launches": args.steps * (1 + 3 + 1 + 10),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
