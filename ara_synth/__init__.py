@@ -147,16 +147,47 @@ def _fill_ids(seed: int, catalog: int, out: np.ndarray, threads: int) -> None:
             list(ex.map(work, range(n_chunks)))
 
 
-def _sorted_timestamps(seed: int, offsets: np.ndarray, days: float) -> np.ndarray:
-    """Uniform [0, days) time-stamps, sorted ascending within each trial."""
+_TS_TRIALS = 1 << 14  # trials per independently seeded chunk of time-stamps
+
+
+def _sorted_timestamps(seed: int, offsets: np.ndarray, days: float, threads: int = 1) -> np.ndarray:
+    """Uniform [0, days) time-stamps, sorted ascending within each trial.
+
+    The n order statistics of n uniforms on [0, 1) are distributed as the
+    partial sums of n + 1 standard exponential gaps divided by their total
+    (Devroye, Non-Uniform Random Variate Generation, 1986, V.2), so each
+    trial's sorted time-stamps come from one cumulative sum, with no sort.
+    Chunks of 2^14 trials draw from their own seeded streams."""
+    n = offsets.shape[0] - 1
     m = int(offsets[-1])
-    g = rng_for(seed, "yet-ts")
-    u = g.random(m, dtype=np.float64) * days
-    counts = np.diff(offsets)
-    trial = np.repeat(np.arange(counts.shape[0], dtype=np.int64), counts)
-    order = np.lexsort((u, trial))
-    ts = u[order].astype(np.float32)
-    # float32 rounding keeps the order (rounding is monotone), so ts stays sorted.
+    ts = np.empty(m, dtype=np.float32)
+    n_chunks = (n + _TS_TRIALS - 1) // _TS_TRIALS
+
+    def work(c: int) -> None:
+        t0, t1 = c * _TS_TRIALS, min(n, (c + 1) * _TS_TRIALS)
+        a, b = int(offsets[t0]), int(offsets[t1])
+        counts = np.diff(offsets[t0:t1 + 1])
+        g = rng_for(seed, "yet-ts", c)
+        gaps = g.standard_exponential(b - a + (t1 - t0))
+        cs = np.cumsum(gaps)
+        # trial t's gaps sit at [start[t], start[t] + counts[t]], one extra gap
+        # closing the trial; its time-stamps are the first counts[t] partial
+        # sums, less the sum before the trial, over the trial's total
+        start = (offsets[t0:t1] - a) + np.arange(t1 - t0)
+        before = np.where(start > 0, cs[np.maximum(start - 1, 0)], 0.0)
+        total = cs[start + counts] - before
+        trial = np.repeat(np.arange(t1 - t0), counts)
+        pos = np.arange(b - a) + trial  # index of each event's gap
+        u = (cs[pos] - before[trial]) / total[trial]
+        # float32 rounding is monotone, so each trial stays sorted
+        ts[a:b] = np.minimum(u * days, np.nextafter(np.float32(days), np.float32(0))).astype(np.float32)
+
+    if n_chunks <= 1 or threads <= 1:
+        for c in range(n_chunks):
+            work(c)
+    else:
+        with _fut.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(work, range(n_chunks)))
     return ts
 
 
@@ -174,8 +205,9 @@ def make_yet(seed: int, catalog_size: int, n_trials: int, lam: float,
     np.cumsum(counts, out=offsets[1:])
     m = int(offsets[-1])
     ids = np.empty(m, dtype=np.int32)
-    _fill_ids(seed, catalog_size, ids, threads or min(32, os.cpu_count() or 1))
-    ts = _sorted_timestamps(seed, offsets, days) if with_timestamps else None
+    threads = threads or min(32, os.cpu_count() or 1)
+    _fill_ids(seed, catalog_size, ids, threads)
+    ts = _sorted_timestamps(seed, offsets, days, threads) if with_timestamps else None
     return YET(catalog_size, offsets, ids, ts)
 
 
@@ -245,12 +277,16 @@ def paper_scale(seed: int = DEFAULT_SEED, n_trials: int = 1_000_000, lam: float 
 
 def batched(seed: int = DEFAULT_SEED, n_layers: int = 64, n_trials: int = 1_000_000,
             lam: float = 1000.0, catalog_size: int = 2_000_000, n_pool: int = 256,
-            with_timestamps: bool = False) -> Workload:
+            with_timestamps: bool = False, yet: Optional[YET] = None) -> Workload:
     """Batched layers: the paper-scale YET shared by ``n_layers`` layers; each
     covers k ~ U{1..32} ELTs from a pool of 256 ELTs of U{10k..50k} events;
     per-layer OccR, OccL, AggR, AggL log-uniform over [1e4,1e6], [1e6,1e8],
-    [1e5,1e7], [1e7,1e9]."""
-    yet = make_yet(seed, catalog_size, n_trials, lam, with_timestamps=with_timestamps)
+    [1e5,1e7], [1e7,1e9].  ``yet``: an already drawn YET to share (the
+    paper-scale YET of the same seed is this YET)."""
+    if yet is None:
+        yet = make_yet(seed, catalog_size, n_trials, lam, with_timestamps=with_timestamps)
+    elif yet.catalog_size != catalog_size:
+        raise ValueError("the shared YET has another catalog size")
     g = rng_for(seed, "pool-sizes")
     sizes = g.integers(10_000, 50_001, size=n_pool)
     gt = rng_for(seed, "pool-terms")

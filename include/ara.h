@@ -516,6 +516,38 @@ ARA_API ara_status ara_set_kernel_timing(ara_ctx *ctx, int32_t enable);
 ARA_API ara_status ara_kernel_timing(ara_ctx *ctx, int32_t channel, int64_t *launches,
                              double *total_ms);
 
+/* Ceilings of the YLT kernel's inner loop, measured on a device (they are
+ * not part of the method: a benchmark states the kernels' rates against
+ * them).  Per occurrence the YLT kernel tests one bit of a shared-memory
+ * bitmap at a random word and, when the event may have a nonzero loss,
+ * gathers its entry from a per-event table held in L2 (Section IV-B: one
+ * memory access per direct-access-table lookup); an FP64 running sum would
+ * need one binary64 add per occurrence.  Each call allocates and frees its
+ * own device buffers on a stream of its own, runs a warm-up launch and
+ * returns the best of five timed launches; messages go to
+ * ara_last_error(NULL).  Errors: ARA_E_INVALID_ARG, ARA_E_NOMEM, ARA_E_CUDA.
+ *
+ * ara_probe_gather: rows of load_bytes x lanes_per_row bytes (at most one
+ * 128-byte line) at random positions of a table of table_bytes, warmed into
+ * L2 by the first launch; each row is read by lanes_per_row lanes of one
+ * warp instruction, load_bytes (8, 16 or 32) each, four rows in flight per
+ * lane group, with the YLT kernel's cache policy (no L1 allocation, L2
+ * evict-last); grid = SM count x ctas_per_sm CTAs of threads_per_cta
+ * threads.  *rows_per_s: rows read per second; *sectors_per_s: 32-byte
+ * sectors per second (a row of fewer than 32 bytes counts one). */
+ARA_API ara_status ara_probe_gather(int device, int64_t table_bytes, int32_t load_bytes,
+                                    int32_t lanes_per_row, int32_t threads_per_cta,
+                                    int32_t ctas_per_sm, double *rows_per_s, double *sectors_per_s);
+
+/* Random 32-bit shared-memory reads per second over the whole device: one
+ * CTA of 1024 threads per SM holding the largest shared array a CTA may
+ * have, eight independent lookups in flight per thread. */
+ARA_API ara_status ara_probe_smem_lookup(int device, double *lookups_per_s);
+
+/* Binary64 adds per second over the whole device: eight independent chains
+ * of round-to-nearest adds per thread, eight CTAs of 256 threads per SM. */
+ARA_API ara_status ara_probe_fp64_add(int device, double *adds_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,9 @@ def load(path: Optional[str] = None):
     lib.ara_oracle_layer_ylt.argtypes = [i32, i64, p, p, i32, p, p, p, p, p, f64, f64, f64, f64,
                                          i32, i32, p, i64, p, p]
     lib.ara_oracle_layer_ylt.restype = C.c_int
+    lib.ara_oracle_layers_ylt.argtypes = [i32, i64, p, p, i32, p, p, p, p, p, p, p, p, p, p, i32, i32,
+                                          p, i64, p, p]
+    lib.ara_oracle_layers_ylt.restype = C.c_int
     lib.ara_oracle_layer_yelt.argtypes = [i32, i64, p, p, i32, p, p, p, p, p, f64, f64, f64, f64,
                                           i32, i32, p, i64, p, p, p, p, p]
     lib.ara_oracle_layer_yelt.restype = C.c_int
@@ -121,6 +124,31 @@ def layer_ylt(yet, pool, layer, trials: Optional[np.ndarray] = None, mode: str =
                                   1 if mode == "memo" else 0, int(threads or os.cpu_count() or 1),
                                   _ptr(sel), int(n), _ptr(ylt), _ptr(pre))
     _check(rc, "ara_oracle_layer_ylt")
+    return ylt, pre
+
+
+def layers_ylt(yet, pool, layers, trials: Optional[np.ndarray] = None, mode: str = "memo",
+               threads: Optional[int] = None, lib=None) -> Tuple[np.ndarray, np.ndarray]:
+    """Trial losses and pre-aggregate sums of several layers, layer by layer
+    (Algorithm 1's loop over the layers of a Program), the YET checked once.
+    Returns (ylt, presum), both float64 of shape (len(layers), n)."""
+    lib = lib or load()
+    off = _c(yet.offsets, np.int64)
+    ids = _c(yet.ids, np.int32)
+    sel = None if trials is None else _c(trials, np.int64)
+    n = yet.n_trials if sel is None else sel.shape[0]
+    nl = len(layers)
+    parts = [_layer_elts(pool, L.elts) for L in layers]  # kept alive for the call
+    ptrs = lambda k: (C.c_void_p * max(nl, 1))(*[_ptr(q[k]) for q in parts])  # noqa: E731
+    n_elts = _c([len(L.elts) for L in layers], np.int32)
+    terms = [_c([getattr(L, a) for L in layers], np.float64) for a in ("occ_ret", "occ_lim", "agg_ret", "agg_lim")]
+    ylt = np.zeros((nl, n), dtype=np.float64)
+    pre = np.zeros((nl, n), dtype=np.float64)
+    rc = lib.ara_oracle_layers_ylt(int(yet.catalog_size), int(yet.n_trials), _ptr(off), _ptr(ids), nl,
+                                   _ptr(n_elts), ptrs(0), ptrs(1), ptrs(2), ptrs(3), ptrs(4),
+                                   *[_ptr(t) for t in terms], 1 if mode == "memo" else 0,
+                                   int(threads or os.cpu_count() or 1), _ptr(sel), int(n), _ptr(ylt), _ptr(pre))
+    _check(rc, "ara_oracle_layers_ylt")
     return ylt, pre
 
 
@@ -195,3 +223,68 @@ def pml_tvar(ylt: np.ndarray, return_periods: Sequence[float], lib=None):
                                  _ptr(pml), _ptr(tvar))
     _check(rc, "ara_oracle_pml_tvar")
     return pml, tvar
+
+
+# ----------------------------------------------------------------- comparison
+# Error forms for checking another implementation's results against the
+# oracle's (pure NumPy on the two result arrays; no part of the method).
+FP64_REL = 1e-12
+REDUCED_REL, REDUCED_FLOOR = 1e-5, 1.0
+
+
+def compare_fp64(g, o, presum) -> dict:
+    """Per-trial errors of YLT g against the oracle's o.  The gate (reading R9)
+    divides by max(|o|, S_o), S_o the oracle's pre-aggregate sum, because the
+    aggregate clamp is 1-Lipschitz; the plain form |g - o| / |o| is reported
+    beside it (a trial with o == 0 fails it when g != 0)."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    pre = np.asarray(presum, dtype=np.float64)
+    err = np.abs(g - o)
+    denom = np.maximum(np.abs(o), pre)
+    r9 = np.where(denom > 0, err / np.where(denom > 0, denom, 1.0), np.where(err > 0, np.inf, 0.0))
+    absn = np.abs(o)
+    plain = np.where(absn > 0, err / np.where(absn > 0, absn, 1.0), np.where(err > 0, np.inf, 0.0))
+    return {"trials": int(g.size), "max_rel_err_r9": float(r9.max()) if r9.size else 0.0,
+            "trials_over_r9_bar": int(np.count_nonzero(r9 > FP64_REL)),
+            "max_rel_err_plain": float(plain.max()) if plain.size else 0.0,
+            "trials_over_plain_bar": int(np.count_nonzero(plain > FP64_REL)),
+            "bitwise_equal_trials": int(np.count_nonzero(g.view(np.uint64) == o.view(np.uint64))),
+            "max_abs_err": float(err.max()) if err.size else 0.0}
+
+
+def compare_reduced(g, o, presum) -> dict:
+    """The same for a reduced-precision YLT: the gate is |g - o| <=
+    max(1e-5 * max(|o|, S_o), 1 USD); the plain form max(1e-5 * |o|, 1 USD)
+    is reported beside it."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    pre = np.asarray(presum, dtype=np.float64)
+    err = np.abs(g - o)
+    bound = np.maximum(REDUCED_REL * np.maximum(np.abs(o), pre), REDUCED_FLOOR)
+    plain = np.maximum(REDUCED_REL * np.abs(o), REDUCED_FLOOR)
+    return {"trials": int(g.size), "max_err_over_bar": float((err / bound).max()) if err.size else 0.0,
+            "trials_over_bar": int(np.count_nonzero(err > bound)),
+            "max_err_over_plain_bar": float((err / plain).max()) if err.size else 0.0,
+            "trials_over_plain_bar": int(np.count_nonzero(err > plain)),
+            "max_rel_err": float(np.max(err / np.maximum(np.maximum(np.abs(o), pre), 1e-300))) if err.size else 0.0,
+            "max_abs_err": float(err.max()) if err.size else 0.0}
+
+
+def compare_pml_tvar(pml_g, tvar_g, pml_o, tvar_o, return_periods, n: int, max_trial_err: float) -> dict:
+    """PML/TVaR of an implementation (from its own YLT of n trials) against
+    the oracle's (from the oracle's YLT).  Order statistics and means of the
+    k largest are 1-Lipschitz in the largest per-trial error; the oracle's
+    sequential tail sum of k = floor(n / RP) terms carries at most (k - 1)
+    roundings of 2^-53 of the sum, and each side's division one more, so the
+    bound is max_trial_err + (k + 1) * 2^-53 * TVaR."""
+    pml_g, tvar_g = np.asarray(pml_g, np.float64), np.asarray(tvar_g, np.float64)
+    pml_o, tvar_o = np.asarray(pml_o, np.float64), np.asarray(tvar_o, np.float64)
+    k = np.floor(n / np.asarray(return_periods, np.float64))
+    bound = max_trial_err + (k + 1.0) * 2.0 ** -53 * np.abs(tvar_o)
+    return {"return_periods": [float(r) for r in return_periods],
+            "pml_abs_err": np.abs(pml_g - pml_o).tolist(), "tvar_abs_err": np.abs(tvar_g - tvar_o).tolist(),
+            "pml_rel_err": (np.abs(pml_g - pml_o) / np.maximum(np.abs(pml_o), 1e-300)).tolist(),
+            "tvar_rel_err": (np.abs(tvar_g - tvar_o) / np.maximum(np.abs(tvar_o), 1e-300)).tolist(),
+            "bound": bound.tolist(),
+            "within_bound": bool(np.all(np.abs(pml_g - pml_o) <= bound) and np.all(np.abs(tvar_g - tvar_o) <= bound))}

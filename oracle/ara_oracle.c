@@ -173,10 +173,21 @@ static int check_yet(int32_t catalog, int64_t n_trials, const int64_t *offsets,
   return ORACLE_OK;
 }
 
+typedef struct {
+  layer_t *L;
+  int32_t first, last; /* event range */
+} memo_job_t;
+
+static void *run_memo_job(void *arg) {
+  memo_job_t *J = (memo_job_t *)arg;
+  for (int32_t e = J->first; e < J->last; ++e) J->L->memo[e] = combined_elt_loss(J->L, e);
+  return NULL;
+}
+
 static int init_layer(layer_t *L, int32_t catalog, int32_t n_elts, const int64_t *elt_off,
                       const int32_t *elt_ids, const double *elt_losses, const double *ded,
                       const double *lim, double occ_ret, double occ_lim, double agg_ret,
-                      double agg_lim, int memoise) {
+                      double agg_lim, int memoise, int32_t n_threads) {
   memset(L, 0, sizeof(*L));
   if (n_elts < 0) return ORACLE_E_ARG;
   L->catalog = catalog;
@@ -194,7 +205,24 @@ static int init_layer(layer_t *L, int32_t catalog, int32_t n_elts, const int64_t
      * once per catalog event with the same ELT loop gives the same bits. */
     L->memo = (double *)malloc((size_t)(catalog ? catalog : 1) * sizeof(double));
     if (!L->memo) return ORACLE_E_NOMEM;
-    for (int32_t e = 0; e < catalog; ++e) L->memo[e] = combined_elt_loss(L, e);
+    /* threads split the catalog; each event's ELT loop is the same sequential
+     * loop whichever thread runs it */
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    if (catalog < 65536) n_threads = 1;
+    pthread_t th[256];
+    memo_job_t jobs[256];
+    for (int32_t i = 0; i < n_threads; ++i) {
+      jobs[i].L = L;
+      jobs[i].first = (int32_t)((int64_t)catalog * i / n_threads);
+      jobs[i].last = (int32_t)((int64_t)catalog * (i + 1) / n_threads);
+    }
+    int32_t started = 0;
+    if (n_threads > 1)
+      for (; started < n_threads; ++started)
+        if (pthread_create(&th[started], NULL, run_memo_job, &jobs[started])) break;
+    for (int32_t i = started; i < n_threads; ++i) run_memo_job(&jobs[i]);
+    for (int32_t i = 0; i < started; ++i) pthread_join(th[i], NULL);
   }
   return ORACLE_OK;
 }
@@ -202,6 +230,40 @@ static int init_layer(layer_t *L, int32_t catalog, int32_t n_elts, const int64_t
 static void free_layer(layer_t *L) {
   free(L->dats);
   free(L->memo);
+}
+
+/* Threads split the trial list; per-trial arithmetic is sequential, so the
+ * results do not depend on the thread count. */
+static void run_trials(const layer_t *L, const int64_t *offsets, const int32_t *ids, const int64_t *sel,
+                       int64_t n, int32_t n_threads, double *ylt_out, double *presum_out) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  if (n < n_threads) n_threads = n > 0 ? (int32_t)n : 1;
+  pthread_t th[256];
+  job_t jobs[256];
+  for (int32_t i = 0; i < n_threads; ++i) {
+    jobs[i].L = L;
+    jobs[i].offsets = offsets;
+    jobs[i].ids = ids;
+    jobs[i].sel = sel;
+    jobs[i].first = n * i / n_threads;
+    jobs[i].last = n * (i + 1) / n_threads;
+    jobs[i].ylt = ylt_out;
+    jobs[i].presum = presum_out;
+  }
+  int32_t started = 0;
+  if (n_threads > 1)
+    for (; started < n_threads; ++started)
+      if (pthread_create(&th[started], NULL, run_job, &jobs[started])) break;
+  for (int32_t i = started; i < n_threads; ++i) run_job(&jobs[i]);
+  for (int32_t i = 0; i < started; ++i) pthread_join(th[i], NULL);
+}
+
+static int check_sel(int64_t n_trials, const int64_t *sel, int64_t n_sel) {
+  if (sel)
+    for (int64_t i = 0; i < n_sel; ++i)
+      if (sel[i] < 0 || sel[i] >= n_trials) return ORACLE_E_ARG;
+  return ORACLE_OK;
 }
 
 /*
@@ -213,8 +275,6 @@ static void free_layer(layer_t *L) {
  *   ded, lim f64[n_elts]                                     -- FT1 per ELT
  *   mode 0 = literal (ELT loop per occurrence), 1 = memoised (R6)
  *   ylt_out f64[n_sel or n_trials]; presum_out (nullable): sum before FT3.
- * Threads split the trial list; per-trial arithmetic is sequential, so the
- * results do not depend on the thread count.
  */
 int ara_oracle_layer_ylt(int32_t catalog, int64_t n_trials, const int64_t *offsets,
                          const int32_t *ids, int32_t n_elts, const int64_t *elt_off,
@@ -223,43 +283,48 @@ int ara_oracle_layer_ylt(int32_t catalog, int64_t n_trials, const int64_t *offse
                          double agg_lim, int32_t mode, int32_t n_threads, const int64_t *sel,
                          int64_t n_sel, double *ylt_out, double *presum_out) {
   int rc = check_yet(catalog, n_trials, offsets, ids);
+  if (!rc) rc = check_sel(n_trials, sel, n_sel);
   if (rc) return rc;
-  int64_t n = sel ? n_sel : n_trials;
-  if (sel)
-    for (int64_t i = 0; i < n_sel; ++i)
-      if (sel[i] < 0 || sel[i] >= n_trials) return ORACLE_E_ARG;
   layer_t L;
   rc = init_layer(&L, catalog, n_elts, elt_off, elt_ids, elt_losses, ded, lim, occ_ret,
-                  occ_lim, agg_ret, agg_lim, mode == 1);
-  if (rc) {
-    free_layer(&L);
-    return rc;
-  }
-  if (n_threads < 1) n_threads = 1;
-  if (n_threads > 256) n_threads = 256;
-  if (n < n_threads) n_threads = n > 0 ? (int32_t)n : 1;
-  pthread_t th[256];
-  job_t jobs[256];
-  for (int32_t i = 0; i < n_threads; ++i) {
-    jobs[i].L = &L;
-    jobs[i].offsets = offsets;
-    jobs[i].ids = ids;
-    jobs[i].sel = sel;
-    jobs[i].first = n * i / n_threads;
-    jobs[i].last = n * (i + 1) / n_threads;
-    jobs[i].ylt = ylt_out;
-    jobs[i].presum = presum_out;
-  }
-  if (n_threads == 1) {
-    run_job(&jobs[0]);
-  } else {
-    int32_t started = 0;
-    for (; started < n_threads; ++started)
-      if (pthread_create(&th[started], NULL, run_job, &jobs[started])) break;
-    for (int32_t i = started; i < n_threads; ++i) run_job(&jobs[i]);
-    for (int32_t i = 0; i < started; ++i) pthread_join(th[i], NULL);
-  }
+                  occ_lim, agg_ret, agg_lim, mode == 1, n_threads);
+  if (!rc) run_trials(&L, offsets, ids, sel, sel ? n_sel : n_trials, n_threads, ylt_out, presum_out);
   free_layer(&L);
+  return rc;
+}
+
+/*
+ * The YLTs of n_layers layers (Algorithm 1's outer loop over the layers of a
+ * Program, each layer's trials priced as ara_oracle_layer_ylt does), with the
+ * YET checked once.  Layer i has n_elts[i] ELTs in the arrays elt_off[i],
+ * elt_ids[i], elt_losses[i], ded[i], lim[i] and the terms occ_ret[i],
+ * occ_lim[i], agg_ret[i], agg_lim[i]; its outputs are
+ * ylt_out[i * n .. i * n + n) and (nullable) presum_out[same], n = n_sel or
+ * n_trials.  Same bits as one ara_oracle_layer_ylt call per layer.
+ */
+int ara_oracle_layers_ylt(int32_t catalog, int64_t n_trials, const int64_t *offsets,
+                          const int32_t *ids, int32_t n_layers, const int32_t *n_elts,
+                          const int64_t *const *elt_off, const int32_t *const *elt_ids,
+                          const double *const *elt_losses, const double *const *ded,
+                          const double *const *lim, const double *occ_ret, const double *occ_lim,
+                          const double *agg_ret, const double *agg_lim, int32_t mode,
+                          int32_t n_threads, const int64_t *sel, int64_t n_sel, double *ylt_out,
+                          double *presum_out) {
+  if (n_layers < 0) return ORACLE_E_ARG;
+  int rc = check_yet(catalog, n_trials, offsets, ids);
+  if (!rc) rc = check_sel(n_trials, sel, n_sel);
+  if (rc) return rc;
+  const int64_t n = sel ? n_sel : n_trials;
+  for (int32_t i = 0; i < n_layers; ++i) {
+    layer_t L;
+    rc = init_layer(&L, catalog, n_elts[i], elt_off[i], elt_ids[i], elt_losses[i], ded[i], lim[i],
+                    occ_ret[i], occ_lim[i], agg_ret[i], agg_lim[i], mode == 1, n_threads);
+    if (!rc)
+      run_trials(&L, offsets, ids, sel, n, n_threads, ylt_out + (size_t)i * (size_t)n,
+                 presum_out ? presum_out + (size_t)i * (size_t)n : NULL);
+    free_layer(&L);
+    if (rc) return rc;
+  }
   return ORACLE_OK;
 }
 
@@ -317,7 +382,7 @@ int ara_oracle_layer_yelt(int32_t catalog, int64_t n_trials, const int64_t *offs
   }
   layer_t L;
   rc = init_layer(&L, catalog, n_elts, elt_off, elt_ids, elt_losses, ded, lim, occ_ret,
-                  occ_lim, agg_ret, agg_lim, mode == 1);
+                  occ_lim, agg_ret, agg_lim, mode == 1, n_threads);
   if (rc) {
     free_layer(&L);
     return rc;
@@ -355,7 +420,7 @@ int ara_oracle_trial_trace(int32_t catalog, int64_t count, const int32_t *ids, i
     if (ids[k] < 0 || ids[k] >= catalog) return ORACLE_E_RANGE;
   layer_t L;
   int rc = init_layer(&L, catalog, n_elts, elt_off, elt_ids, elt_losses, ded, lim, occ_ret,
-                      occ_lim, agg_ret, agg_lim, 0);
+                      occ_lim, agg_ret, agg_lim, 0, 1);
   if (rc) {
     free_layer(&L);
     return rc;
@@ -372,7 +437,7 @@ int ara_oracle_event_table(int32_t catalog, int32_t n_elts, const int64_t *elt_o
                            const double *lim, double occ_ret, double occ_lim, double *out) {
   layer_t L;
   int rc = init_layer(&L, catalog, n_elts, elt_off, elt_ids, elt_losses, ded, lim, occ_ret,
-                      occ_lim, 0.0, 0.0, 0);
+                      occ_lim, 0.0, 0.0, 0, 1);
   if (rc) {
     free_layer(&L);
     return rc;

@@ -95,6 +95,9 @@ PROTOTYPES = {
     "ara_service_cancel": (_i32, [_vp, _i64]),
     "ara_service_get_stats": (_i32, [_vp, C.POINTER(ServiceStats)]),
     "ara_service_destroy": (None, [_vp]),
+    "ara_probe_gather": (_i32, [C.c_int, _i64, _i32, _i32, _i32, _i32, C.POINTER(_f64), C.POINTER(_f64)]),
+    "ara_probe_smem_lookup": (_i32, [C.c_int, C.POINTER(_f64)]),
+    "ara_probe_fp64_add": (_i32, [C.c_int, C.POINTER(_f64)]),
 }
 
 
@@ -305,3 +308,26 @@ def ara_service_get_stats(svc: int) -> ServiceStats:
 
 def ara_service_destroy(svc: int) -> None:
     lib.ara_service_destroy(svc)
+
+
+def ara_probe_gather(device: int, table_bytes: int, load_bytes: int, lanes_per_row: int,
+                     threads_per_cta: int = 1024, ctas_per_sm: int = 1):
+    """(rows/s, 32-byte sectors/s) of random row reads from an L2-resident table."""
+    rows, sectors = _f64(0.0), _f64(0.0)
+    _check(None, lib.ara_probe_gather(int(device), int(table_bytes), int(load_bytes), int(lanes_per_row),
+                                      int(threads_per_cta), int(ctas_per_sm), C.byref(rows), C.byref(sectors)))
+    return rows.value, sectors.value
+
+
+def ara_probe_smem_lookup(device: int) -> float:
+    """Random 32-bit shared-memory lookups per second over the device."""
+    out = _f64(0.0)
+    _check(None, lib.ara_probe_smem_lookup(int(device), C.byref(out)))
+    return out.value
+
+
+def ara_probe_fp64_add(device: int) -> float:
+    """Binary64 adds per second over the device."""
+    out = _f64(0.0)
+    _check(None, lib.ara_probe_fp64_add(int(device), C.byref(out)))
+    return out.value

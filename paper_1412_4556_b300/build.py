@@ -6,6 +6,7 @@ built library.  The library exports the C ABI declared in ``include/ara.h``.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -15,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libara_b300.so")
-SOURCES = ["ara_api.cu", "fold.cu", "ylt.cu", "select.cu", "validate.cu", "noalloc.cu", "service.cu", "yelt.cu", "plan.cu", "ingest.cu", "compact.cu", "tail.cu"]
+SOURCES = ["ara_api.cu", "fold.cu", "ylt.cu", "select.cu", "validate.cu", "noalloc.cu", "service.cu", "yelt.cu", "plan.cu", "ingest.cu", "compact.cu", "tail.cu", "probe.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
@@ -36,13 +37,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     objdir = os.path.join(PKG, "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
-    for src in SOURCES:
-        obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, "-Xptxas", "-v" if verbose else "-O3", "-c",
-               os.path.join(CSRC, src), "-o", obj]
-        subprocess.check_call(cmd)
-        objs.append(obj)
+    objs = [os.path.join(objdir, src.replace(".cu", ".o")) for src in SOURCES]
+
+    def compile_one(src_obj):
+        src, obj = src_obj
+        subprocess.check_call([NVCC, *ARCH, *FLAGS, "-Xptxas", "-v" if verbose else "-O3", "-c",
+                               os.path.join(CSRC, src), "-o", obj])
+
+    # the translation units are independent: compile them side by side
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        list(ex.map(compile_one, zip(SOURCES, objs)))
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt",
                            "-lpthread", "-ldl"])

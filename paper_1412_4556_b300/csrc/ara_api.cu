@@ -18,7 +18,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <numeric>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -68,6 +70,30 @@ bool is_device_ptr(const void *p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device memory of a GPU other than the current one.  Every entry point makes
+// the context's device current before it looks at pointers, so such an array
+// belongs to another GPU: it is not a host array (a host-to-device copy from
+// it fails) and this device's kernels cannot read it (unmapped peer memory
+// would fault), so the entry points reject it with ARA_E_INVALID_ARG.
+bool foreign_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  int dev = -1;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device != dev;
+}
+
+ara_status reject_foreign(ara_ctx *c, std::initializer_list<std::pair<const void *, const char *>> ptrs) {
+  for (const auto &pn : ptrs)
+    if (foreign_device_ptr(pn.first))
+      return fail(c, ARA_E_INVALID_ARG, "%s is memory of another GPU than the context's (device %d)", pn.second,
+                  c->device);
+  return ARA_OK;
 }
 
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
@@ -605,6 +631,7 @@ ara_status ara_load_yet(ara_ctx *c, int32_t catalog, int64_t n_trials, const int
                         const int32_t *ids, const float *ts) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{offsets, "trial_offsets"}, {ids, "event_ids"}, {ts, "timestamps"}})) return st_ptr;
   if (catalog < 1) return fail(c, ARA_E_INVALID_ARG, "catalog_size must be >= 1 (got %d)", catalog);
   if (n_trials < 0 || n_trials > (int64_t)1 << 40)
     return fail(c, ARA_E_INVALID_ARG, "n_trials out of range (got %lld)", (long long)n_trials);
@@ -945,6 +972,7 @@ ara_status ara_release_layer(ara_ctx *c, int32_t layer) {
 ara_status ara_layer_event_table(ara_ctx *c, int32_t layer, double *out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{out, "out"}})) return st_ptr;
   LayerRec *L = nullptr;
   ara_status st = get_layer(c, layer, &L);
   if (st) return st;
@@ -971,6 +999,7 @@ ara_status ara_layer_ylt(ara_ctx *c, int32_t layer, int64_t n_trials, double *yl
                          void *cuda_stream) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{ylt_out, "ylt_out"}})) return st_ptr;
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
   LayerRec *L = nullptr;
   ara_status st = get_layer(c, layer, &L);
@@ -1074,6 +1103,7 @@ ara_status ara_pml_tvar(ara_ctx *c, const double *ylt, int64_t n, const double *
                         double *pml_out, double *tvar_out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{ylt, "ylt"}})) return st_ptr;
   if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
   if (!pml_out || !tvar_out) return fail(c, ARA_E_INVALID_ARG, "NULL output array");
   int64_t k[kMaxReturnPeriods];
@@ -1107,6 +1137,7 @@ ara_status ara_pml_tvar_async(ara_ctx *c, const double *ylt, int64_t n, const do
                               double *out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{ylt, "ylt"}, {out, "out"}})) return st_ptr;
   if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
   if (!out) return fail(c, ARA_E_INVALID_ARG, "NULL output array");
   if (!is_device_ptr(ylt) || !is_device_ptr(out))
@@ -1127,6 +1158,7 @@ ara_status ara_pml_tvar_async(ara_ctx *c, const double *ylt, int64_t n, const do
 ara_status ara_ylt_tail(ara_ctx *c, const double *ylt, int64_t n, int64_t k, double *tail_out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{ylt, "ylt"}, {tail_out, "tail_out"}})) return st_ptr;
   if (n < 1 || !ylt) return fail(c, ARA_E_INVALID_ARG, "need n >= 1 trial losses");
   if (k < 1 || k > n) return fail(c, ARA_E_INVALID_ARG, "k = %lld outside [1, %lld]", (long long)k, (long long)n);
   if (!tail_out) return fail(c, ARA_E_INVALID_ARG, "tail_out is NULL");
@@ -1158,6 +1190,7 @@ ara_status ara_pml_tvar_tail(ara_ctx *c, const double *tail, int64_t m, int64_t 
                              int32_t n_rp, double *pml_out, double *tvar_out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{tail, "tail"}})) return st_ptr;
   if (m < 1 || !tail) return fail(c, ARA_E_INVALID_ARG, "need m >= 1 tail values");
   if (n_total < m) return fail(c, ARA_E_INVALID_ARG, "n_total %lld < m %lld", (long long)n_total, (long long)m);
   if (!pml_out || !tvar_out) return fail(c, ARA_E_INVALID_ARG, "NULL output array");
@@ -1171,6 +1204,7 @@ ara_status ara_layers_ylt(ara_ctx *c, int32_t n_layers, const int32_t *layers, i
                           double *ylt_out, void *cuda_stream) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{ylt_out, "ylt_out"}})) return st_ptr;
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
   if (n_layers < 1 || !layers) return fail(c, ARA_E_INVALID_ARG, "need n_layers >= 1 layer handles");
   if (n_trials < 0 || n_trials > c->n_trials)
@@ -1210,6 +1244,7 @@ ara_status ara_layer_yelt(ara_ctx *c, int32_t layer, int64_t n_trials, double *y
                           double *occ_max_out, void *cuda_stream) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{yelt_out, "yelt_out"}, {occ_max_out, "occ_max_out"}})) return st_ptr;
   if (!c->yet_loaded) return fail(c, ARA_E_STATE, "no YET loaded");
   LayerRec *L = nullptr;
   ara_status st = get_layer(c, layer, &L);
@@ -1326,6 +1361,7 @@ ara_status ara_pml_tvar_batch(ara_ctx *c, const double *ylt, int32_t n_layers, i
                               const double *rps, int32_t n_rp, double *pml_out, double *tvar_out) {
   ARA_ENTER(c);
   ARA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (ara_status st_ptr = reject_foreign(c, {{ylt, "ylt"}})) return st_ptr;
   if (n < 1 || !ylt || n_layers < 1) return fail(c, ARA_E_INVALID_ARG, "need n_layers >= 1 and n >= 1 trial losses");
   if (n_layers > 65535) return fail(c, ARA_E_INVALID_ARG, "at most 65535 layers per call");
   if (n_rp < 1 || n_rp > kMaxReturnPeriods || !rps || !pml_out || !tvar_out)

@@ -4,7 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <initializer_list>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ara.h"
@@ -177,6 +179,9 @@ ara_status cuda_fail(ara_ctx *c, cudaError_t e, const char *what);
   } while (0)
 
 bool is_device_ptr(const void *p);
+// ARA_E_INVALID_ARG (message naming the argument) when one of the pointers is
+// device memory of a GPU other than the current one (the context's).
+ara_status reject_foreign(ara_ctx *c, std::initializer_list<std::pair<const void *, const char *>> ptrs);
 
 template <typename T>
 cudaError_t ensure(T **buf, size_t *cap, size_t count) {

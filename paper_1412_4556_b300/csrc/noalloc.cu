@@ -79,12 +79,25 @@ extern "C" ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const d
              (int)n_rp, ara::kMaxReturnPeriods);
     return noalloc_fail(ARA_E_INVALID_ARG, msg);
   }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return noalloc_fail(ARA_E_CUDA, "ara_pml_tvar_noalloc: no current CUDA device");
+  }
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, ylt) != cudaSuccess ||
       (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
     cudaGetLastError();
     return noalloc_fail(ARA_E_INVALID_ARG,
                         "ara_pml_tvar_noalloc: ylt must be device memory (a host copy would need a buffer)");
+  }
+  // The selection kernels run on the current device and read ylt directly:
+  // another GPU's memory is not readable there, so it is refused before any
+  // launch.
+  if (attr.type == cudaMemoryTypeDevice && attr.device != dev) {
+    snprintf(msg, sizeof(msg),
+             "ara_pml_tvar_noalloc: ylt is memory of device %d but the current device is %d", attr.device, dev);
+    return noalloc_fail(ARA_E_INVALID_ARG, msg);
   }
   int64_t k[ara::kMaxReturnPeriods];
   for (int32_t r = 0; r < n_rp; ++r) {
@@ -98,8 +111,6 @@ extern "C" ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const d
   unsigned char *scratch = nullptr;
   ara_status st = scratch_for_current_device(&scratch);
   if (st != ARA_OK) return st;
-  int dev = 0;
-  cudaGetDevice(&dev);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double *d_out = reinterpret_cast<double *>(scratch + kOutOffset);
   unsigned int *d_err = reinterpret_cast<unsigned int *>(scratch + kErrOffset);

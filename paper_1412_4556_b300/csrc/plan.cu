@@ -285,6 +285,7 @@ ara_status ara_plan_run(ara_plan *p, double *ylt_out, double *pml_out, double *t
     if (h >= (int32_t)c->layers.size() || !c->layers[(size_t)h].live || c->layers[(size_t)h].gen != p->gens[i])
       return fail(c, ARA_E_STATE, "layer %d was released or redefined after the plan was made", h);
   }
+  if (ara_status st = reject_foreign(c, {{ylt_out, "ylt_out"}})) return st;
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
   ARA_CUDA(c, cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
   const size_t total = p->layers.size() * (size_t)p->n_trials;

@@ -1,13 +1,11 @@
 """Batched layers (several layers in one pass over the YET) against the
 single-layer path and the oracle, and batched PML/TVaR."""
-import math
-
 import numpy as np
 import pytest
 
 import ara_synth as S
 import oracle
-from parity import FP64_REL_TOL, assert_fp64_parity
+from parity import assert_fp64_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -75,28 +73,3 @@ def test_batched_rejects_bad_handles(engine):
     assert ei.value.name == "ARA_E_NOT_FOUND"
     with pytest.raises(AraError):
         engine.layers_ylt(hs, n_trials=101)
-
-
-def test_batched_64_layers_full_size_sampled():
-    """64 layers over the paper-scale YET (1,000,000 trials x Poisson(1000));
-    the oracle (memoised Algorithm 1) checks sampled trials of sampled layers."""
-    from paper_1412_4556_b300 import Engine
-    w = S.batched()
-    with Engine(0) as e:
-        e.load_yet_from(w.yet)
-        hs = define_all(e, w)
-        y = e.layers_ylt(hs)
-        pml, tvar = e.pml_tvar_batch(y, w.return_periods)
-    assert y.shape == (64, 1_000_000)
-    rng = np.random.default_rng(3)
-    for li in rng.choice(64, 6, replace=False):
-        lay = w.layers[li]
-        assert np.all(y[li] >= 0) and np.all(y[li] <= lay.agg_lim)
-        sel = np.sort(rng.choice(w.yet.n_trials, 300, replace=False))
-        o, pre = oracle.layer_ylt(w.yet, w.pool, lay, trials=sel, mode="memo")
-        assert_fp64_parity(y[li][sel], o, pre, what=f"layer {li}")
-        s = np.sort(y[li])[::-1]
-        for r, p, t in zip(w.return_periods, pml[li], tvar[li]):
-            k = int(math.floor(y.shape[1] / r))
-            assert p == s[k - 1]
-            assert t == pytest.approx(math.fsum(s[:k]) / k, rel=1e-13)

@@ -96,28 +96,3 @@ def test_fp32_layers_four_per_pass(engine, n_layers):
     rev = engine.layers_ylt(hs[::-1], n_trials=777)
     for i, h in enumerate(hs[::-1]):
         np.testing.assert_array_equal(rev[i], batch[hs.index(h)][:777])
-
-
-def test_fp32_64_layers_full_size_sampled():
-    """Config 3 at full size: the 64 batched layers over the paper-scale YET as
-    FP32 tables, in the plan (graph) the benchmark times; sampled trials of
-    sampled layers against the FP64 oracle at 1e-5 (1 USD floor)."""
-    from paper_1412_4556_b300 import ARA_FP32_TABLE, Engine, Plan
-    w = S.batched()
-    with Engine(0) as e:
-        e.load_yet_from(w.yet)
-        first = e.load_pool(w.pool)
-        hs = [e.define_layer([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim,
-                             precision=ARA_FP32_TABLE) for L in w.layers]
-        y = np.empty((64, w.yet.n_trials))
-        with Plan(e, hs, w.return_periods) as plan:
-            pml, tvar = plan.run(ylt_out=y)
-    rng = np.random.default_rng(5)
-    for li in rng.choice(64, 5, replace=False):
-        lay = w.layers[li]
-        sel = np.sort(rng.choice(w.yet.n_trials, 300, replace=False))
-        o, pre = oracle.layer_ylt(w.yet, w.pool, lay, trials=sel, mode="memo")
-        assert_reduced_parity(y[li][sel], o, pre, what=f"layer {li}")
-        s = np.sort(y[li])[::-1]
-        for r, p in zip(w.return_periods, pml[li]):
-            assert p == s[int(y.shape[1] // r) - 1]

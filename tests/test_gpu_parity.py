@@ -1,13 +1,12 @@
 """CUDA engine vs the FP64 oracle, element by element, through the C ABI."""
 import math
-import os
 
 import numpy as np
 import pytest
 
 import ara_synth as S
 import oracle
-from parity import FP64_REL_TOL, assert_fp64_parity, load_workload, r9_rel_error
+from parity import FP64_REL_TOL, assert_fp64_parity, load_workload
 from test_oracle import hand_instance
 
 pytestmark = pytest.mark.gpu
@@ -73,10 +72,16 @@ def test_paper_shaped_workload_20k_trials(engine):
     o, pre = oracle.layer_ylt(w.yet, w.pool, layer, mode="memo")
     g = engine.layer_ylt(L)
     assert_fp64_parity(g, o, pre)
-    pml_o, tvar_o = oracle.pml_tvar(o, w.return_periods[:2])
-    pml_g, tvar_g = engine.pml_tvar(o, w.return_periods[:2])
+    # every return period of the workload (k = 200, 80, 40 of 20,000)
+    pml_o, tvar_o = oracle.pml_tvar(o, w.return_periods)
+    pml_g, tvar_g = engine.pml_tvar(o, w.return_periods)
     np.testing.assert_array_equal(pml_g, pml_o)
     np.testing.assert_allclose(tvar_g, tvar_o, rtol=1e-13, atol=0)
+    # and from the engine's own YLT, within the largest per-trial error
+    pml_e, tvar_e = engine.pml_tvar(g, w.return_periods)
+    pt = oracle.compare_pml_tvar(pml_e, tvar_e, pml_o, tvar_o, w.return_periods, g.size,
+                                 float(np.max(np.abs(g - o))))
+    assert pt["within_bound"], pt
 
 
 # -------------------------------------------------------------- edge cases
@@ -263,42 +268,8 @@ def test_invalid_inputs_are_rejected_with_status(engine):
     assert engine.layer_ylt(L).shape == (1,)
 
 
-# ------------------------------------------------- full paper-scale workload
-@pytest.fixture(scope="module")
-def paper_full():
-    return S.paper_scale()
-
-
-def test_paper_scale_full_size_sampled(paper_full):
-    """1,000,000 trials x Poisson(1000) events (~1e9 occurrences), 16 ELTs, in
-    the launch configuration the benchmark times (compact id stream; the
-    stored layout gives the same bits); the oracle checks a sample of trials
-    one by one, plus properties that hold at any size."""
-    from paper_1412_4556_b300 import Engine
-    w = paper_full
-    layer = w.layers[0]
-    with Engine(0) as e:
-        (L,) = load_workload(e, w)
-        stored = e.layer_ylt(L)
-        e.compact_yet()  # the benchmark prices from the compact id stream
-        g = e.layer_ylt(L)
-        pml_g, tvar_g = e.pml_tvar(g, w.return_periods)
-    np.testing.assert_array_equal(g.view(np.uint64), stored.view(np.uint64))
-    assert g.shape == (1_000_000,)
-    assert np.all(g >= 0) and np.all(g <= layer.agg_lim)
-    counts = np.diff(w.yet.offsets)
-    rng = np.random.default_rng(1)
-    sel = np.unique(np.concatenate([rng.choice(g.size, 1500, replace=False),
-                                    [0, g.size - 1, int(np.argmax(counts)), int(np.argmin(counts))],
-                                    np.argsort(g)[-50:]]))
-    o, pre = oracle.layer_ylt(w.yet, w.pool, layer, trials=sel, mode="memo")
-    assert_fp64_parity(g[sel], o, pre)
-    # PML/TVaR of the engine's YLT are the order statistics of that YLT
-    s = np.sort(g)[::-1]
-    for r, p, t in zip(w.return_periods, pml_g, tvar_g):
-        k = int(math.floor(g.size / r))
-        assert p == s[k - 1]
-        assert t == pytest.approx(math.fsum(s[:k]) / k, rel=1e-13)
+# The full paper-scale workload (every trial against the oracle) is in
+# test_gpu_fullsize.py.
 
 
 @pytest.mark.parametrize("catalog", [(1 << 21) - 1, 1 << 21])

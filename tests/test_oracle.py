@@ -190,6 +190,49 @@ def test_trial_subset_matches_full_run():
     np.testing.assert_array_equal(sub, full[sel])
 
 
+def test_many_layer_call_equals_one_call_per_layer():
+    """The many-layer entry (the YET checked once, each layer's memo built on
+    several threads) gives each layer the bits of its own call, whatever the
+    thread count, with the hand-worked layer among them."""
+    yet, pool, layer = _random_instance(4, catalog=70_000, n_trials=200)
+    other = Layer([2, 0], 100.0, 1e4, 0.0, 5e4)
+    g, hy, hp, hl = hand_instance()
+    layers = [layer, other, Layer([1], 0.0, math.inf, 0.0, math.inf)]
+    y, p = oracle.layers_ylt(yet, pool, layers, threads=5)
+    assert y.shape == (3, yet.n_trials)
+    for i, L in enumerate(layers):
+        a, pa = oracle.layer_ylt(yet, pool, L, mode="literal", threads=2)
+        np.testing.assert_array_equal(y[i].view(np.uint64), a.view(np.uint64))
+        np.testing.assert_array_equal(p[i].view(np.uint64), pa.view(np.uint64))
+    sel = np.array([5, 1, 199], np.int64)
+    ys, _ = oracle.layers_ylt(yet, pool, layers, trials=sel, mode="literal", threads=1)
+    np.testing.assert_array_equal(ys, y[:, sel])
+    hy_out, _ = oracle.layers_ylt(hy, hp, [hl, hl])
+    assert hy_out[0].tolist() == g["ylt"] and hy_out[1].tolist() == g["ylt"]
+
+
+def test_comparison_forms():
+    """The R9 gate divides by max(|o|, S_o); the plain form by |o|; the
+    reduced-precision gate is max(1e-5 max(|o|, S_o), 1 USD)."""
+    o = np.array([0.0, 1.0, 100.0, 0.0])
+    pre = np.array([0.0, 1e6, 100.0, 5.0])
+    g = np.array([0.0, 1.0 + 1e-7, 100.0, 1e-12])
+    r = oracle.compare_fp64(g, o, pre)
+    assert r["trials_over_r9_bar"] == 0             # 1e-7 / 1e6 and 1e-12 / 5 pass the gate
+    assert r["trials_over_plain_bar"] == 2          # 1e-7 / 1 and 1e-12 / 0 fail the plain form
+    assert r["bitwise_equal_trials"] == 2
+    r = oracle.compare_fp64(np.array([1.0]), np.array([0.0]), np.array([0.0]))
+    assert r["trials_over_r9_bar"] == 1             # a loss where the oracle has no sum at all
+    q = oracle.compare_reduced(np.array([0.5, 1e6 + 20.0, 3.0]), np.array([0.0, 1e6, 0.0]),
+                               np.array([0.0, 1e6, 4e6]))
+    assert q["trials_over_bar"] == 1                # 20 USD > 1e-5 * 1e6; 3 USD <= 1e-5 * 4e6
+    assert q["trials_over_plain_bar"] == 2
+    pt = oracle.compare_pml_tvar([10.0], [12.0], [10.5], [12.0], [100.0], 1000, 0.5)
+    assert pt["within_bound"]
+    pt = oracle.compare_pml_tvar([10.0], [12.0], [10.6], [12.0], [100.0], 1000, 0.5)
+    assert not pt["within_bound"]
+
+
 def test_closed_form_repeated_event():
     """A trial that repeats one event n times: loss = clamp(n*c - AggR, 0, AggL),
     with c the event's occurrence-net loss (integers, so exact)."""

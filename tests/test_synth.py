@@ -22,6 +22,10 @@ def test_yet_layout():
     for t in range(0, 2_000, 97):
         seg = y.ts[y.offsets[t]:y.offsets[t + 1]]
         assert np.all(np.diff(seg) >= 0) and (seg.size == 0 or (seg[0] >= 0 and seg[-1] < 365))
+    # uniform over the year: mean 182.5, each month-sized bin about 1/12
+    assert abs(float(y.ts.mean()) - 182.5) < 1.0
+    h, _ = np.histogram(y.ts, bins=12, range=(0.0, 365.0))
+    assert np.all(np.abs(h / h.sum() - 1.0 / 12.0) < 0.005)
 
 
 def test_elt_pool_distinct_ids_and_terms():
