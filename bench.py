@@ -3,28 +3,37 @@
 
 One step = one pass of the whole path over the paper-scale workload
 (catalog 2,000,000 events; one layer over 16 ELTs of 20,000 events;
-1,000,000 trials of Poisson(1000) events, about 1e9 occurrences):
+1,000,000 trials of Poisson(1000) events, about 1e9 occurrences, each an
+int32 event id and a float32 time-stamp):
 
     ara_define_layer  (per-layer ELT fold pre-pass on the device)
     ara_layer_ylt     (per-trial gather + exact sum + aggregate terms)
     ara_pml_tvar      (PML and TVaR at return periods 100 / 250 / 500)
 
 The YET and the ELT pool are resident in HBM when the timed region starts
-(the paper's pre-processing stage); the 4 GB id stream is larger than L2, so
-every step reads it from HBM.  ``e2e`` repeats the step through the same C
-ABI with host buffers: the YET, the ELTs and the layer go host->device and
-the YLT, PML and TVaR come back, inside the timed region.
+(the paper's pre-processing stage); the id stream is larger than L2, so every
+step reads it from HBM.  ``e2e`` repeats the step through the same C ABI with
+host buffers: the YET (ids and time-stamps), the ELTs and the layer go
+host->device and the YLT, PML and TVaR come back, inside the timed region.
+
+The default line also carries, each with its own clock record:
+  parity    every trial's loss and PML/TVaR against the FP64 oracle;
+  batched   64 FP64 layers over the same YET priced as one CUDA graph
+            (speed-up over the plain per-layer path, error against the oracle);
+  mixed     the same 64 layers with FP32 tables;
+  service   a seeded stream of layer-pricing requests at 50/s (p50/p99).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
 
 Under torchrun (N > 1) every rank prices its own shard of 1,000,000 trials
-(weak scaling); the shards' YLTs are all-gathered for the portfolio-wide
-PML/TVaR.  ``--impl reference`` times the FP64 CPU oracle (the only reference
-this path has) on a bounded sample of the same workload.
+(weak scaling); each shard's largest losses are all-gathered for the
+portfolio-wide PML/TVaR.  ``--impl reference`` times the FP64 CPU oracle (the
+only reference this path has) on the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures
 import json
 import math
 import os
@@ -48,7 +57,18 @@ UNIT = "trial-events/s"
 PAPER_1GPU_TRIAL_EVENTS_PER_S = 1e9 / 19.93  # Tesla M2050, Section IV-C (context only)
 WORKLOAD = ("paper-scale plain ARA, FP64: catalog 2,000,000 events; 1 layer over 16 ELTs x 20,000 "
             "events (lognormal(12,1.5) losses, D~U[5e3,5e4], Lim~U[1e6,1e7]); 1,000,000 trials x "
-            "Poisson(1000) events; OccR 1e5, OccL 2e7, AggR 5e5, AggL 1e8; RP 100/250/500")
+            "Poisson(1000) events (int32 ids + float32 time-stamps); OccR 1e5, OccL 2e7, AggR 5e5, "
+            "AggL 1e8; RP 100/250/500")
+
+
+def paper_config(N: int, M: int, C: int, elts: int, world: int, k_tail: int = 0) -> dict:
+    """The workload's config dict, the same for the engine and reference arms."""
+    return {"workload": WORKLOAD, "n_trials_per_gpu": N, "occurrences_per_gpu": M, "catalog": C,
+            "elts": elts, "return_periods": [100, 250, 500],
+            "l2": "inputs larger than L2: the 2-4 GB YET id stream is re-read from HBM every step",
+            "parallelism": (f"trial shards x{world}; each rank sends its {k_tail} largest trial losses "
+                            "(ara_ylt_tail, NCCL all-gather) and rank 0 prices the union "
+                            "(ara_pml_tvar_tail)") if world > 1 else "1 GPU"}
 
 
 def compact(eng, args):
@@ -60,6 +80,12 @@ def compact(eng, args):
     t = time.perf_counter()
     eng.compact_yet()
     return (time.perf_counter() - t) * 1e3
+
+
+def yet_layout(compact_ms):
+    return ("stored order, 6 packed ids per 16 bytes" if compact_ms is None else
+            "ara_compact_yet: 8 difference-coded ids per 16 bytes, each group of 8 ascending (prepared once "
+            "before timing, %.1f ms)" % compact_ms)
 
 
 # ------------------------------------------------------------ distributed
@@ -199,6 +225,50 @@ def ncu_traffic_per_launch(occurrences: int, profile: str = "ylt_fp64_kernel_pap
     return float(b.group(1)) * occurrences
 
 
+def measure_ceilings(device: int) -> dict:
+    """Rates the YLT kernel's inner loop is built from, measured on this GPU
+    (ara_probe_*): random reads of one row from an L2-resident table (16-byte
+    rows from a 32 MB table: one FP64 layer; 32-byte rows from a 64 MB table:
+    a pass over two FP64 or four FP32-table layers), random shared-memory
+    lookups (the zero-skip bitmap test) and binary64 adds."""
+    from paper_1412_4556_b300 import _native as nat
+    mb = 1 << 20
+    r16, _ = nat.ara_probe_gather(device, 32 * mb, 16, 1, 1024, 1)
+    r32, _ = nat.ara_probe_gather(device, 64 * mb, 32, 1, 1024, 1)
+    return {"gather16_rows_per_s": r16, "gather32_rows_per_s": r32,
+            "smem_lookups_per_s": nat.ara_probe_smem_lookup(device),
+            "fp64_adds_per_s": nat.ara_probe_fp64_add(device),
+            "how": "ara_probe_gather (1024-thread CTAs, one per SM, 4 rows in flight per lane, evict-last), "
+                   "ara_probe_smem_lookup, ara_probe_fp64_add: best of 5 launches"}
+
+
+def l1tex_roofline(gathers: float, lookups: float, kernel_ms: float, rows_per_s: float, ceil: dict) -> dict:
+    """The kernel against its L1TEX co-bound: each occurrence takes one random
+    shared-memory lookup and each nonzero one a random L2 row read; both go
+    through the SM's L1TEX pipe, so their measured times add up to a floor."""
+    t_g = gathers / rows_per_s
+    t_l = lookups / ceil["smem_lookups_per_s"]
+    floor_ms = (t_g + t_l) * 1e3
+    return {"bound": "l1tex", "unit": "ms", "kernel_ms": kernel_ms, "floor_ms": floor_ms,
+            "frac": floor_ms / kernel_ms,
+            "gathers_per_launch": gathers, "lookups_per_launch": lookups,
+            "achieved_gathers_per_s": gathers / (kernel_ms / 1e3), "peak_gathers_per_s": rows_per_s,
+            "achieved_lookups_per_s": lookups / (kernel_ms / 1e3), "peak_lookups_per_s": ceil["smem_lookups_per_s"],
+            "note": "floor = algorithmic gathers (occurrences whose event has a nonzero table value) / measured "
+                    "random L2 row rate + occurrences / measured random shared-memory lookup rate; the two share "
+                    "the L1TEX pipe"}
+
+
+def event_counts(ids: np.ndarray, catalog: int, threads: int = 16) -> np.ndarray:
+    """Occurrences of every catalog event (threaded bincount)."""
+    n = ids.size
+    k = max(1, threads)
+    parts = [(i * n // k, (i + 1) * n // k) for i in range(k)]
+    with concurrent.futures.ThreadPoolExecutor(k) as ex:
+        cs = list(ex.map(lambda p: np.bincount(ids[p[0]:p[1]], minlength=catalog), parts))
+    return np.sum(cs, axis=0)
+
+
 # ------------------------------------------------------------ CPU oracle
 def sample_yet(yet, sel):
     """A YET of the trials sel (ascending indices) of yet, in CSR form."""
@@ -214,7 +284,8 @@ def _time_oracle(w, sel, threads):
     their occurrence count.  A sample of a tenth of the trials or less is
     priced as a YET of its own (built before the clock starts), so the
     oracle's per-call pass over its input covers the sample, not the whole
-    YET; a larger one goes through the oracle's trial selection."""
+    YET; a larger one goes through the oracle's trial selection, and all the
+    trials go through no selection at all."""
     import oracle
     layer = w.layers[0]
     occ = int((w.yet.offsets[sel + 1] - w.yet.offsets[sel]).sum())
@@ -222,6 +293,9 @@ def _time_oracle(w, sel, threads):
         y = sample_yet(w.yet, sel)
         t0 = time.perf_counter()
         oracle.layer_ylt(y, w.pool, layer, mode="literal", threads=threads)
+    elif sel.size == w.yet.n_trials:
+        t0 = time.perf_counter()
+        oracle.layer_ylt(w.yet, w.pool, layer, mode="literal", threads=threads)
     else:
         t0 = time.perf_counter()
         oracle.layer_ylt(w.yet, w.pool, layer, trials=sel, mode="literal", threads=threads)
@@ -244,18 +318,35 @@ def oracle_cost_model(w, threads, rng):
 
 def oracle_sample(w, budget_s: float = 12.0, threads=None, model=None, rng=None):
     """Time the FP64 oracle (literal Algorithm 1) on a bounded trial sample
-    sized to about budget_s seconds."""
+    sized to about budget_s seconds (all the trials when they fit)."""
     threads = threads or os.cpu_count() or 1
     rng = rng or np.random.default_rng(5)
     n = w.yet.n_trials
     fixed, per_trial = model or oracle_cost_model(w, threads, rng)
     k = int(min(n, max(256, (budget_s - fixed) / per_trial)))
-    sel = np.sort(rng.choice(n, k, replace=False))
+    sel = np.arange(n) if k == n else np.sort(rng.choice(n, k, replace=False))
     dt, occ = _time_oracle(w, sel, threads)
-    return {"value": occ / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": occ / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "seconds": dt,
+            "trials": k, "occurrences": occ,
             "sample": f"{k} of {n} trials ({occ} trial-events), literal Algorithm 1 "
                       f"(16 direct-access-table lookups per event), {dt:.2f} s including the "
                       f"table build"}
+
+
+def oracle_parity(w, g, pml_g, tvar_g) -> dict:
+    """Every trial loss g (and PML/TVaR from g) against the FP64 oracle
+    (memoised Algorithm 1 on all host cores, same bits as the literal loop)."""
+    import oracle
+    t = time.perf_counter()
+    o, pre = oracle.layer_ylt(w.yet, w.pool, w.layers[0], mode="memo")
+    pml_o, tvar_o = oracle.pml_tvar(o, w.return_periods)
+    rep = oracle.compare_fp64(g, o, pre)
+    rep["pml_tvar"] = oracle.compare_pml_tvar(pml_g, tvar_g, pml_o, tvar_o, w.return_periods, g.size,
+                                              rep["max_abs_err"])
+    rep["gate"] = "|g - o| / max(|o|, S_o) <= 1e-12 per trial (S_o: the oracle's pre-aggregate sum)"
+    rep["plain_form"] = "|g - o| / |o| <= 1e-12 (reported, not gated)"
+    rep["oracle_seconds"] = time.perf_counter() - t
+    return rep
 
 
 # --------------------------------------------------------------- engine arm
@@ -271,7 +362,8 @@ def run_engine(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    w = S.paper_scale(seed=shard_seed(S.DEFAULT_SEED, rank), n_trials=args.trials)
+    w = S.paper_scale(seed=shard_seed(S.DEFAULT_SEED, rank), n_trials=args.trials,
+                      with_timestamps=not args.no_timestamps)
     layer = w.layers[0]
     rps = w.return_periods
     M, N, C = w.yet.n_occurrences, w.yet.n_trials, w.yet.catalog_size
@@ -286,6 +378,7 @@ def run_engine(args):
     # PML then TVaR of the latest step, written in stream order (one GPU)
     res_dev = torch.empty(2 * len(rps), dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
+    ceil = measure_ceilings(local)
 
     gather_buf = tail_dev = None
     k_tail = tail_size(N, world, rps)
@@ -358,8 +451,20 @@ def run_engine(args):
     peak, peak_kind = measured_hbm_peak()
     traffic = ncu_traffic_per_launch(M)
 
+    # The last step's YLT, for the parity check and the L1TEX co-bound (its
+    # table's nonzero events and their occurrences).
+    g = ylt_dev.cpu().numpy()
+    L = eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
+    nonzero = eng.event_table(L) != 0.0
+    eng.release_layer(L)
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+    gathers = float(event_counts(w.yet.ids, C)[nonzero].sum())
+    l1tex = l1tex_roofline(gathers, float(M), ylt_avg_ms, ceil["gather16_rows_per_s"], ceil)
+
     # End to end through the C ABI with host buffers (pinned), per step.
-    e2e = run_e2e(args, w, handles_count=len(layer.elts), local=local) if rank == 0 else None
+    e2e = run_e2e(args, w, local=local) if rank == 0 else None
 
     if world > 1:
         import torch.distributed as dist
@@ -369,7 +474,18 @@ def run_engine(args):
             import torch.distributed as dist
             dist.destroy_process_group()
         return
+    parity = oracle_parity(w, g, res[0], res[1]) if world == 1 and not args.no_parity else None
+    nested = {}
+    if world == 1 and not args.no_nested:
+        bw = S.batched(yet=w.yet)
+        nested["batched"] = batched_result(args, bw, mixed=False, ceil=ceil)
+        nested["mixed"] = batched_result(args, bw, mixed=True, ceil=ceil)
+        del bw
+        nested["service"] = service_result(args, S.batched(n_layers=1, yet=w.yet), nested=True)
     cpu = oracle_sample(w, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
+    if cpu:
+        for key in ("seconds", "trials", "occurrences"):
+            cpu.pop(key, None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -378,28 +494,23 @@ def run_engine(args):
         "vs_baseline_basis": "paper's best single GPU run (Tesla M2050, 19.93 s for 1e9 trial-events, "
                              "Section IV-C); other hardware, context only",
         "dtype": "f64", "data": "synthetic (seeded; stands in for the paper's proprietary industry data)",
-        "config": {"workload": WORKLOAD, "n_trials_per_gpu": N, "occurrences_per_gpu": M,
-                   "catalog": C, "elts": len(layer.elts),
-                   "step": ("ara_define_layer (ELT fold) + ara_layer_ylt + ara_pml_tvar_async (PML/TVaR "
-                            "queued, results kept in HBM; read back after the timed steps)") if world == 1 else
-                           "ara_define_layer (ELT fold) + ara_layer_ylt + ara_ylt_tail + all-gather + "
-                           "ara_pml_tvar_tail",
-                   "yet_layout": ("stored order, 6 packed ids per 16 bytes" if compact_ms is None else
-                                  "ara_compact_yet: 8 difference-coded ids per 16 bytes, each group of 8 ascending (prepared once "
-                                  "before timing, %.1f ms)" % compact_ms),
-                   "l2": "inputs larger than L2: the 2-2.7 GB chunked YET id stream is re-read from HBM every step",
-                   "parallelism": (f"trial shards x{world}; each rank sends its {k_tail} largest trial losses "
-                                   "(ara_ylt_tail, NCCL all-gather) and rank 0 prices the union "
-                                   "(ara_pml_tvar_tail)") if world > 1 else "1 GPU"},
+        "config": paper_config(N, M, C, len(layer.elts), world, k_tail),
+        "step": ("ara_define_layer (ELT fold) + ara_layer_ylt + ara_pml_tvar_async (PML/TVaR queued, results "
+                 "kept in HBM; read back after the timed steps)") if world == 1 else
+                "ara_define_layer (ELT fold) + ara_layer_ylt + ara_ylt_tail + all-gather + ara_pml_tvar_tail",
+        "yet_layout": yet_layout(compact_ms),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "ylt_fp64_kernel", "kernel_ms": ylt_avg_ms,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "frac_of_nominal_8000_gbs": achieved / 8000.0},
+                     "frac_of_nominal_8000_gbs": achieved / 8000.0,
+                     "l1tex": l1tex},
+        "ceilings": ceil,
         "breakdown_ms_per_step": {"fold": fold_ms / max(args.steps, 1), "ylt": ylt_ms / max(args.steps, 1),
                                   "pml_tvar": pml_ms / max(args.steps, 1)},
         "pml": list(map(float, res[0])), "tvar": list(map(float, res[1])),
+        "parity": parity,
         "clocks": clocks.summary(),
         "e2e": e2e,
         # fold, YLT, selection (init + 8 passes + sum) and, on one GPU, the
@@ -408,15 +519,18 @@ def run_engine(args):
         "gpu_launches": args.steps * (1 + 1 + 10 + (13 if world > 1 else 1)),
         "cpu_baseline": cpu,
     }
+    line.update(nested)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def run_e2e(args, w, handles_count: int, local: int):
+def run_e2e(args, w, local: int):
     """Same step through the public C ABI with pinned host buffers: H2D of the
-    YET and the ELTs, the layer definition, the YLT and PML/TVaR back to host."""
+    YET (ids and, when the workload has them, time-stamps, which the load
+    checks on the device) and the ELTs, the layer definition, the YLT and
+    PML/TVaR back to host.  Also timed with the ids alone."""
     import torch
     from paper_1412_4556_b300 import Engine
 
@@ -424,6 +538,7 @@ def run_e2e(args, w, handles_count: int, local: int):
     rps = w.return_periods
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     h_off, h_ids = pin(w.yet.offsets), pin(w.yet.ids)
+    h_ts = pin(w.yet.ts) if w.yet.ts is not None else None
     p = w.pool
     h_eoff, h_eids, h_eloss = pin(p.offsets), pin(p.ids), pin(p.losses)
     h_ded, h_lim = pin(p.deductibles), pin(p.limits)
@@ -431,8 +546,8 @@ def run_e2e(args, w, handles_count: int, local: int):
     eng = Engine(local)
     N, M = w.yet.n_trials, w.yet.n_occurrences
 
-    def step():
-        eng.load_yet(w.yet.catalog_size, h_off.numpy(), h_ids.numpy())
+    def step(ts):
+        eng.load_yet(w.yet.catalog_size, h_off.numpy(), h_ids.numpy(), None if ts is None else ts.numpy())
         first = eng.load_elts(h_eoff.numpy(), h_eids.numpy(), h_eloss.numpy(), h_ded.numpy(),
                               h_lim.numpy())
         L = eng.define_layer([first + j for j in layer.elts], layer.occ_ret, layer.occ_lim,
@@ -442,22 +557,29 @@ def run_e2e(args, w, handles_count: int, local: int):
         eng.release_layer(L)
         return res
 
-    for _ in range(max(1, min(args.warmup, 2))):
-        step()
-    torch.cuda.synchronize()
-    k = max(1, min(args.steps, args.e2e_steps))
-    t0 = time.perf_counter()
-    for _ in range(k):
-        step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / k
+    def timed(ts):
+        for _ in range(max(1, min(args.warmup, 2))):
+            step(ts)
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, args.e2e_steps))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            step(ts)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / k, k
+
+    dt, k = timed(h_ts)
+    dt_ids, _ = timed(None) if h_ts is not None else (dt, k)
     eng.close()
-    h2d = 8 * (N + 1) + 4 * M + 8 * (p.n_elts + 1) + 12 * p.ids.size + 16 * p.n_elts
+    h2d_ids = 8 * (N + 1) + 4 * M + 8 * (p.n_elts + 1) + 12 * p.ids.size + 16 * p.n_elts
+    h2d = h2d_ids + (4 * M if h_ts is not None else 0)
     d2h = 8 * N + 16 * len(rps)
     return {"value": M / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": dt * 1e3, "steps": k,
-            "note": "pinned host buffers through ara_load_yet/ara_load_elts/ara_define_layer/"
-                    "ara_layer_ylt(host out)/ara_pml_tvar; YET ids validated on the device each step"}
+            "ids_only": {"value": M / dt_ids, "ms_per_step": dt_ids * 1e3, "h2d_bytes_per_step": int(h2d_ids)},
+            "note": "pinned host buffers through ara_load_yet (ids and float32 time-stamps, both checked on the "
+                    "device)/ara_load_elts/ara_define_layer/ara_layer_ylt(host out)/ara_pml_tvar; ids_only: the "
+                    "same without the time-stamps"}
 
 
 # ------------------------------------------------------- batched layers
@@ -480,24 +602,21 @@ def batched_roofline(M, N, C, layers, table_bytes_per_event, ylt_ms, passes):
             "algorithmic_bytes_per_step": alg, "peak_kind": peak_kind,
             "frac_of_nominal_8000_gbs": achieved / 8000.0,
             "note": "the algorithmic minimum reads the YET once for all layers; the passes re-read it once "
-                    "per pass and gather one 32-byte sector per occurrence any of a pass's layers needs, "
-                    "which bounds them (L1TEX, not HBM)"}
+                    "per pass and are bound by their L1TEX line requests (see l1tex), not by HBM"}
 
 
-def run_batched(args):
-    """Config-2 step: define 64 layers (ELT folds), price them in pairs in one
-    call (ara_layers_ylt), PML/TVaR for all (ara_pml_tvar_batch).  Also times
-    the plain path (ara_layer_ylt once per layer) for comparison.  With
-    --workload mixed the layers use FP32 tables (config 3) and the line
-    reports their error against the FP64 path."""
+def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -> dict:
+    """Config-2 step (config 3 with mixed=True: FP32 tables): one replay of a
+    plan (a CUDA graph of the 64 ELT folds, the grouped YLT passes and the
+    batched PML/TVaR).  Also times the same work as calls (ara_layers_ylt)
+    and as the plain per-layer path (ara_layer_ylt per layer), and checks a
+    sample of trials of every layer against the FP64 oracle."""
     import torch
-    from paper_1412_4556_b300 import ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_YLT, Engine
+    import oracle
+    from paper_1412_4556_b300 import ARA_FP32_TABLE, ARA_FP64, ARA_TIMING_YLT, Engine, Plan
 
-    mixed = args.workload == "mixed"
     prec = ARA_FP32_TABLE if mixed else ARA_FP64
-
-    w = S.batched(n_trials=args.trials)
-    M, N = w.yet.n_occurrences, w.yet.n_trials
+    M, N, C = w.yet.n_occurrences, w.yet.n_trials, w.yet.catalog_size
     G = len(w.layers)
     stream = torch.cuda.Stream()
     eng = Engine(0, stream=stream)
@@ -507,6 +626,7 @@ def run_batched(args):
     handles = [[first + j for j in L.elts] for L in w.layers]
     out = torch.empty((G, N), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
+    ceil = ceil or measure_ceilings(0)
 
     def define(p=prec):
         return [eng.define_layer(h, L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim, precision=p)
@@ -520,8 +640,8 @@ def run_batched(args):
             eng.release_layer(h)
         return res
 
-    def step_plain():
-        hs = define()
+    def step_plain(p=prec):
+        hs = define(p)
         for i, h in enumerate(hs):
             eng.layer_ylt(h, out=out[i])
         res = eng.pml_tvar_batch(out, w.return_periods)
@@ -544,7 +664,6 @@ def run_batched(args):
         eng.set_kernel_timing(False)
         return e0.elapsed_time(e1) / steps, k_ms / steps
 
-    from paper_1412_4556_b300 import Plan
     plan_layers = define()
     plan = Plan(eng, plan_layers, w.return_periods, autotune=True)
 
@@ -552,75 +671,102 @@ def run_batched(args):
         # one graph launch: 64 ELT folds, the grouped YLT passes, PML/TVaR
         return plan.run(ylt_out=out, stream=stream)
 
-    steps = max(3, min(args.steps, 20))
+    steps = max(3, min(args.steps, 10))
     with ClockSampler(0) as clocks:
         clocks.wait_first_sample()
         t0 = time.monotonic()
-        ms_g, ylt_g = timed(step_plan, steps)
+        ms_g, _ = timed(step_plan, steps)
         t1 = time.monotonic()
         time.sleep(0.3)
         clocks.mark(t0, t1)
+    y_plan = out.cpu().numpy()
+    pml_plan, tvar_plan = eng.pml_tvar_batch(out, w.return_periods)
     ms_b, ylt_b = timed(step_batched, steps)
     ms_p, ylt_p = timed(step_plain, steps)
+    ms_p64 = timed(lambda: step_plain(ARA_FP64), steps)[0] if mixed else ms_p
     passes = plan.passes()
+    # nonzero events of every layer (for the passes' L1TEX floor)
+    nz = np.stack([eng.event_table(h) != 0.0 for h in plan_layers])
     plan.close()
     for h in plan_layers:
         eng.release_layer(h)
+    eng.close()
     value = G * M / (ms_g / 1e3)
-    accuracy = None
-    if mixed:
-        # Error of the FP32-table YLTs and PML/TVaR against the FP64 path (which
-        # matches the FP64 oracle within 1e-12 per trial in the parity tests).
-        h32, h64 = define(ARA_FP32_TABLE), define(ARA_FP64)
-        # pre-aggregate sums S (same layers with neutral aggregate terms): the
-        # per-trial bar is |err| <= max(1e-5 * max(|y|, S), 1 USD)
-        hpre = [eng.define_layer(h, L.occ_ret, L.occ_lim, 0.0, math.inf) for h, L in zip(handles, w.layers)]
-        y32 = eng.layers_ylt(h32)
-        y64 = eng.layers_ylt(h64)
-        s64 = eng.layers_ylt(hpre)
-        p32, t32 = eng.pml_tvar_batch(y32, w.return_periods)
-        p64, t64 = eng.pml_tvar_batch(y64, w.return_periods)
-        err = np.abs(y32 - y64)
-        scale = np.maximum(np.abs(y64), s64)
-        rel = err / np.maximum(scale, 1e-300)
-        accuracy = {"max_rel_trial_err_vs_fp64": float(rel.max()),
-                    "relative_to": "max(|y_fp64|, pre-aggregate sum S)",
-                    "max_err_over_bound(1e-5 rel, 1 USD)": float(np.max(err / np.maximum(1e-5 * scale, 1.0))),
-                    "max_abs_trial_err_usd": float(err.max()),
-                    "max_rel_pml_err": float((np.abs(p32 - p64) / np.maximum(p64, 1.0)).max()),
-                    "max_rel_tvar_err": float((np.abs(t32 - t64) / np.maximum(t64, 1.0)).max())}
-        for h in h32 + h64 + hpre:
-            eng.release_layer(h)
-    line = {
-        "metric": METRIC, "value": value, "unit": "layer-trial-events/s", "n_gpus": 1, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-        "config": {"workload": BATCHED, "layers": G, "n_trials": N, "occurrences": M,
-                   "step": "ara_plan_run: one CUDA graph of 64 ELT folds + the grouped YLT passes + "
-                           "batched PML/TVaR (launch shapes autotuned at plan creation)",
-                   "yet_layout": ("stored order, 6 packed ids per 16 bytes" if compact_ms is None else
-                                  "ara_compact_yet: 8 difference-coded ids per 16 bytes, each group of 8 ascending (prepared once "
-                                  "before timing, %.1f ms)" % compact_ms),
-                   "l2": "inputs larger than L2 (4 GB YET id stream per pass)"},
+
+    cnt = event_counts(w.yet.ids, C)
+    gathers = 0.0
+    for eb, g, _lpt, _u, _pf, pos in passes:
+        gathers += float(cnt[np.logical_or.reduce(nz[list(pos)])].sum())
+    rows = ceil["gather32_rows_per_s"] if any(g > 1 for _, g, *_ in passes) else ceil["gather16_rows_per_s"]
+    l1tex = l1tex_roofline(gathers, float(M) * len(passes), ylt_b, rows, ceil)
+    l1tex["note"] = ("floor = for every pass, the occurrences whose event is nonzero in any of the pass's "
+                     "layers / measured random 32-byte row rate (64 MB table) + its occurrences / measured "
+                     "random shared-memory lookup rate")
+
+    # a sample of trials of every layer against the FP64 oracle
+    rng = np.random.default_rng(11)
+    sel = np.sort(rng.choice(N, min(N, oracle_trials), replace=False))
+    t = time.perf_counter()
+    o, pre = oracle.layers_ylt(w.yet, w.pool, w.layers, trials=sel, mode="memo")
+    o_s = time.perf_counter() - t
+    worst = {}
+    for i in range(G):
+        rep = (oracle.compare_reduced if mixed else oracle.compare_fp64)(y_plan[i][sel], o[i], pre[i])
+        for k, v in rep.items():
+            if k == "trials":
+                worst[k] = worst.get(k, 0) + v
+            elif k.startswith("trials_over") or k == "bitwise_equal_trials":
+                worst[k] = worst.get(k, 0) + v
+            else:
+                worst[k] = max(worst.get(k, 0.0), v)
+    accuracy = {"vs": "FP64 oracle (memoised Algorithm 1)", "layers": G, "trials_per_layer": int(sel.size),
+                **worst, "oracle_seconds": o_s,
+                "gate": ("|g - o| <= max(1e-5 * max(|o|, S_o), 1 USD)" if mixed else
+                         "|g - o| / max(|o|, S_o) <= 1e-12")}
+    res = {
+        "workload": ("mixed precision (FP32 tables): " if mixed else "") + BATCHED,
+        "metric": "layer-trial-events/s", "value": value, "unit": "layer-trial-events/s",
+        "ms_per_step": ms_g, "steps": steps, "warmup": args.warmup,
+        "dtype": "f32 tables, exact trial sums" if mixed else "f64",
+        "step": "ara_plan_run: one CUDA graph of 64 ELT folds + the grouped YLT passes + batched PML/TVaR "
+                "(launch shapes autotuned at plan creation)",
+        "yet_layout": yet_layout(compact_ms),
+        "l2": "inputs larger than L2 (a 2-2.7 GB YET id stream per pass)",
         "ylt_kernels_ms_per_step": ylt_b,
-        "ylt_kernels_note": "CUDA events around the YLT launches of ara_layers_ylt (the graph replays the "
-                            "same kernels in the same shapes)",
-        "passes": [{"entry_bytes": eb, "layers": g, "lanes_per_trial": lpt, "unroll": u, "l2_prefetch": pf}
-                   for eb, g, lpt, u, pf, _ in passes],
+        "passes": [{"entry_bytes": eb, "layers": list(pos), "lanes_per_trial": lpt, "unroll": u, "l2_prefetch": pf}
+                   for eb, g, lpt, u, pf, pos in passes],
         "calls_per_step": {"ms_per_step": ms_b, "ylt_kernels_ms_per_step": ylt_b,
-                           "value": G * M / (ms_b / 1e3),
                            "step": "64 x ara_define_layer + ara_layers_ylt + ara_pml_tvar_batch"},
         "plain_per_layer": {"ms_per_step": ms_p, "ylt_kernels_ms_per_step": ylt_p,
-                            "value": G * M / (ms_p / 1e3),
                             "step": "64 x ara_define_layer + 64 x ara_layer_ylt + ara_pml_tvar_batch"},
         "speedup_vs_plain": ms_p / ms_g,
-        "roofline": batched_roofline(M, N, w.yet.catalog_size, G, 4 if mixed else 8, ylt_b, len(passes)),
+        "roofline": batched_roofline(M, N, C, G, 4 if mixed else 8, ylt_b, len(passes)),
+        "accuracy": accuracy,
+        "pml_tvar_sample": {"layer0_pml": pml_plan[0].tolist(), "layer0_tvar": tvar_plan[0].tolist()},
         "clocks": clocks.summary(),
+        "gpu_launches_per_step": None,
     }
+    res["roofline"]["l1tex"] = l1tex
     if mixed:
-        line["dtype"] = "f32 tables, exact trial sums"
-        line["config"]["workload"] = "mixed precision (FP32 tables): " + BATCHED
-        line["accuracy"] = accuracy
+        res["plain_fp64_per_layer_ms_per_step"] = ms_p64
+        res["speedup_vs_plain_fp64"] = ms_p64 / ms_g
+    # 64 folds, one YLT launch per pass, the batched selection (init + 8
+    # passes + sum), and the interleave of each multi-layer pass
+    res["gpu_launches_per_step"] = G + len(passes) + 10 + sum(1 for _, g, *_ in passes if g > 1)
+    return res
+
+
+def run_batched(args):
+    """The config-2 (or, with --workload mixed, config-3) line on its own."""
+    w = S.batched(n_trials=args.trials)
+    r = batched_result(args, w, mixed=args.workload == "mixed")
+    line = {"metric": METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": 1, "steps": r["steps"],
+            "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic (seeded)",
+            "config": {"workload": r["workload"], "layers": len(w.layers), "n_trials": w.yet.n_trials,
+                       "occurrences": w.yet.n_occurrences, "l2": r["l2"]},
+            "gpu_launches": r["gpu_launches_per_step"] * r["steps"]}
+    line.update({k: v for k, v in r.items() if k not in line and k not in ("workload", "gpu_launches_per_step")})
     print(json.dumps(line), flush=True)
 
 
@@ -630,18 +776,19 @@ SERVICE = ("ad hoc pricing service: paper-scale YET (catalog 2,000,000 events; 1
            "FP32 tables with exact trial sums; PML/TVaR at RP 100/250/500")
 
 
-def run_service(args):
+def service_result(args, w, nested: bool = False) -> dict:
     """Config-4 serving run: a seeded Poisson stream of layer-pricing requests
     played open-loop against the pricing service (continuous batching over
-    slots, admission by device memory); reports requests/s and p50/p99
-    latency, then the same requests all at once (saturating) and at a higher
-    rate; 1% of the requests are checked against the oracle on sampled trials."""
+    slots, admission by device memory); requests/s and p50/p99 latency, then
+    the same requests all at once (saturating) and, unless nested, at ten
+    times the rate; 1% of the requests are checked against the oracle on
+    sampled trials."""
     from paper_1412_4556_b300 import ARA_FP32_TABLE, ARA_FP64, Engine, Service
     import oracle
 
     rps = (100.0, 250.0, 500.0)
-    w = S.batched(n_layers=1, n_trials=args.trials)
-    reqs = S.service_requests(n_requests=args.requests, rate_per_s=args.rate)
+    n_req = args.nested_requests if nested else args.requests
+    reqs = S.service_requests(n_requests=n_req, rate_per_s=args.rate)
     eng = Engine(0)
     eng.load_yet_from(w.yet)
     compact_ms = compact(eng, args)
@@ -728,13 +875,15 @@ def run_service(args):
         time.sleep(0.3)
         clocks.mark(t0, t1)
     _, saturating = play(None)
-    _, fast = play(10.0)
+    fast = None if nested else play(10.0)[1]
 
     # 1% of the requests against the FP64 oracle (memoised Algorithm 1) on
-    # sampled trials; PML/TVaR against the FP64 GPU path, which matches the
-    # oracle within 1e-12 per trial in the parity tests.
+    # sampled trials; PML/TVaR against the oracle's PML/TVaR of the request's
+    # whole YLT when it is the 100k-trial prefix, else against the FP64 GPU
+    # path (which matches the oracle on every trial in the parity tests).
     g = np.random.default_rng(7)
-    worst_rel, worst_bound, worst_pml, worst_tvar, oracle_s, oracle_occ = 0.0, 0.0, 0.0, 0.0, 0.0, 0
+    worst = {"max_err_over_bar": 0.0, "trials_over_bar": 0, "trials_over_plain_bar": 0, "max_rel_err": 0.0}
+    worst_pml, oracle_s, oracle_occ = 0.0, 0.0, 0
     for i in sample:
         rq, r = reqs[i], res[i]
         sel = np.sort(g.choice(rq.n_trials, min(rq.n_trials, args.oracle_trials), replace=False))
@@ -742,47 +891,53 @@ def run_service(args):
         o, pre = oracle.layer_ylt(w.yet, w.pool, rq.layer, trials=sel, mode="memo")
         oracle_s += time.perf_counter() - t
         oracle_occ += int(np.sum(np.diff(w.yet.offsets)[sel]))
-        err = np.abs(r.ylt[sel] - o)
-        worst_rel = max(worst_rel, float(np.max(err / np.maximum(np.maximum(np.abs(o), pre), 1e-300))))
-        worst_bound = max(worst_bound, float(np.max(err / np.maximum(1e-5 * np.maximum(np.abs(o), pre), 1.0))))
+        rep = oracle.compare_reduced(r.ylt[sel], o, pre)
+        for k in worst:
+            worst[k] = (worst[k] + rep[k]) if k.startswith("trials") else max(worst[k], rep[k])
         L = rq.layer
         h = eng.define_layer([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim,
                              precision=ARA_FP64)
         p64, t64 = eng.pml_tvar(eng.layer_ylt(h, rq.n_trials), rps)
         eng.release_layer(h)
-        worst_pml = max(worst_pml, float(np.max(np.abs(r.pml - p64) / np.maximum(p64, 1.0))))
-        worst_tvar = max(worst_tvar, float(np.max(np.abs(r.tvar - t64) / np.maximum(t64, 1.0))))
+        worst_pml = max(worst_pml, float(np.max(np.abs(r.pml - p64) / np.maximum(p64, 1.0))),
+                        float(np.max(np.abs(r.tvar - t64) / np.maximum(t64, 1.0))))
     eng.close()
     import multiprocessing
-    line = {
-        "metric": METRIC, "value": saturating["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
-        "steps": len(reqs), "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / saturating["requests_per_s"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 tables, exact trial sums", "data": "synthetic (seeded)",
-        "config": {"workload": SERVICE, "requests": len(reqs), "arrival_rate_per_s": args.rate,
-                   "slots": args.slots, "max_batch": args.max_batch,
-                   "step": "one request: fold + YLT + PML/TVaR, host in and out",
-                   "yet_layout": ("stored order, 6 packed ids per 16 bytes" if compact_ms is None else
-                                  "ara_compact_yet: 8 difference-coded ids per 16 bytes, each group of 8 ascending (prepared once "
-                                  "before timing, %.1f ms)" % compact_ms),
-                   "l2": "inputs larger than L2 (up to 4 GB of YET ids per request)"},
+    return {
+        "workload": SERVICE, "requests": len(reqs), "arrival_rate_per_s": args.rate,
+        "slots": args.slots, "max_batch": args.max_batch, "yet_layout": yet_layout(compact_ms),
+        "requests_per_s_saturating": saturating["requests_per_s"],
         "latency_ms": {"p50": paced["p50_ms"], "p99": paced["p99_ms"], "at_rate_per_s": args.rate},
         "alone_ms_by_trials": device_ms,
         "paced": paced, "paced_10x": fast, "saturating": saturating,
-        "accuracy_1pct": {"requests": len(sample), "trials_per_request": args.oracle_trials,
-                          "max_rel_trial_err_vs_oracle": worst_rel,
-                          "max_err_over_bound(1e-5 rel, 1 USD)": worst_bound,
-                          "max_rel_pml_err_vs_fp64": worst_pml, "max_rel_tvar_err_vs_fp64": worst_tvar},
+        "accuracy_1pct": {"vs": "FP64 oracle (memoised Algorithm 1)", "requests": len(sample),
+                          "trials_per_request": args.oracle_trials, **worst,
+                          "max_rel_pml_tvar_err_vs_fp64_path": worst_pml,
+                          "gate": "|g - o| <= max(1e-5 * max(|o|, S_o), 1 USD)"},
         "cpu_baseline": {"value": oracle_occ / oracle_s, "unit": "layer-trial-events/s",
                          "cores": multiprocessing.cpu_count(), "kind": "oracle",
                          "sample": f"memoised oracle on {args.oracle_trials} sampled trials of each of "
                                    f"{len(sample)} requests"},
         "clocks": clocks.summary(),
     }
+
+
+def run_service(args):
+    """The config-4 line on its own (requests/s saturating is its value)."""
+    w = S.batched(n_layers=1, n_trials=args.trials)
+    r = service_result(args, w)
+    line = {"metric": METRIC, "value": r["requests_per_s_saturating"], "unit": "requests/s", "n_gpus": 1,
+            "steps": r["requests"], "warmup": max(args.warmup, 3),
+            "ms_per_step": 1e3 / r["requests_per_s_saturating"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 tables, exact trial sums", "data": "synthetic (seeded)",
+            "config": {"workload": r["workload"], "requests": r["requests"],
+                       "arrival_rate_per_s": r["arrival_rate_per_s"], "slots": r["slots"],
+                       "max_batch": r["max_batch"], "l2": "inputs larger than L2 (up to 4 GB of YET ids per request)"}}
+    line.update({k: v for k, v in r.items() if k not in line and k != "workload"})
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------ oracle arm
+# ------------------------------------------------------------ YELT arm
 YELT_WORKLOAD = ("paper-scale Year Event Loss Table, FP64: the paper-scale YET and layer; step = "
                  "ara_define_layer + ara_layer_yelt (every occurrence's increment and each trial's "
                  "largest, device outputs) + ara_rpl_report (AEP/OEP return period losses, RP "
@@ -908,40 +1063,54 @@ def run_yelt(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ oracle arm
+def reference_step_trials(n: int, fixed: float, per_trial: float, steps: int, warmup: int,
+                          budget_s: float) -> int:
+    """Trials each reference step prices: all n when (steps + warmup) steps of
+    them fit in budget_s seconds, else the largest sample that does."""
+    per_step = budget_s / max(steps + warmup, 1)
+    if fixed + n * per_trial <= per_step:
+        return n
+    return int(max(256, min(n, (per_step - fixed) / per_trial)))
+
+
 def run_reference(args):
+    """The oracle (literal Algorithm 1 on all host cores) timed on the engine
+    arm's workload and config: each step prices the whole YET when the run
+    fits the budget, else the same fixed trial sample every step; value and
+    ms_per_step are the priced trials' own, measured, not extrapolated."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     w = S.paper_scale(n_trials=args.trials)
-    M = w.yet.n_occurrences
+    N, C = w.yet.n_trials, w.yet.catalog_size
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(5)
-    model = oracle_cost_model(w, threads, rng)
-    # Each timed step prices a fresh trial sample sized so that the whole run
-    # stays within a few minutes; warm-up steps price 256 trials.
-    per = max(0.25, min(args.cpu_budget, 150.0 / max(args.steps + args.warmup, 1)))
+    fixed, per_trial = oracle_cost_model(w, threads, rng)
+    k = reference_step_trials(N, fixed, per_trial, args.steps, args.warmup, args.reference_budget)
+    sel = np.arange(N) if k == N else np.sort(rng.choice(N, k, replace=False))
     for _ in range(args.warmup):
-        oracle_sample(w, budget_s=0.0, threads=threads, model=model, rng=rng)
-    vals, samples = [], []
+        _time_oracle(w, sel, threads)
+    secs, occ = [], 0
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        r = oracle_sample(w, budget_s=per, threads=threads, model=model, rng=rng)
-        vals.append(r["value"])
-        samples.append(r)
+        dt, occ = _time_oracle(w, sel, threads)
+        secs.append(dt)
     wall = time.perf_counter() - t_all
-    value = statistics.median(vals)
-    ms_step = M / value * 1e3
+    ms_step = 1e3 * sum(secs) / len(secs)
+    value = occ / (ms_step / 1e3)
+    sample = (f"{k} of {N} trials ({occ} trial-events) per step, literal Algorithm 1 (16 direct-access-table "
+              f"lookups per event), {threads} threads")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
-        "config": {"workload": WORKLOAD, "n_trials_per_gpu": w.yet.n_trials, "occurrences_per_gpu": M,
-                   "note": "each step times the oracle on a fresh bounded trial sample (about "
-                           f"{per:.2f} s of it, so that the run ends within minutes; the oracle's fixed "
-                           "cost per call, its table build, weighs more in short samples); "
-                           "ms_per_step is extrapolated to the full workload from the median rate"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[-1]["cores"], "kind": "oracle",
-                         "sample": samples[-1]["sample"]},
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; stands in for the paper's proprietary "
+                                                      "industry data)", "impl": "reference",
+        "config": paper_config(N, w.yet.n_occurrences, C, len(w.layers[0].elts), world,
+                               tail_size(N, world, w.return_periods)),
+        "step": "oracle: literal Algorithm 1 over the step's trials (FP64, threaded over trials)",
+        "trials_per_step": k,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
@@ -951,22 +1120,30 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--workload", choices=["paper", "batched", "mixed", "service", "yelt"], default="paper",
-                    help="paper: the single-layer paper-scale step (default); batched: 64 layers; "
-                         "mixed: 64 FP32-table layers; service: the pricing-request stream; "
-                         "yelt: the Year Event Loss Table and RPL report")
+                    help="paper: the single-layer paper-scale step with the other configs nested (default); "
+                         "batched: 64 layers; mixed: 64 FP32-table layers; service: the pricing-request "
+                         "stream; yelt: the Year Event Loss Table and RPL report")
     ap.add_argument("--requests", type=int, default=2000, help="service: requests in the stream")
+    ap.add_argument("--nested-requests", type=int, default=500,
+                    help="requests of the service run nested in the default line")
     ap.add_argument("--rate", type=float, default=50.0, help="service: Poisson arrival rate per s")
     ap.add_argument("--slots", type=int, default=4, help="service: batches in flight")
     ap.add_argument("--max-batch", type=int, default=16, help="service: requests per batch")
     ap.add_argument("--oracle-trials", type=int, default=2000, help="service: trials checked per sample")
     ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work (cpu_baseline)")
+    ap.add_argument("--reference-budget", type=float, default=240.0,
+                    help="seconds the --impl reference run may take over all its steps")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-parity", action="store_true", help="skip the full oracle comparison")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="default line without the nested batched/mixed/service runs")
+    ap.add_argument("--no-timestamps", action="store_true", help="YET without time-stamps")
     ap.add_argument("--no-compact", action="store_true",
                     help="price from the stored-order id layout (skip ara_compact_yet)")
     args = ap.parse_args()
