@@ -261,12 +261,14 @@ def tiny(seed: int = DEFAULT_SEED, n_trials: int = 1_000) -> Workload:
 
 
 def paper_scale(seed: int = DEFAULT_SEED, n_trials: int = 1_000_000, lam: float = 1000.0,
-                with_timestamps: bool = False, catalog_size: int = 2_000_000) -> Workload:
+                with_timestamps: bool = False, catalog_size: int = 2_000_000,
+                threads: Optional[int] = None) -> Workload:
     """Paper-scale plain ARA (Section IV-C workload shape): catalog 2,000,000;
     one layer over 16 ELTs x 20,000 events; deductibles U[5e3, 5e4], limits
     U[1e6, 1e7]; Poisson(1000) events per trial over 1,000,000 trials; layer
-    terms as in ``tiny``; RP 100/250/500."""
-    yet = make_yet(seed, catalog_size, n_trials, lam, with_timestamps=with_timestamps)
+    terms as in ``tiny``; RP 100/250/500.  The YET's time-stamps are drawn when
+    with_timestamps is set (the YLT does not read them)."""
+    yet = make_yet(seed, catalog_size, n_trials, lam, with_timestamps=with_timestamps, threads=threads)
     g = rng_for(seed, "elt-terms")
     ded = g.uniform(5e3, 5e4, size=16)
     lim = g.uniform(1e6, 1e7, size=16)

@@ -113,6 +113,22 @@ def merge_shard_tails(parts):
     return np.concatenate([np.asarray(p, dtype=np.float64) for p in parts])
 
 
+def shard_step(eng, handles, layer, ylt_out, k_tail, tail_out, gather_out, n_per_rank, rank, world, rps,
+               all_gather):
+    """One step of a trial shard under torchrun: fold the layer, price this
+    rank's trials, send its k_tail largest losses (ara_ylt_tail) through
+    all_gather(gather_out, tail_out), and on rank 0 price the union as the
+    whole YLT of n_per_rank * world trials (ara_pml_tvar_tail).  Returns
+    (PML, TVaR) on rank 0, None elsewhere."""
+    L = eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
+    eng.layer_ylt(L, out=ylt_out)
+    eng.ylt_tail(ylt_out, k_tail, out=tail_out)
+    all_gather(gather_out, tail_out)
+    res = eng.pml_tvar_tail(gather_out, n_per_rank * world, rps) if rank == 0 else None
+    eng.release_layer(L)
+    return res
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -362,8 +378,12 @@ def run_engine(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
+    t_gen = time.perf_counter()
+    # ranks share the host's cores while they draw their shards
     w = S.paper_scale(seed=shard_seed(S.DEFAULT_SEED, rank), n_trials=args.trials,
-                      with_timestamps=not args.no_timestamps)
+                      with_timestamps=not args.no_timestamps,
+                      threads=max(1, (os.cpu_count() or 1) // world))
+    gen_s = time.perf_counter() - t_gen
     layer = w.layers[0]
     rps = w.return_periods
     M, N, C = w.yet.n_occurrences, w.yet.n_trials, w.yet.catalog_size
@@ -386,24 +406,24 @@ def run_engine(args):
         tail_dev = torch.empty(k_tail, dtype=torch.float64, device=dev)
         gather_buf = torch.empty(k_tail * world, dtype=torch.float64, device=dev)
 
+    def all_gather(out, inp):
+        import torch.distributed as dist
+        with torch.cuda.stream(stream):
+            dist.all_gather_into_tensor(out, inp)
+
     def step():
-        L = eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
-        eng.layer_ylt(L, out=ylt_dev)
         if world > 1:
             # each shard sends its k_tail largest losses (not its whole YLT)
-            import torch.distributed as dist
-            eng.ylt_tail(ylt_dev, k_tail, out=tail_dev)
-            with torch.cuda.stream(stream):
-                dist.all_gather_into_tensor(gather_buf, tail_dev)
-            res = eng.pml_tvar_tail(gather_buf, N * world, rps) if rank == 0 else None
-        else:
-            # queued without a host wait, so the next step's launches overlap
-            # this one's kernels; the results stay in HBM (the e2e line reads
-            # them back every step)
-            eng.pml_tvar_async(ylt_dev, rps, res_dev)
-            res = None
+            return shard_step(eng, handles, layer, ylt_dev, k_tail, tail_dev, gather_buf, N, rank, world, rps,
+                              all_gather)
+        L = eng.define_layer(handles, layer.occ_ret, layer.occ_lim, layer.agg_ret, layer.agg_lim)
+        eng.layer_ylt(L, out=ylt_dev)
+        # queued without a host wait, so the next step's launches overlap this
+        # one's kernels; the results stay in HBM (the e2e line reads them back
+        # every step)
+        eng.pml_tvar_async(ylt_dev, rps, res_dev)
         eng.release_layer(L)
-        return res
+        return None
 
     def barrier():
         if world > 1:
@@ -518,6 +538,7 @@ def run_engine(args):
         # kernels) and the selection over the union
         "gpu_launches": args.steps * (1 + 1 + 10 + (13 if world > 1 else 1)),
         "cpu_baseline": cpu,
+        "host_generation_s": gen_s,
     }
     line.update(nested)
     print(json.dumps(line), flush=True)

@@ -361,12 +361,19 @@ ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const doub
  * pre-pass of ara_define_layer), the grouped passes of ara_layers_ylt over
  * the first n_trials trials, and the PML/TVaR selection of
  * ara_pml_tvar_batch.  ara_plan_run replays it with one graph launch and
- * gives the same values as those calls.  With autotune != 0, plan creation
- * first times the YLT kernel's launch shapes (lanes per trial -- the trials a
- * warp sums side by side --, id loads per lane, and whether the id stream is
- * prefetched into L2) on the plan's own layers
- * and the first min(n_trials, 2^20) trials, and keeps the fastest for this
- * plan and for later ara_layers_ylt / ara_layer_ylt calls on the context.
+ * gives the same values as those calls.  The plan groups its layers into
+ * passes whose layers share most of their possibly nonzero events (each pass
+ * gathers one table row per occurrence that any of its layers needs): layers
+ * are taken densest first and each pass is filled with the layers whose
+ * zero-skip bitmaps overlap its union most.  Without autotune a pass holds 2
+ * FP64 or 4 FP32-table layers.  With autotune != 0, plan creation first
+ * times the YLT kernel's launch shapes (lanes per trial -- the trials a warp
+ * sums side by side --, id loads per lane, and whether the id stream is
+ * prefetched into L2) and, per entry width, the group size (FP64: 2 or 1
+ * layers per pass; FP32 tables: 4, 2 or 1) by timing the whole set of passes,
+ * on the plan's own layers and the first min(n_trials, 2^20) trials, and
+ * keeps the fastest; the launch shapes also serve later ara_layers_ylt /
+ * ara_layer_ylt calls on the context.
  * The plan owns its output buffers.  A plan stops working (ARA_E_STATE from
  * ara_plan_run) when the YET is reloaded or one of its layers is released;
  * ara_destroy destroys the context's plans.
@@ -390,9 +397,10 @@ ARA_API ara_status ara_plan_run(ara_plan *plan, double *ylt_out, double *pml_out
                                 void *cuda_stream);
 
 /* The plan's YLT passes: *n_passes receives their number and, for the first
- * max_passes, info[6*i .. 6*i+5] = entry bytes (16 FP64, 8 FP32-table),
- * layers in the pass, lanes per trial, id loads per lane, L2 prefetch (1/0),
- * and the position in the plan's layer list of the pass's first layer. */
+ * max_passes, info[9*i .. 9*i+8] = entry bytes (16 FP64, 8 FP32-table),
+ * layers in the pass (G), lanes per trial, id loads per lane, L2 prefetch
+ * (1/0), and the positions in the plan's layer list of the pass's G layers
+ * (then -1 up to four). */
 ARA_API ara_status ara_plan_passes(const ara_plan *plan, int32_t max_passes, int32_t *info,
                                    int32_t *n_passes);
 

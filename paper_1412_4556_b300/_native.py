@@ -255,12 +255,17 @@ def ara_plan_run(ctx: int, plan: int, ylt_out: int, pml_out: int, tvar_out: int,
 
 
 def ara_plan_passes(ctx: int, plan: int):
-    """List of (entry bytes, layers, lanes per trial, unroll, prefetch, first layer) per YLT pass."""
+    """List of (entry bytes, layers G, lanes per trial, unroll, prefetch, (positions of the G layers))
+    per YLT pass."""
     n = _i32(0)
     _check(ctx, lib.ara_plan_passes(plan, 0, None, C.byref(n)))
-    info = (_i32 * (6 * max(n.value, 1)))()
+    info = (_i32 * (9 * max(n.value, 1)))()
     _check(ctx, lib.ara_plan_passes(plan, n.value, info, C.byref(n)))
-    return [tuple(info[6 * i:6 * i + 6]) for i in range(n.value)]
+    out = []
+    for i in range(n.value):
+        eb, g, lpt, u, pf = info[9 * i:9 * i + 5]
+        out.append((eb, g, lpt, u, pf, tuple(info[9 * i + 5:9 * i + 5 + g])))
+    return out
 
 
 def ara_plan_destroy(plan: int) -> None:

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -94,6 +95,25 @@ ara_status reject_foreign(ara_ctx *c, std::initializer_list<std::pair<const void
       return fail(c, ARA_E_INVALID_ARG, "%s is memory of another GPU than the context's (device %d)", pn.second,
                   c->device);
   return ARA_OK;
+}
+
+int current_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  const int slot = dev < kMaxDev ? dev : kMaxDev - 1;
+  int sms = cache[slot].load(std::memory_order_relaxed);
+  if (sms > 0 && dev < kMaxDev) return sms;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  if (dev < kMaxDev) cache[slot].store(sms, std::memory_order_relaxed);
+  return sms;
 }
 
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
@@ -441,8 +461,79 @@ ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, d
   return ARA_OK;
 }
 
+std::vector<LayerGroup> group_in_order(const std::vector<LayerRec *> &Ls, int g16, int g8) {
+  std::vector<LayerGroup> out;
+  for (const int eb : {16, 8}) {
+    std::vector<int32_t> idx;
+    for (size_t i = 0; i < Ls.size(); ++i)
+      if (Ls[i]->entry_bytes() == eb) idx.push_back((int32_t)i);
+    const int gmax = eb == 16 ? g16 : g8;
+    for (size_t p = 0; p < idx.size();) {
+      int G = (int)std::min<size_t>((size_t)gmax, idx.size() - p);
+      if (G == 3) G = 2;
+      out.push_back(LayerGroup{eb, std::vector<int32_t>(idx.begin() + (long)p, idx.begin() + (long)p + G)});
+      p += (size_t)G;
+    }
+  }
+  return out;
+}
+
+ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g16, int g8, cudaStream_t s,
+                            std::vector<LayerGroup> *out) {
+  out->clear();
+  if (Ls.empty()) return ARA_OK;
+  const size_t words64 = (size_t)Ls[0]->bm.words / 2;  // bitmaps hold a multiple of 4 words
+  std::vector<uint64_t> bits(Ls.size() * words64);
+  for (size_t i = 0; i < Ls.size(); ++i)
+    ARA_CUDA(c, cudaMemcpyAsync(bits.data() + i * words64, Ls[i]->d_bitmap, words64 * 8, cudaMemcpyDeviceToHost, s),
+             "copy zero-skip bitmap");
+  ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  auto row = [&](size_t i) { return bits.data() + i * words64; };
+  std::vector<int64_t> pop(Ls.size(), 0);
+  for (size_t i = 0; i < Ls.size(); ++i)
+    for (size_t w = 0; w < words64; ++w) pop[i] += __builtin_popcountll(row(i)[w]);
+  std::vector<uint64_t> uni(words64);
+  for (const int eb : {16, 8}) {
+    const int gmax = eb == 16 ? g16 : g8;
+    std::vector<int32_t> left;
+    for (size_t i = 0; i < Ls.size(); ++i)
+      if (Ls[i]->entry_bytes() == eb) left.push_back((int32_t)i);
+    std::stable_sort(left.begin(), left.end(), [&](int32_t a, int32_t b) { return pop[(size_t)a] > pop[(size_t)b]; });
+    while (!left.empty()) {
+      std::vector<int32_t> g{left.front()};
+      left.erase(left.begin());
+      std::copy(row((size_t)g[0]), row((size_t)g[0]) + words64, uni.begin());
+      while ((int)g.size() < gmax && !left.empty()) {
+        size_t best = 0;
+        int64_t best_ov = -1;
+        for (size_t k = 0; k < left.size(); ++k) {
+          const uint64_t *b = row((size_t)left[k]);
+          int64_t ov = 0;
+          for (size_t w = 0; w < words64; ++w) ov += __builtin_popcountll(uni[w] & b[w]);
+          if (ov > best_ov) {
+            best_ov = ov;
+            best = k;
+          }
+        }
+        const uint64_t *b = row((size_t)left[best]);
+        for (size_t w = 0; w < words64; ++w) uni[w] |= b[w];
+        g.push_back(left[best]);
+        left.erase(left.begin() + (long)best);
+      }
+      if (g.size() == 3) {  // no 3-layer pass: 2 + 1
+        out->push_back(LayerGroup{eb, {g[0], g[1]}});
+        out->push_back(LayerGroup{eb, {g[2]}});
+      } else {
+        out->push_back(LayerGroup{eb, g});
+      }
+    }
+  }
+  return ARA_OK;
+}
+
 ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, int64_t n_trials,
-                         double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap) {
+                         double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap,
+                         const std::vector<LayerGroup> *groups) {
   std::vector<LayerRec *> Ls((size_t)n_layers);
   for (int32_t i = 0; i < n_layers; ++i) {
     ara_status st = get_layer(c, layers[i], &Ls[(size_t)i]);
@@ -455,47 +546,46 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
     }
   const BitmapLayout bm = Ls[0]->bm;  // every layer of a catalog shares the layout
   const size_t entries = (size_t)c->catalog + 1;
-  // FP64 layers go two to a pass (2 x 16-byte entries per event), FP32-table
-  // layers four to a pass (4 x 8 bytes): one 32-byte L2 sector per gather.
-  for (const int eb : {16, 8}) {
-    std::vector<int32_t> idx;
-    for (int32_t i = 0; i < n_layers; ++i)
-      if (Ls[(size_t)i]->entry_bytes() == eb) idx.push_back(i);
-    const int gmax = 32 / eb;
-    for (size_t p = 0; p < idx.size();) {
-      int G = (int)std::min<size_t>((size_t)gmax, idx.size() - p);
-      if (G == 3) G = 2;
-      LayerOut outs[4];
-      Tables4 tabs{};
-      Bitmaps4 bms{};
-      for (int g = 0; g < G; ++g) {
-        const LayerRec *L = Ls[(size_t)idx[p + (size_t)g]];
-        outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim,
-                           dst + (size_t)idx[p + (size_t)g] * (size_t)n_trials};
-        tabs.t[g] = L->d_table;
-        bms.b[g] = L->d_bitmap;
-      }
-      const void *table = tabs.t[0];
-      const uint32_t *bitmap = bms.b[0];
-      if (G > 1) {
-        ARA_CUDA(c, launch_interleave(tabs, eb, G, (int64_t)entries, pair_table, bms, bm.words, pair_bitmap, s),
-                 "interleave layer tables");
-        table = pair_table;
-        bitmap = pair_bitmap;
-      }
-      const YltStream ys = ylt_stream(c, G);
-      const double mean_chunks = (double)ys.h_coff[(size_t)n_trials] / (double)n_trials;
-      YltLaunch cfg;
-      ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, ys.layout, eb, G, entries * (size_t)(eb * G),
-                           c->tuned[eb == 8 ? 1 : 0][G], &cfg),
-               "plan YLT launch");
-      TimedLaunch tl(c, ARA_TIMING_YLT, s);
-      ARA_CUDA(c, launch_ylt_group(ys.coff, ys.chunks, ys.layout, n_trials, table, eb, bitmap, bm, c->catalog,
-                                   G, outs, cfg, s),
-               "YLT kernel launch");
-      tl.done();
-      p += (size_t)G;
+  // By default FP64 layers go two to a pass (2 x 16-byte entries per event)
+  // and FP32-table layers four to a pass (4 x 8 bytes): one 32-byte L2
+  // sector per gather.
+  const std::vector<LayerGroup> in_order = groups ? std::vector<LayerGroup>() : group_in_order(Ls, 2, 4);
+  for (const LayerGroup &grp : groups ? *groups : in_order) {
+    const int eb = grp.eb;
+    const int G = (int)grp.idx.size();
+    if (!((eb == 16 && (G == 1 || G == 2)) || (eb == 8 && (G == 1 || G == 2 || G == 4))))
+      return fail(c, ARA_E_INVALID_ARG, "a pass of %d layers of %d-byte entries", G, eb);
+    LayerOut outs[4];
+    Tables4 tabs{};
+    Bitmaps4 bms{};
+    for (int g = 0; g < G; ++g) {
+      const int32_t i = grp.idx[(size_t)g];
+      if (i < 0 || i >= n_layers || Ls[(size_t)i]->entry_bytes() != eb)
+        return fail(c, ARA_E_INVALID_ARG, "pass layer position %d", i);
+      const LayerRec *L = Ls[(size_t)i];
+      outs[g] = LayerOut{L->q, L->agg_fx, L->agg_ret, L->agg_lim, dst + (size_t)i * (size_t)n_trials};
+      tabs.t[g] = L->d_table;
+      bms.b[g] = L->d_bitmap;
     }
+    const void *table = tabs.t[0];
+    const uint32_t *bitmap = bms.b[0];
+    if (G > 1) {
+      ARA_CUDA(c, launch_interleave(tabs, eb, G, (int64_t)entries, pair_table, bms, bm.words, pair_bitmap, s),
+               "interleave layer tables");
+      table = pair_table;
+      bitmap = pair_bitmap;
+    }
+    const YltStream ys = ylt_stream(c, G);
+    const double mean_chunks = (double)ys.h_coff[(size_t)n_trials] / (double)n_trials;
+    YltLaunch cfg;
+    ARA_CUDA(c, plan_ylt(c->device, bm, mean_chunks, ys.layout, eb, G, entries * (size_t)(eb * G),
+                         c->tuned[eb == 8 ? 1 : 0][G], &cfg),
+             "plan YLT launch");
+    TimedLaunch tl(c, ARA_TIMING_YLT, s);
+    ARA_CUDA(c, launch_ylt_group(ys.coff, ys.chunks, ys.layout, n_trials, table, eb, bitmap, bm, c->catalog,
+                                 G, outs, cfg, s),
+             "YLT kernel launch");
+    tl.done();
   }
   return ARA_OK;
 }

@@ -253,10 +253,32 @@ ara_status define_layer_on(ara_ctx *c, int32_t n_elts, const int32_t *handles, d
                            double occ_lim, double agg_ret, double agg_lim, int32_t precision,
                            cudaStream_t s, int32_t *layer_out, EltDesc *stage = nullptr);
 
+// The layers of one YLT pass: their entry width (16 FP64, 8 FP32-table) and
+// their positions in a layer list (1 or 2 layers of 16 bytes, 1, 2 or 4 of 8
+// bytes: at most one 32-byte sector per event).
+struct LayerGroup {
+  int eb;
+  std::vector<int32_t> idx;
+};
+
+// Passes over the layers Ls in list order, g16 FP64 layers or g8 FP32-table
+// layers to a pass (a group of three splits 2 + 1).
+std::vector<LayerGroup> group_in_order(const std::vector<LayerRec *> &Ls, int g16, int g8);
+
+// Passes whose layers share most of their possibly nonzero events: layers
+// taken densest first, each pass filled with the layers whose zero-skip
+// bitmaps overlap its union most (bitmaps copied to the host on stream s).
+// A pass gathers one table row for every occurrence that any of its layers
+// needs, so overlapping layers gather fewer rows.  g16 / g8 as above.
+ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g16, int g8, cudaStream_t s,
+                            std::vector<LayerGroup> *out);
+
 // The kernels of ara_layers_ylt on stream s: device output dst (layer-major),
 // pair_table / pair_bitmap scratch of 2 * (catalog + 1) entries and of the
-// layers' bitmap size.  Layers must be folded for the loaded YET.
+// layers' bitmap size.  Layers must be folded for the loaded YET.  groups:
+// the passes to run (positions in layers), or NULL for group_in_order(2, 4).
 ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, int64_t n_trials,
-                         double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap);
+                         double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap,
+                         const std::vector<LayerGroup> *groups = nullptr);
 
 }  // namespace ara

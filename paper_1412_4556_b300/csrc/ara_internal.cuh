@@ -232,6 +232,10 @@ __device__ __forceinline__ U128 warp_sum_u128(U128 v) {
   return v;
 }
 
+// SM count of the current device (queried once per device; 148 on B300), for
+// grids sized in multiples of the SMs.
+int current_sm_count();
+
 // --------------------------------------------------------- launchers
 // Each returns cudaSuccess or the launch error.
 // f64_out (nullable) gets every event's binary64 value; with inexact given,

@@ -360,7 +360,7 @@ cudaError_t launch_compact_scan(int64_t *count_plain, int64_t n_trials, int64_t 
 
 cudaError_t launch_compact_encode(const int64_t *raw_off, const int64_t *coff, const int4 *chunks, int64_t n_trials,
                                   const uint32_t *sorted, const int64_t *dcoff, int4 *dchunks, cudaStream_t s) {
-  compact_encode_kernel<<<148 * 8, 256, 0, s>>>(raw_off, coff, chunks, n_trials, sorted, dcoff, dchunks);
+  compact_encode_kernel<<<current_sm_count() * 8, 256, 0, s>>>(raw_off, coff, chunks, n_trials, sorted, dcoff, dchunks);
   return cudaGetLastError();
 }
 

@@ -146,7 +146,8 @@ cudaError_t launch_elt_ingest(const int64_t *d_off, int n_elts, int64_t total, c
   if (total <= 0) return cudaSuccess;
   const int threads = 256;
   const int64_t want = (total + threads - 1) / threads;
-  const int blocks = (int)(want < 148 * 16 ? want : 148 * 16);
+  const int64_t cap = (int64_t)current_sm_count() * 16;
+  const int blocks = (int)(want < cap ? want : cap);
   elt_count_kernel<<<blocks, threads, 0, s>>>(d_off, n_elts, d_raw_ids, d_raw_losses, catalog, nb, seen,
                                              seen_words, count, max_loss, max_id, bad);
   cudaError_t e = cudaGetLastError();

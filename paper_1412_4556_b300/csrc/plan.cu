@@ -2,10 +2,13 @@
 // layer's ELT fold, the grouped YLT passes over the YET and the batched
 // PML/TVaR selection -- captured once into a CUDA graph and replayed with one
 // launch (Section III: a Program or Portfolio is a set of Layers, each priced
-// by Algorithm 1).  Before capture an optional autotuner times the YLT
-// kernel's launch shapes (lanes per trial, i.e. trials summed side by side
-// per warp, id loads per lane, and the L2 prefetch of the id stream) on the
-// plan's own layers and trials, and the captured passes use the fastest.
+// by Algorithm 1).  A plan groups its layers into passes whose layers share
+// most of their nonzero events (a pass gathers one table row for every
+// occurrence any of its layers needs).  Before capture an optional autotuner
+// times the YLT kernel's launch shapes (lanes per trial, i.e. trials summed
+// side by side per warp, id loads per lane, and the L2 prefetch of the id
+// stream) and the group size (layers per pass) on the plan's own layers and
+// trials, and the captured passes use the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,10 +40,14 @@ struct ara_plan {
   unsigned int *d_err = nullptr;
   double *h_out = nullptr;           // pinned copy of d_out
   unsigned int *h_err = nullptr;     // pinned copy of d_err
-  std::vector<int32_t> pass_info;    // 6 per pass: entry bytes, layers, lanes per trial, unroll, prefetch, first layer
+  std::vector<ara::LayerGroup> groups;  // the YLT passes (positions in layers)
+  std::vector<int32_t> pass_info;    // kPassInfo per pass: entry bytes, layers, lanes per trial, unroll, prefetch,
+                                     // the layers' positions (-1 padded to 4)
 };
 
 namespace {
+
+constexpr int kPassInfo = 9;
 
 void free_plan(ara_plan *p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -61,33 +68,9 @@ void free_plan(ara_plan *p) {
   delete p;
 }
 
-// The passes ara_layers_ylt makes for these layers: FP64 layers two at a
-// time, FP32-table layers four at a time (groups of three split 2 + 1).
-struct Pass {
-  int eb;
-  std::vector<int32_t> idx;  // positions in the plan's layer list
-};
-
-std::vector<Pass> group_passes(ara_ctx *c, const std::vector<int32_t> &layers) {
-  std::vector<Pass> out;
-  for (const int eb : {16, 8}) {
-    std::vector<int32_t> idx;
-    for (size_t i = 0; i < layers.size(); ++i)
-      if (c->layers[(size_t)layers[i]].entry_bytes() == eb) idx.push_back((int32_t)i);
-    const int gmax = 32 / eb;
-    for (size_t p = 0; p < idx.size();) {
-      int G = (int)std::min<size_t>((size_t)gmax, idx.size() - p);
-      if (G == 3) G = 2;
-      out.push_back(Pass{eb, std::vector<int32_t>(idx.begin() + (long)p, idx.begin() + (long)p + G)});
-      p += (size_t)G;
-    }
-  }
-  return out;
-}
-
 // Time the YLT kernel of one pass in every launch shape on the first n trials
 // and keep the fastest in the context (ara_layers_ylt then uses it too).
-ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
+ara_status tune_pass(ara_plan *p, const LayerGroup &ps, int64_t n) {
   ara_ctx *c = p->c;
   const int G = (int)ps.idx.size();
   LayerOut outs[4];
@@ -155,6 +138,82 @@ ara_status tune_pass(ara_plan *p, const Pass &ps, int64_t n) {
   return ARA_OK;
 }
 
+// Milliseconds of the passes `groups` over the first n trials (best of two
+// after a warm-up run).
+ara_status time_groups(ara_plan *p, const std::vector<LayerGroup> &groups, int64_t n, float *ms_out) {
+  ara_ctx *c = p->c;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ARA_CUDA(c, cudaEventCreate(&a), "cudaEventCreate");
+  cudaError_t e = cudaEventCreate(&b);
+  ara_status st = e == cudaSuccess ? ARA_OK : cuda_fail(c, e, "cudaEventCreate");
+  float best = 1e30f;
+  for (int rep = 0; rep < 3 && st == ARA_OK; ++rep) {
+    if ((e = cudaEventRecord(a, p->cap)) != cudaSuccess) {
+      st = cuda_fail(c, e, "cudaEventRecord");
+      break;
+    }
+    st = layers_ylt_on(c, p->layers.data(), (int32_t)p->layers.size(), n, p->d_ylt, p->cap, p->d_pair,
+                       p->d_pair_bm, &groups);
+    float t = 0.f;
+    if (st == ARA_OK && ((e = cudaEventRecord(b, p->cap)) != cudaSuccess ||
+                         (e = cudaEventSynchronize(b)) != cudaSuccess ||
+                         (e = cudaEventElapsedTime(&t, a, b)) != cudaSuccess))
+      st = cuda_fail(c, e, "time YLT passes");
+    if (st == ARA_OK && rep > 0) best = std::min(best, t);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  *ms_out = best;
+  return st;
+}
+
+// The plan's passes with the autotuner: for each entry width, every group
+// size the kernel has (FP64: 2 or 1 layers per pass; FP32 tables: 4, 2 or
+// 1), layers grouped by overlap, launch shapes tuned per group size, and the
+// whole set of passes of that width timed on the first n trials; the
+// fastest group size per width is kept.
+ara_status choose_groups(ara_plan *p, const std::vector<LayerRec *> &Ls, int64_t n, std::vector<LayerGroup> *out) {
+  ara_ctx *c = p->c;
+  out->clear();
+  bool tuned[2][5] = {};
+  // Only the group sizes the plan keeps leave their tuned launch shapes in
+  // the context (the others were tuned on this plan's passes alone).
+  YltShape before[2][5];
+  for (int a = 0; a < 2; ++a)
+    for (int g = 0; g < 5; ++g) before[a][g] = c->tuned[a][g];
+  for (const int eb : {16, 8}) {
+    std::vector<LayerGroup> best;
+    float best_ms = 1e30f;
+    for (const int gm : eb == 16 ? std::vector<int>{2, 1} : std::vector<int>{4, 2, 1}) {
+      std::vector<LayerGroup> all, mine;
+      ara_status st = group_by_overlap(c, Ls, gm, gm, p->cap, &all);
+      if (st) return st;
+      for (const LayerGroup &g : all)
+        if (g.eb == eb) mine.push_back(g);
+      if (mine.empty()) break;
+      for (const LayerGroup &g : mine) {
+        const int G = (int)g.idx.size();
+        if (tuned[eb == 8][G]) continue;
+        tuned[eb == 8][G] = true;
+        if ((st = tune_pass(p, g, n)) != ARA_OK) return st;
+      }
+      float ms = 0.f;
+      if ((st = time_groups(p, mine, n, &ms)) != ARA_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = mine;
+      }
+    }
+    out->insert(out->end(), best.begin(), best.end());
+  }
+  bool kept[2][5] = {};
+  for (const LayerGroup &g : *out) kept[g.eb == 8][g.idx.size()] = true;
+  for (int a = 0; a < 2; ++a)
+    for (int g = 0; g < 5; ++g)
+      if (!kept[a][g]) c->tuned[a][g] = before[a][g];
+  return ARA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -219,19 +278,18 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     cudaGetLastError();
     return bail(fail(c, ARA_E_NOMEM, "plan buffers: %s", cudaGetErrorString(e)));
   }
-  const std::vector<Pass> passes = group_passes(c, p->layers);
-  if (autotune) {
-    const int64_t n_tune = std::min<int64_t>(n_trials, 1 << 20);
-    bool seen[2][5] = {};
-    for (const Pass &ps : passes) {
-      const int G = (int)ps.idx.size();
-      if (seen[ps.eb == 8][G]) continue;
-      seen[ps.eb == 8][G] = true;
-      ara_status st = tune_pass(p, ps, n_tune);
-      if (st) return bail(st);
-    }
-  }
-  for (const Pass &ps : passes) {
+  std::vector<LayerRec *> Ls;
+  for (const int32_t h : p->layers) Ls.push_back(&c->layers[(size_t)h]);
+  ara_status gst = ARA_OK;
+  const bool timing_was = c->timing;  // the autotuner's launches stay off the timing channels
+  c->timing = false;
+  if (autotune)
+    gst = choose_groups(p, Ls, std::min<int64_t>(n_trials, 1 << 20), &p->groups);
+  else
+    gst = group_by_overlap(c, Ls, 2, 4, p->cap, &p->groups);
+  c->timing = timing_was;
+  if (gst) return bail(gst);
+  for (const LayerGroup &ps : p->groups) {
     const int G = (int)ps.idx.size();
     const YltStream ys = ylt_stream(c, G);
     const double mean_chunks = (double)ys.h_coff[(size_t)n_trials] / (double)n_trials;
@@ -239,7 +297,8 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     e = plan_ylt(c->device, bm, mean_chunks, ys.layout, ps.eb, G, ((size_t)c->catalog + 1) * (size_t)(ps.eb * G),
                  c->tuned[ps.eb == 8][G], &cfg);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "plan YLT launch"));
-    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch, ps.idx[0]});
+    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch});
+    for (int g = 0; g < 4; ++g) p->pass_info.push_back(g < G ? ps.idx[(size_t)g] : -1);
   }
   // Capture: folds, grouped YLT passes, batched selection, result copies.
   const bool timing = c->timing;
@@ -248,7 +307,8 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
   ara_status st = e == cudaSuccess ? ARA_OK : cuda_fail(c, e, "cudaStreamBeginCapture");
   for (size_t i = 0; i < nl && st == ARA_OK; ++i) st = enqueue_fold(c, c->layers[(size_t)p->layers[i]], p->cap);
   if (st == ARA_OK)
-    st = layers_ylt_on(c, p->layers.data(), n_layers, n_trials, p->d_ylt, p->cap, p->d_pair, p->d_pair_bm);
+    st = layers_ylt_on(c, p->layers.data(), n_layers, n_trials, p->d_ylt, p->cap, p->d_pair, p->d_pair_bm,
+                       &p->groups);
   if (st == ARA_OK && (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), p->cap)) != cudaSuccess)
     st = cuda_fail(c, e, "cudaMemsetAsync");
   if (st == ARA_OK && (e = launch_pml_tvar_batch(p->d_ylt, n_layers, n_trials, p->k, n_rp, p->d_ws, p->d_out,
@@ -306,11 +366,11 @@ ara_status ara_plan_run(ara_plan *p, double *ylt_out, double *pml_out, double *t
 
 ara_status ara_plan_passes(const ara_plan *p, int32_t max_passes, int32_t *info, int32_t *n_passes) {
   if (!p || !n_passes) return fail_free(ARA_E_INVALID_ARG, "NULL argument");
-  const int32_t n = (int32_t)(p->pass_info.size() / 6);
+  const int32_t n = (int32_t)(p->pass_info.size() / kPassInfo);
   *n_passes = n;
   if (info)
     for (int32_t i = 0; i < std::min(n, max_passes); ++i)
-      for (int j = 0; j < 6; ++j) info[6 * i + j] = p->pass_info[(size_t)(6 * i + j)];
+      for (int j = 0; j < kPassInfo; ++j) info[kPassInfo * i + j] = p->pass_info[(size_t)(kPassInfo * i + j)];
   return ARA_OK;
 }
 

@@ -232,8 +232,9 @@ cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, c
   select_init_kernel<<<n_layers, 256, 0, s>>>(st, ka, n_rp);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  int sms = 0;
+  err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (err != cudaSuccess) return err;
   int64_t blocks = (n + kSelectThreads - 1) / kSelectThreads;
   int64_t cap = ((int64_t)sms * 4 + n_layers - 1) / n_layers;
   if (cap < 1) cap = 1;

@@ -10,6 +10,8 @@
 // output holds the values above tau in index order, then k - count copies
 // of tau.  Values compare as binary64 bit patterns, as in the selection
 // (trial losses are finite and >= 0, so the patterns order like the values).
+#include <algorithm>
+
 #include "ara_internal.cuh"
 
 namespace ara {
@@ -17,7 +19,6 @@ namespace ara {
 namespace {
 
 constexpr int kTailThreads = 1024;
-constexpr int kTailMaxBlocks = 592;  // 148 SMs x 4
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -100,7 +101,10 @@ tail_write_kernel(const double *__restrict__ y, int64_t n, int64_t per, const do
 cudaError_t launch_ylt_tail(const double *y, int64_t n, int64_t k, const double *tau, int64_t *scratch,
                             double *out, cudaStream_t s) {
   int64_t nb = (n + kTailThreads - 1) / kTailThreads;
-  if (nb > kTailMaxBlocks) nb = kTailMaxBlocks;
+  // four blocks per SM, and no more block counts than the offsets kernel's
+  // threads (and the scratch) hold
+  const int64_t cap = std::min<int64_t>((int64_t)current_sm_count() * 4, std::min(kTailThreads, kTailScratch));
+  if (nb > cap) nb = cap;
   if (nb < 1) nb = 1;
   const int64_t per = (n + nb - 1) / nb > 0 ? (n + nb - 1) / nb : 1;
   nb = (n + per - 1) / per > 0 ? (n + per - 1) / per : 1;

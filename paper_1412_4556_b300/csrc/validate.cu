@@ -82,7 +82,7 @@ cudaError_t launch_pad_ids_range(const int32_t *src, const int64_t *off, const i
                                  int64_t t0, int64_t t1, bool last, int4 *dst, int32_t catalog,
                                  bool packed, unsigned long long *bad_count, cudaStream_t s) {
   int64_t blocks = (t1 - t0 + 7) / 8;
-  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks > (int64_t)current_sm_count() * 16) blocks = (int64_t)current_sm_count() * 16;
   if (blocks < 1) blocks = 1;
   if (packed)
     pad_ids_kernel<true><<<(int)blocks, 256, 0, s>>>(src, off, coff, t0, t1, last, dst, catalog, bad_count);
@@ -101,7 +101,7 @@ cudaError_t launch_check_ts(const int64_t *offsets, int64_t n_trials, const floa
                             unsigned long long *bad_count, cudaStream_t s) {
   if (n_trials <= 0) return cudaSuccess;
   int64_t blocks = (n_trials + 7) / 8;
-  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (blocks > (int64_t)current_sm_count() * 8) blocks = (int64_t)current_sm_count() * 8;
   check_ts_kernel<<<(int)blocks, 256, 0, s>>>(offsets, n_trials, ts, bad_count);
   return cudaGetLastError();
 }

@@ -417,7 +417,7 @@ cudaError_t launch_yelt(const int64_t *coff, const int4 *chunks, const int64_t *
                         int device, cudaStream_t s, const ulonglong2 *comb, const unsigned int *inexact) {
   if (n_trials <= 0) return cudaSuccess;
   if (yelt != nullptr && (comb == nullptr || inexact == nullptr)) return cudaErrorInvalidValue;
-  int sms = 148;
+  int sms = 0;
   cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
   const bool out = yelt != nullptr;
@@ -455,7 +455,7 @@ cudaError_t launch_yelt_comb(const void *table, int entry_bytes, const double *t
   if (n_events <= 0) return cudaSuccess;
   if (entry_bytes != 16 && entry_bytes != 8) return cudaErrorInvalidValue;
   int64_t blocks = (n_events + 255) / 256;
-  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (blocks > (int64_t)current_sm_count() * 8) blocks = (int64_t)current_sm_count() * 8;
   yelt_comb_kernel<<<(int)blocks, 256, 0, s>>>(table, entry_bytes, table64, n_events, comb);
   return cudaGetLastError();
 }

@@ -501,7 +501,7 @@ __global__ void interleave_kernel(Tables4 in, int64_t entries, void *__restrict_
 
 cudaError_t launch_interleave(const Tables4 &in, int entry_bytes, int G, int64_t entries, void *out,
                               const Bitmaps4 &bin, int32_t words, uint32_t *bout, cudaStream_t s) {
-  const dim3 grid(148 * 8), block(256);
+  const dim3 grid(current_sm_count() * 8), block(256);
   if (entry_bytes == 16 && G == 2)
     interleave_kernel<16, 2><<<grid, block, 0, s>>>(in, entries, out, bin, words, bout);
   else if (entry_bytes == 8 && G == 2)
