@@ -716,7 +716,7 @@ def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -
 
     cnt = event_counts(w.yet.ids, C)
     gathers = 0.0
-    for eb, g, _lpt, _u, _pf, pos in passes:
+    for eb, g, _lpt, _u, _pf, _th, pos in passes:
         gathers += float(cnt[np.logical_or.reduce(nz[list(pos)])].sum())
     rows = ceil["gather32_rows_per_s"] if any(g > 1 for _, g, *_ in passes) else ceil["gather16_rows_per_s"]
     l1tex = l1tex_roofline(gathers, float(M) * len(passes), ylt_b, rows, ceil)
@@ -754,8 +754,8 @@ def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -
         "yet_layout": yet_layout(compact_ms),
         "l2": "inputs larger than L2 (a 2-2.7 GB YET id stream per pass)",
         "ylt_kernels_ms_per_step": ylt_b,
-        "passes": [{"entry_bytes": eb, "layers": list(pos), "lanes_per_trial": lpt, "unroll": u, "l2_prefetch": pf}
-                   for eb, g, lpt, u, pf, pos in passes],
+        "passes": [{"entry_bytes": eb, "layers": list(pos), "lanes_per_trial": lpt, "unroll": u, "l2_prefetch": pf,
+                    "threads": th} for eb, g, lpt, u, pf, th, pos in passes],
         "calls_per_step": {"ms_per_step": ms_b, "ylt_kernels_ms_per_step": ylt_b,
                            "step": "64 x ara_define_layer + ara_layers_ylt + ara_pml_tvar_batch"},
         "plain_per_layer": {"ms_per_step": ms_p, "ylt_kernels_ms_per_step": ylt_p,

@@ -368,8 +368,8 @@ ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const doub
  * zero-skip bitmaps overlap its union most.  Without autotune a pass holds 2
  * FP64 or 4 FP32-table layers.  With autotune != 0, plan creation first
  * times the YLT kernel's launch shapes (lanes per trial -- the trials a warp
- * sums side by side --, id loads per lane, and whether the id stream is
- * prefetched into L2) and, per entry width, the group size (FP64: 2 or 1
+ * sums side by side --, id loads per lane, whether the id stream is
+ * prefetched into L2, and 1024- or 768-thread CTAs) and, per entry width, the group size (FP64: 2 or 1
  * layers per pass; FP32 tables: 4, 2 or 1) by timing the whole set of passes,
  * on the plan's own layers and the first min(n_trials, 2^20) trials, and
  * keeps the fastest; the launch shapes also serve later ara_layers_ylt /
@@ -397,10 +397,10 @@ ARA_API ara_status ara_plan_run(ara_plan *plan, double *ylt_out, double *pml_out
                                 void *cuda_stream);
 
 /* The plan's YLT passes: *n_passes receives their number and, for the first
- * max_passes, info[9*i .. 9*i+8] = entry bytes (16 FP64, 8 FP32-table),
+ * max_passes, info[10*i .. 10*i+9] = entry bytes (16 FP64, 8 FP32-table),
  * layers in the pass (G), lanes per trial, id loads per lane, L2 prefetch
- * (1/0), and the positions in the plan's layer list of the pass's G layers
- * (then -1 up to four). */
+ * (1/0), threads per CTA, and the positions in the plan's layer list of the
+ * pass's G layers (then -1 up to four). */
 ARA_API ara_status ara_plan_passes(const ara_plan *plan, int32_t max_passes, int32_t *info,
                                    int32_t *n_passes);
 

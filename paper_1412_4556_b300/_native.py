@@ -255,16 +255,16 @@ def ara_plan_run(ctx: int, plan: int, ylt_out: int, pml_out: int, tvar_out: int,
 
 
 def ara_plan_passes(ctx: int, plan: int):
-    """List of (entry bytes, layers G, lanes per trial, unroll, prefetch, (positions of the G layers))
-    per YLT pass."""
+    """List of (entry bytes, layers G, lanes per trial, unroll, prefetch, threads per CTA,
+    (positions of the G layers)) per YLT pass."""
     n = _i32(0)
     _check(ctx, lib.ara_plan_passes(plan, 0, None, C.byref(n)))
-    info = (_i32 * (9 * max(n.value, 1)))()
+    info = (_i32 * (10 * max(n.value, 1)))()
     _check(ctx, lib.ara_plan_passes(plan, n.value, info, C.byref(n)))
     out = []
     for i in range(n.value):
-        eb, g, lpt, u, pf = info[9 * i:9 * i + 5]
-        out.append((eb, g, lpt, u, pf, tuple(info[9 * i + 5:9 * i + 5 + g])))
+        eb, g, lpt, u, pf, th = info[10 * i:10 * i + 6]
+        out.append((eb, g, lpt, u, pf, th, tuple(info[10 * i + 6:10 * i + 6 + g])))
     return out
 
 

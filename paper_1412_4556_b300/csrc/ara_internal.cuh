@@ -248,7 +248,7 @@ cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, doub
 
 struct YltLaunch {
   int blocks;
-  int threads;
+  int threads;          // 1024 (64 registers a thread) or 768 (85)
   size_t smem;
   int unroll;           // 16-byte id loads in flight per lane
   int lanes_per_trial;  // 16 or 32: a warp sums 32 / lanes_per_trial trials at once
@@ -260,6 +260,7 @@ struct YltShape {
   int unroll = 0;
   int lanes_per_trial = 0;
   int prefetch = -1;  // 0 off, 1 on, -1 the planner's choice
+  int threads = 0;    // threads per CTA (1024 or 768; 0 = the planner's choice)
 };
 
 // Per-layer constants and output of one YLT kernel launch.

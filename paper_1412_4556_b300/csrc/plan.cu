@@ -42,12 +42,12 @@ struct ara_plan {
   unsigned int *h_err = nullptr;     // pinned copy of d_err
   std::vector<ara::LayerGroup> groups;  // the YLT passes (positions in layers)
   std::vector<int32_t> pass_info;    // kPassInfo per pass: entry bytes, layers, lanes per trial, unroll, prefetch,
-                                     // the layers' positions (-1 padded to 4)
+                                     // threads per CTA, the layers' positions (-1 padded to 4)
 };
 
 namespace {
 
-constexpr int kPassInfo = 9;
+constexpr int kPassInfo = 10;
 
 void free_plan(ara_plan *p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -104,13 +104,13 @@ ara_status tune_pass(ara_plan *p, const LayerGroup &ps, int64_t n) {
   const size_t table_bytes = ((size_t)c->catalog + 1) * (size_t)(ps.eb * G);
   YltShape best{};
   float best_ms = 1e30f;
-  for (const int lpt : {16, 32})
-    for (const int unroll : {1, 2})
-      for (const int prefetch : {0, 1}) {
+  // every shape: lanes per trial 16/32 x id loads 1/2 x L2 prefetch off/on x 1024/768 threads
+  for (int shape = 0; shape < 16 && e == cudaSuccess; ++shape) {
       YltShape hint;
-      hint.lanes_per_trial = lpt;
-      hint.unroll = unroll;
-      hint.prefetch = prefetch;
+      hint.lanes_per_trial = (shape & 8) ? 32 : 16;
+      hint.unroll = (shape & 4) ? 2 : 1;
+      hint.prefetch = (shape & 2) ? 1 : 0;
+      hint.threads = (shape & 1) ? 768 : 1024;
       YltLaunch cfg;
       e = plan_ylt(c->device, bm, mean_chunks, ys.layout, ps.eb, G, table_bytes, hint, &cfg);
       float ms = 1e30f;
@@ -128,7 +128,7 @@ ara_status tune_pass(ara_plan *p, const LayerGroup &ps, int64_t n) {
       if (e != cudaSuccess) break;
       if (ms < best_ms) {
         best_ms = ms;
-        best = YltShape{cfg.unroll, cfg.lanes_per_trial, cfg.prefetch};
+        best = YltShape{cfg.unroll, cfg.lanes_per_trial, cfg.prefetch, cfg.threads};
       }
     }
   cudaEventDestroy(a);
@@ -297,7 +297,7 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     e = plan_ylt(c->device, bm, mean_chunks, ys.layout, ps.eb, G, ((size_t)c->catalog + 1) * (size_t)(ps.eb * G),
                  c->tuned[ps.eb == 8][G], &cfg);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "plan YLT launch"));
-    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch});
+    p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch, cfg.threads});
     for (int g = 0; g < 4; ++g) p->pass_info.push_back(g < G ? ps.idx[(size_t)g] : -1);
   }
   // Capture: folds, grouped YLT passes, batched selection, result copies.

@@ -263,7 +263,7 @@ ara_status ara_probe_fp64_add(int device, double *adds_per_s) {
   ProbeScope ps;
   if ((e = cudaStreamCreateWithFlags(&ps.s, cudaStreamNonBlocking)) != cudaSuccess) return probe_fail(e, "stream");
   if ((e = cudaMalloc(&ps.buf, 64)) != cudaSuccess) return probe_fail(e, "sink");
-  const int threads = 256, per_sm = 8, iters = 4096;
+  const int threads = 256, per_sm = 8, iters = 512;
   auto launch = [&]() -> cudaError_t {
     probe_dadd_kernel<<<sms * per_sm, threads, 0, ps.s>>>(0.5, iters, static_cast<double *>(ps.buf));
     return cudaGetLastError();

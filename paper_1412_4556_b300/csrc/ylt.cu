@@ -205,8 +205,8 @@ struct GroupOut {
 // one 128-bit accumulator per layer.  A warp sums 32 / LPT consecutive trials
 // side by side, LPT lanes per trial: fewer lanes idle in the last step of a
 // trial, and one group reduction and one epilogue serve 32 / LPT trials.
-template <int U, int LAYOUT, int EB, int G, int LPT>
-__global__ void __launch_bounds__(kYltThreads, 1)
+template <int U, int LAYOUT, int EB, int G, int LPT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
                 int64_t n_trials, const void *__restrict__ table,
                 const uint4 *__restrict__ bitmap4, int bm_words4, uint32_t bm_mul,
@@ -341,11 +341,11 @@ ylt_fp64_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunk
   }
 }
 
-template <int U, int LAYOUT, int EB, int G, int LPT>
+template <int U, int LAYOUT, int EB, int G, int LPT, int THREADS>
 static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
                             const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
                             const YltLaunch &cfg, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, LAYOUT, EB, G, LPT>,
+  cudaError_t err = cudaFuncSetAttribute(ylt_fp64_kernel<U, LAYOUT, EB, G, LPT, THREADS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
   if (err != cudaSuccess) return err;
   int32_t sv[6] = {sentinel, sentinel, sentinel, sentinel, sentinel, sentinel};
@@ -353,33 +353,49 @@ static cudaError_t launch_u(const int64_t *coff, const int4 *chunks, int64_t n_t
   const int4 sentd = delta_sentinel_chunk(sentinel);
   GroupOut<G> go;
   for (int g = 0; g < G; ++g) go.l[g] = outs[g];
-  ylt_fp64_kernel<U, LAYOUT, EB, G, LPT><<<cfg.blocks, cfg.threads, cfg.smem, s>>>(
+  ylt_fp64_kernel<U, LAYOUT, EB, G, LPT, THREADS><<<cfg.blocks, THREADS, cfg.smem, s>>>(
       coff, chunks, n_trials, table, reinterpret_cast<const uint4 *>(bitmap), bm.words / 4, bm.mul, sent4, sentd,
       (uint32_t)sentinel, go, cfg.prefetch);
   return cudaGetLastError();
 }
 
-// The kernel for (unroll, lanes per trial) as a function pointer and as a
-// launch, for one (LAYOUT, EB, G).
+// The kernel for (unroll, lanes per trial, threads per CTA) as a function
+// pointer and as a launch, for one (LAYOUT, EB, G).
 template <int LAYOUT, int EB, int G>
 struct YltVariants {
-  static const void *fn(int unroll, int lpt) {
+  template <int THREADS>
+  static const void *fn_t(int unroll, int lpt) {
     if (lpt == 16)
-      return unroll == 1 ? (const void *)ylt_fp64_kernel<1, LAYOUT, EB, G, 16>
-                         : (const void *)ylt_fp64_kernel<2, LAYOUT, EB, G, 16>;
-    return unroll == 1 ? (const void *)ylt_fp64_kernel<1, LAYOUT, EB, G, 32>
-                       : (const void *)ylt_fp64_kernel<2, LAYOUT, EB, G, 32>;
+      return unroll == 1 ? (const void *)ylt_fp64_kernel<1, LAYOUT, EB, G, 16, THREADS>
+                         : (const void *)ylt_fp64_kernel<2, LAYOUT, EB, G, 16, THREADS>;
+    return unroll == 1 ? (const void *)ylt_fp64_kernel<1, LAYOUT, EB, G, 32, THREADS>
+                       : (const void *)ylt_fp64_kernel<2, LAYOUT, EB, G, 32, THREADS>;
+  }
+  static const void *fn(int unroll, int lpt, int threads) {
+    return threads == 768 ? fn_t<768>(unroll, lpt) : fn_t<1024>(unroll, lpt);
+  }
+  template <int THREADS>
+  static cudaError_t launch_t(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
+                              const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
+                              const YltLaunch &cfg, cudaStream_t s) {
+    if (cfg.lanes_per_trial == 16)
+      return cfg.unroll == 1
+                 ? launch_u<1, LAYOUT, EB, G, 16, THREADS>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
+                                                           cfg, s)
+                 : launch_u<2, LAYOUT, EB, G, 16, THREADS>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
+                                                           cfg, s);
+    return cfg.unroll == 1
+               ? launch_u<1, LAYOUT, EB, G, 32, THREADS>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
+                                                         cfg, s)
+               : launch_u<2, LAYOUT, EB, G, 32, THREADS>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs,
+                                                         cfg, s);
   }
   static cudaError_t launch(const int64_t *coff, const int4 *chunks, int64_t n_trials, const void *table,
                             const uint32_t *bitmap, BitmapLayout bm, int32_t sentinel, const LayerOut *outs,
                             const YltLaunch &cfg, cudaStream_t s) {
-    if (cfg.lanes_per_trial == 16)
-      return cfg.unroll == 1
-                 ? launch_u<1, LAYOUT, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
-                 : launch_u<2, LAYOUT, EB, G, 16>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
-    return cfg.unroll == 1
-               ? launch_u<1, LAYOUT, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s)
-               : launch_u<2, LAYOUT, EB, G, 32>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    if (cfg.threads == 768)
+      return launch_t<768>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
+    return launch_t<1024>(coff, chunks, n_trials, table, bitmap, bm, sentinel, outs, cfg, s);
   }
 };
 
@@ -413,7 +429,9 @@ struct LaunchF {
 
 template <int LAYOUT, int EB, int G>
 struct FnF {
-  static const void *call(int unroll, int lpt) { return YltVariants<LAYOUT, EB, G>::fn(unroll, lpt); }
+  static const void *call(int unroll, int lpt, int threads) {
+    return YltVariants<LAYOUT, EB, G>::fn(unroll, lpt, threads);
+  }
 };
 
 cudaError_t launch_ylt_group(const int64_t *coff, const int4 *chunks, int layout, int64_t n_trials,
@@ -461,17 +479,23 @@ cudaError_t plan_ylt(int device, const BitmapLayout &bm, double mean_chunks, int
     int l = std::atoi(env);
     if (l == 16 || l == 32) lpt = l;
   }
-  out->threads = kYltThreads;
+  int threads = kYltThreads;
+  if (hint.threads == 768 || hint.threads == 1024) threads = hint.threads;
+  if (const char *env = std::getenv("ARA_YLT_THREADS")) {
+    int t = std::atoi(env);
+    if (t == 768 || t == 1024) threads = t;
+  }
+  out->threads = threads;
   out->smem = (size_t)bm.words * 4u;
   out->unroll = unroll;
   out->lanes_per_trial = lpt;
   out->prefetch = prefetch;
   if (layout < 0 || layout > 2) return cudaErrorInvalidValue;
-  const void *fn = dispatch<FnF>(layout, entry_bytes, G, unroll, lpt);
+  const void *fn = dispatch<FnF>(layout, entry_bytes, G, unroll, lpt, threads);
   err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kYltThreads, out->smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, out->smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) per_sm = 1;
   out->blocks = sms * per_sm;

@@ -48,10 +48,10 @@ def test_plan_equals_direct_calls(engine, autotune):
     # every layer in exactly one pass, of its own entry width
     pos = sorted(i for *_, ps in passes for i in ps)
     assert pos == list(range(len(hs)))
-    for eb, g, lpt, u, pf, ps in passes:
+    for eb, g, lpt, u, pf, th, ps in passes:
         assert len(ps) == g and all((eb == 16) == (precs[i] == ARA_FP64) for i in ps)
         assert (eb, g) in ((16, 1), (16, 2), (8, 1), (8, 2), (8, 4))
-        assert lpt in (16, 32) and u in (1, 2) and pf in (0, 1)
+        assert lpt in (16, 32) and u in (1, 2) and pf in (0, 1) and th in (768, 1024)
     if not autotune:
         # the largest groups: 4 FP64 layers -> 2 passes of 2; 3 FP32-table layers -> 2 + 1
         assert sorted((eb, g) for eb, g, *_ in passes) == [(8, 1), (8, 2), (16, 2), (16, 2)]
