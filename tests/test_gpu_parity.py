@@ -268,6 +268,26 @@ def test_invalid_inputs_are_rejected_with_status(engine):
     assert engine.layer_ylt(L).shape == (1,)
 
 
+def test_entry_points_refuse_another_gpus_memory(engine):
+    """Device memory of a GPU other than the context's is refused with a
+    status before anything is queued (its kernels could not read it); needs
+    a second GPU."""
+    import torch
+    from paper_1412_4556_b300 import AraError
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU: no memory of another device to pass")
+    w = S.tiny(n_trials=200)
+    (L,) = load_workload(engine, w)
+    other = torch.ones(200, dtype=torch.float64, device="cuda:1")
+    for call in (lambda: engine.pml_tvar(other, [10.0]), lambda: engine.layer_ylt(L, out=other),
+                 lambda: engine.ylt_tail(other, 5)):
+        with pytest.raises(AraError) as ei:
+            call()
+        assert ei.value.name == "ARA_E_INVALID_ARG" and "another GPU" in str(ei.value)
+    # the context still works
+    assert engine.layer_ylt(L).shape == (200,)
+
+
 # The full paper-scale workload (every trial against the oracle) is in
 # test_gpu_fullsize.py.
 
