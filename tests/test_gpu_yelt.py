@@ -167,9 +167,11 @@ def test_invalid_arguments(engine):
         engine.layer_yelt(L, n_trials=201)
 
 
-def test_paper_scale_full_size_sampled():
+def test_paper_scale_full_size_every_occurrence():
     """The full YELT of the paper-scale workload (~1e9 occurrences, 8 GB on
-    the device); sampled trials against the oracle one by one."""
+    the device): every increment and every trial maximum against the
+    oracle's YELT, the YLT against the oracle's, and the AEP/OEP report
+    against the oracle's return period losses."""
     import torch
     from paper_1412_4556_b300 import Engine
     w = S.paper_scale()
@@ -185,21 +187,28 @@ def test_paper_scale_full_size_sampled():
         ylt = e.layer_ylt(L)
         rep = e.rpl_report(L, w.return_periods)
         torch.cuda.synchronize()
+        g_inc = d_inc.cpu().numpy()
         occ_max = d_max.cpu().numpy()
-        rng = np.random.default_rng(4)
-        sel = np.unique(np.concatenate([rng.choice(w.yet.n_trials, 400, replace=False),
-                                        [0, w.yet.n_trials - 1], np.argsort(ylt)[-20:]]))
-        idx = np.concatenate([np.arange(w.yet.offsets[t], w.yet.offsets[t + 1]) for t in sel])
-        g_inc = d_inc[torch.from_numpy(idx).cuda()].cpu().numpy()
         del d_inc
-    o_inc, out_off, o_max, o_ylt, pre = oracle.layer_yelt(w.yet, w.pool, lay, trials=sel)
-    assert_yelt_parity(g_inc, occ_max[sel], o_inc, out_off, o_max, pre, FP64_REL)
-    s = np.sort(occ_max)[::-1]
-    for r, p in zip(w.return_periods, rep["oep"]):
-        assert p == s[int(math.floor(occ_max.size / r)) - 1]
-    sy = np.sort(ylt)[::-1]
-    for r, p in zip(w.return_periods, rep["aep"]):
-        assert p == sy[int(math.floor(ylt.size / r)) - 1]
+    o_inc, out_off, o_max, o_ylt, pre = oracle.layer_yelt(w.yet, w.pool, lay)
+    np.testing.assert_array_equal(out_off, w.yet.offsets)
+    # every occurrence, a block of trials at a time (bounded temporaries)
+    step = 50_000
+    for t0 in range(0, w.yet.n_trials, step):
+        t1 = min(w.yet.n_trials, t0 + step)
+        a, b = int(out_off[t0]), int(out_off[t1])
+        assert_yelt_parity(g_inc[a:b], occ_max[t0:t1], o_inc[a:b], out_off[t0:t1 + 1] - a, o_max[t0:t1],
+                           pre[t0:t1], FP64_REL, what=f"trials {t0}..{t1}")
+    rep_y = oracle.compare_fp64(ylt, o_ylt, pre)
+    assert rep_y["trials_over_r9_bar"] == 0, rep_y
+    # AEP and OEP return period losses against the oracle's (1-Lipschitz in
+    # the per-trial values)
+    for key_p, key_t, g_vals, o_vals in (("aep", "aep_tvar", ylt, o_ylt), ("oep", "oep_tvar", occ_max, o_max)):
+        p_o, t_o = oracle.pml_tvar(o_vals, w.return_periods)
+        pt = oracle.compare_pml_tvar(rep[key_p], rep[key_t], p_o, t_o, w.return_periods, g_vals.size,
+                                     float(np.max(np.abs(g_vals - o_vals))))
+        assert pt["within_bound"], (key_p, pt)
+    print(f"\nfull-size YELT: {M} occurrences, max |error| {float(np.max(np.abs(g_inc - o_inc))):.3e} USD")
 
 
 def _inside_increments_check(yelt, table, yet):
