@@ -482,11 +482,25 @@ ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g
                             std::vector<LayerGroup> *out) {
   out->clear();
   if (Ls.empty()) return ARA_OK;
-  const size_t words64 = (size_t)Ls[0]->bm.words / 2;  // bitmaps hold a multiple of 4 words
+  // Up to 128 layers every bitmap word takes part; beyond that a strided
+  // sample of the words (every stride-th 64-bit word: overlaps estimated on
+  // a sample), and each layer is compared with at most kWindow candidates,
+  // the next ones in density order, so the host work stays near 1e8 word
+  // operations however many layers a plan has.
+  constexpr size_t kWindow = 64;
+  const size_t full64 = (size_t)Ls[0]->bm.words / 2;  // bitmaps hold a multiple of 4 words
+  const size_t stride = Ls.size() <= 128 ? 1 : (Ls.size() + 127) / 128;
+  const size_t words64 = (full64 + stride - 1) / stride;
   std::vector<uint64_t> bits(Ls.size() * words64);
-  for (size_t i = 0; i < Ls.size(); ++i)
-    ARA_CUDA(c, cudaMemcpyAsync(bits.data() + i * words64, Ls[i]->d_bitmap, words64 * 8, cudaMemcpyDeviceToHost, s),
-             "copy zero-skip bitmap");
+  for (size_t i = 0; i < Ls.size(); ++i) {
+    uint64_t *dst = bits.data() + i * words64;
+    if (stride == 1)
+      ARA_CUDA(c, cudaMemcpyAsync(dst, Ls[i]->d_bitmap, words64 * 8, cudaMemcpyDeviceToHost, s),
+               "copy zero-skip bitmap");
+    else
+      ARA_CUDA(c, cudaMemcpy2DAsync(dst, 8, Ls[i]->d_bitmap, 8 * stride, 8, words64, cudaMemcpyDeviceToHost, s),
+               "copy zero-skip bitmap sample");
+  }
   ARA_CUDA(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
   auto row = [&](size_t i) { return bits.data() + i * words64; };
   std::vector<int64_t> pop(Ls.size(), 0);
@@ -506,7 +520,7 @@ ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g
       while ((int)g.size() < gmax && !left.empty()) {
         size_t best = 0;
         int64_t best_ov = -1;
-        for (size_t k = 0; k < left.size(); ++k) {
+        for (size_t k = 0; k < std::min(left.size(), kWindow); ++k) {
           const uint64_t *b = row((size_t)left[k]);
           int64_t ov = 0;
           for (size_t w = 0; w < words64; ++w) ov += __builtin_popcountll(uni[w] & b[w]);

@@ -267,9 +267,11 @@ std::vector<LayerGroup> group_in_order(const std::vector<LayerRec *> &Ls, int g1
 
 // Passes whose layers share most of their possibly nonzero events: layers
 // taken densest first, each pass filled with the layers whose zero-skip
-// bitmaps overlap its union most (bitmaps copied to the host on stream s).
-// A pass gathers one table row for every occurrence that any of its layers
-// needs, so overlapping layers gather fewer rows.  g16 / g8 as above.
+// bitmaps overlap its union most (bitmaps copied to the host on stream s;
+// among the next 64 layers in density order, on a sample of the bitmap words
+// beyond 128 layers).  A pass gathers one table row for every occurrence
+// that any of its layers needs, so overlapping layers gather fewer rows.
+// g16 / g8 as above.
 ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g16, int g8, cudaStream_t s,
                             std::vector<LayerGroup> *out);
 

@@ -139,7 +139,7 @@ ara_status tune_pass(ara_plan *p, const LayerGroup &ps, int64_t n) {
 }
 
 // Milliseconds of the passes `groups` over the first n trials (best of two
-// after a warm-up run).
+// after a warm-up run; one after the warm-up beyond 64 passes).
 ara_status time_groups(ara_plan *p, const std::vector<LayerGroup> &groups, int64_t n, float *ms_out) {
   ara_ctx *c = p->c;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -147,7 +147,8 @@ ara_status time_groups(ara_plan *p, const std::vector<LayerGroup> &groups, int64
   cudaError_t e = cudaEventCreate(&b);
   ara_status st = e == cudaSuccess ? ARA_OK : cuda_fail(c, e, "cudaEventCreate");
   float best = 1e30f;
-  for (int rep = 0; rep < 3 && st == ARA_OK; ++rep) {
+  const int reps = groups.size() > 64 ? 2 : 3;
+  for (int rep = 0; rep < reps && st == ARA_OK; ++rep) {
     if ((e = cudaEventRecord(a, p->cap)) != cudaSuccess) {
       st = cuda_fail(c, e, "cudaEventRecord");
       break;
@@ -169,9 +170,9 @@ ara_status time_groups(ara_plan *p, const std::vector<LayerGroup> &groups, int64
 
 // The plan's passes with the autotuner: for each entry width, every group
 // size the kernel has (FP64: 2 or 1 layers per pass; FP32 tables: 4, 2 or
-// 1), layers grouped by overlap, launch shapes tuned per group size, and the
-// whole set of passes of that width timed on the first n trials; the
-// fastest group size per width is kept.
+// 1), layers grouped by overlap, launch shapes tuned per group size on the
+// first n trials, and the whole set of passes of that width timed on the
+// first min(n, 2^18) trials; the fastest group size per width is kept.
 ara_status choose_groups(ara_plan *p, const std::vector<LayerRec *> &Ls, int64_t n, std::vector<LayerGroup> *out) {
   ara_ctx *c = p->c;
   out->clear();
@@ -198,7 +199,7 @@ ara_status choose_groups(ara_plan *p, const std::vector<LayerRec *> &Ls, int64_t
         if ((st = tune_pass(p, g, n)) != ARA_OK) return st;
       }
       float ms = 0.f;
-      if ((st = time_groups(p, mine, n, &ms)) != ARA_OK) return st;
+      if ((st = time_groups(p, mine, std::min<int64_t>(n, 1 << 18), &ms)) != ARA_OK) return st;
       if (ms < best_ms) {
         best_ms = ms;
         best = mine;

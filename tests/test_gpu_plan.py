@@ -98,3 +98,26 @@ def test_plan_invalidated_by_release_and_reload(engine):
     Plan(engine, [hs[0]], RPS)
     engine.close()
     assert not engine._plans
+
+
+def test_plan_with_many_layers_groups_each_layer_once(engine):
+    """200 layers (beyond 128 the grouping compares layers on a sample of the
+    bitmap words): every layer in exactly one pass, the plan's bits equal the
+    direct call's, and the first FP64 layers match the oracle."""
+    from paper_1412_4556_b300 import ARA_FP64, Plan
+    n = 200
+    w, hs, precs = setup(engine, n_layers=n, n_trials=1_500)
+    direct = engine.layers_ylt(hs)
+    with Plan(engine, hs, RPS, autotune=False) as plan:
+        y = np.empty_like(direct)
+        plan.run(ylt_out=y)
+        passes = plan.passes()
+    np.testing.assert_array_equal(y.view(np.uint64), direct.view(np.uint64))
+    pos = sorted(i for *_, ps in passes for i in ps)
+    assert pos == list(range(n))
+    # 100 FP64 layers in 50 pairs, 100 FP32-table layers in 25 fours
+    assert sum(1 for eb, g, *rest in passes if eb == 16 and g == 2) == 50
+    assert sum(1 for eb, g, *rest in passes if eb == 8 and g == 4) == 25
+    for i in [i for i, p in enumerate(precs) if p == ARA_FP64][:2]:
+        o, pre = oracle.layer_ylt(w.yet, w.pool, w.layers[i], mode="memo")
+        assert_fp64_parity(direct[i], o, pre, what=f"layer {i}")
