@@ -497,11 +497,18 @@ def run_engine(args):
     parity = oracle_parity(w, g, res[0], res[1]) if world == 1 and not args.no_parity else None
     nested = {}
     if world == 1 and not args.no_nested:
+        # a failure in one of the other configs is reported in its key and
+        # does not take the headline line down with it
+        def guarded(fn):
+            try:
+                return fn()
+            except Exception as exc:  # noqa: BLE001
+                return {"error": f"{type(exc).__name__}: {exc}"}
         bw = S.batched(yet=w.yet)
-        nested["batched"] = batched_result(args, bw, mixed=False, ceil=ceil)
-        nested["mixed"] = batched_result(args, bw, mixed=True, ceil=ceil)
+        nested["batched"] = guarded(lambda: batched_result(args, bw, mixed=False, ceil=ceil))
+        nested["mixed"] = guarded(lambda: batched_result(args, bw, mixed=True, ceil=ceil))
         del bw
-        nested["service"] = service_result(args, S.batched(n_layers=1, yet=w.yet), nested=True)
+        nested["service"] = guarded(lambda: service_result(args, S.batched(n_layers=1, yet=w.yet), nested=True))
     cpu = oracle_sample(w, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
     if cpu:
         for key in ("seconds", "trials", "occurrences"):
