@@ -225,29 +225,35 @@ def test_context_is_owned_while_attached_and_checks_at_submit(workload):
     assert svc.svc == 0
 
 
-def test_service_full_size_requests_sampled():
+def test_service_full_size_requests_every_trial():
     """Config 4 shapes at full size: requests over 1e5 / 2.5e5 / 1e6-trial
     prefixes of the paper-scale YET with the 256-ELT pool, FP32 tables, all
-    submitted at once; sampled trials against the oracle; and each result
-    equals the same request priced alone."""
+    submitted at once; every trial of five of them (one of 2.5e5 trials, one
+    of 1e5, three of 1e6) and their PML/TVaR against the oracle; and each of
+    those results equals the same request priced alone."""
     from paper_1412_4556_b300 import ARA_FP32_TABLE, Engine, Service
     w = S.batched(n_layers=1)
     reqs = S.service_requests(n_requests=24, rate_per_s=1000.0)
+    checked = (0, 5, 10, 16, 21)
     with Engine(0) as e:
         e.load_yet_from(w.yet)
         first = e.load_pool(w.pool)
         with Service(e, RPS, slots=4, max_batch=8) as svc:
-            tickets = [submit(svc, first, rq, ARA_FP32_TABLE, want_ylt=(i % 6 == 0)) for i, rq in enumerate(reqs)]
+            tickets = [submit(svc, first, rq, ARA_FP32_TABLE, want_ylt=i in checked)
+                       for i, rq in enumerate(reqs)]
             mixed = [svc.wait(t) for t in tickets]
-            alone = [svc.wait(submit(svc, first, reqs[i], ARA_FP32_TABLE, want_ylt=True)) for i in range(0, 24, 6)]
+            alone = [svc.wait(submit(svc, first, reqs[i], ARA_FP32_TABLE, want_ylt=True)) for i in checked]
     assert all(r.ok for r in mixed + alone)
-    rng = np.random.default_rng(6)
-    for a, i in zip(alone, range(0, 24, 6)):
+    assert sorted({reqs[i].n_trials for i in checked}) == [100_000, 250_000, 1_000_000]
+    for a, i in zip(alone, checked):
         m = mixed[i]
         np.testing.assert_array_equal(m.ylt.view(np.uint64), a.ylt.view(np.uint64))
         np.testing.assert_array_equal(m.pml, a.pml)
+        np.testing.assert_array_equal(m.tvar, a.tvar)
         rq = reqs[i]
-        sel = np.sort(rng.choice(rq.n_trials, 300, replace=False))
-        o, pre = oracle.layer_ylt(w.yet, w.pool, rq.layer, trials=sel, mode="memo")
-        err = np.abs(m.ylt[sel] - o)
-        assert np.all(err <= np.maximum(1e-5 * np.maximum(np.abs(o), pre), 1.0)), f"request {i}"
+        o, pre = oracle.layer_ylt(w.yet, w.pool, rq.layer, trials=np.arange(rq.n_trials), mode="memo")
+        rep = oracle.compare_reduced(m.ylt, o, pre)
+        assert rep["trials_over_bar"] == 0, (i, rep)
+        p_o, t_o = oracle.pml_tvar(o, RPS)
+        pt = oracle.compare_pml_tvar(m.pml, m.tvar, p_o, t_o, RPS, rq.n_trials, rep["max_abs_err"])
+        assert pt["within_bound"], (i, pt)
