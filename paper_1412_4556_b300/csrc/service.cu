@@ -479,8 +479,10 @@ ara_status ara_service_create(ara_ctx *c, const ara_service_config *cfg, ara_ser
   // Reserve up front what a full load of requests over all loaded trials
   // needs (as far as the budget covers it), so that requests do not wait on
   // cudaMalloc: layer buffers in the context's pool, and each slot's YLT,
-  // selection and paired-table scratch.  The pinned YLT copies for requests
-  // that ask for their YLT grow on first use.
+  // selection and paired-table scratch, and pinned room for one YLT over all
+  // loaded trials (a request that asks for its YLT would otherwise pin pages
+  // inside the scheduler thread, which holds up every other launch; batches
+  // with several such requests grow it on first use).
   const size_t per = svc->request_bytes(64, c->n_trials);
   const size_t n_res = std::min<size_t>((size_t)cfg->slots * (size_t)cfg->max_batch,
                                         (size_t)svc->cfg.memory_budget / std::max<size_t>(per, 1));
@@ -494,6 +496,7 @@ ara_status ara_service_create(ara_ctx *c, const ara_service_config *cfg, ara_ser
     if (e == cudaSuccess) e = ensure(&sl.d_out, &sl.cap_out, per_slot * 2 * kMaxReturnPeriods);
     if (e == cudaSuccess) e = ensure(&sl.d_err, &sl.cap_err, 1);
     if (e == cudaSuccess) e = ensure_pinned(&sl.h_out, &sl.cap_h_out, per_slot * 2 * kMaxReturnPeriods);
+    if (e == cudaSuccess) e = ensure_pinned(&sl.h_ylt, &sl.cap_h_ylt, (size_t)c->n_trials);
     if (e == cudaSuccess && per_slot > 1) e = ensure(&sl.d_pair, &sl.cap_pair, 2 * ((size_t)c->catalog + 1));
     if (e == cudaSuccess && per_slot > 1) e = ensure(&sl.d_pair_bm, &sl.cap_pair_bm, layer_bitmap_bytes(c) / 4);
     if (e != cudaSuccess) st = fail_free(ARA_E_NOMEM, "service reservation: %s", cudaGetErrorString(e));
