@@ -59,6 +59,9 @@ __global__ void select_init_kernel(SelState *states, KArgs ka, int n_rp) {
   }
 }
 
+// FAST: at most four return periods, whose distinct prefixes are compared in
+// registers; otherwise they are read from shared memory.
+template <bool FAST>
 __global__ void __launch_bounds__(kSelectThreads, 4)
 select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pass,
                    SelState *states, unsigned int *err) {
@@ -66,26 +69,61 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   SelState *st = states + blockIdx.y;
   __shared__ unsigned int sh[kMaxReturnPeriods][256];
   __shared__ unsigned long long s_prefix[kMaxReturnPeriods];
+  __shared__ unsigned long long s_pre[kMaxReturnPeriods];  // distinct prefixes, above the current digit
+  __shared__ int s_slot[kMaxReturnPeriods];                // return period -> its prefix's histogram
+  __shared__ int s_nslots;
   __shared__ bool s_last;
   const int tid = threadIdx.x;
   for (int i = tid; i < n_rp * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
   if (tid < n_rp) s_prefix[tid] = st->prefix[tid];
   __syncthreads();
   const int shift = 56 - 8 * pass;
+  // Return periods whose thresholds share the prefix chosen so far (all of
+  // them in the first pass) count into one histogram, so a key takes at most
+  // one shared-memory atomic: the distinct prefixes select disjoint keys.
+  if (tid == 0) {
+    int ns = 0;
+    for (int r = 0; r < n_rp; ++r) {
+      const unsigned long long pr = pass == 0 ? 0ull : s_prefix[r] >> (shift + 8);
+      int sl = -1;
+      for (int q = 0; q < ns; ++q)
+        if (s_pre[q] == pr) sl = q;
+      if (sl < 0) {
+        s_pre[ns] = pr;
+        sl = ns++;
+      }
+      s_slot[r] = sl;
+    }
+    s_nslots = ns;
+  }
+  __syncthreads();
+  const int ns = s_nslots;
+  unsigned long long pre[4] = {0ull, 0ull, 0ull, 0ull};
+  if constexpr (FAST) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pre[q] = q < ns ? s_pre[q] : ~0ull;
+  }
   unsigned long long local_max = 0ull;
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   auto take = [&](double v) {
     const unsigned long long key = (unsigned long long)__double_as_longlong(v);
+    const unsigned int d = (unsigned int)(key >> shift) & 255u;
     if (pass == 0) {
       bad |= key >= 0x7FF0000000000000ull;  // negative, infinite or NaN
       local_max = key > local_max ? key : local_max;
+      atomicAdd(&sh[0][d], 1u);
+      return;
     }
-    const unsigned int d = (unsigned int)(key >> shift) & 255u;
-    for (int r = 0; r < n_rp; ++r) {
-      const bool match = pass == 0 || ((key ^ s_prefix[r]) >> (shift + 8)) == 0ull;
-      if (match) atomicAdd(&sh[r][d], 1u);
+    const unsigned long long kp = key >> (shift + 8);
+    int sl = -1;
+    if constexpr (FAST) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sl = kp == pre[q] ? q : sl;
+    } else {
+      for (int q = 0; q < ns; ++q) sl = kp == s_pre[q] ? q : sl;
     }
+    if (sl >= 0) atomicAdd(&sh[sl][d], 1u);
   };
   // Four independent loads in flight per thread: one load at a time leaves
   // a pass over a many-layer batch (hundreds of MB) latency-bound.
@@ -108,7 +146,7 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   }
   __syncthreads();
   for (int i = tid; i < n_rp * 256; i += blockDim.x) {
-    const unsigned int c = (&sh[0][0])[i];
+    const unsigned int c = sh[s_slot[i >> 8]][i & 255];
     if (c) atomicAdd(&st->hist[0][0] + i, c);
   }
   __threadfence();
@@ -349,8 +387,12 @@ cudaError_t launch_pml_tvar_batch(const double *ylts, int n_layers, int64_t n, c
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   for (int pass = 0; pass < 8; ++pass) {
-    select_pass_kernel<<<dim3((unsigned)blocks, (unsigned)n_layers), kSelectThreads, 0, s>>>(
-        ylts, n, n_rp, pass, st, err_flag);
+    if (n_rp <= 4)
+      select_pass_kernel<true><<<dim3((unsigned)blocks, (unsigned)n_layers), kSelectThreads, 0, s>>>(
+          ylts, n, n_rp, pass, st, err_flag);
+    else
+      select_pass_kernel<false><<<dim3((unsigned)blocks, (unsigned)n_layers), kSelectThreads, 0, s>>>(
+          ylts, n, n_rp, pass, st, err_flag);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
