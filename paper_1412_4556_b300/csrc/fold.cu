@@ -21,9 +21,11 @@
 // entries on a grid chosen so that no trial sum reaches 2^64: half the table
 // bytes; rounding to that grid moves a trial sum by less than its length x
 // 2^(q-1), far below the binary32 rounding of the values themselves.
+#include <algorithm>
 #include <type_traits>
 
 #include "ara_internal.cuh"
+#include "fold_batch.h"
 
 namespace ara {
 
@@ -43,25 +45,33 @@ __device__ __forceinline__ float elt_terms32(double loss, double deductible, dou
 // fits in one round).
 constexpr int kStage = 1024;
 
-// FP32 = true: combine and apply occurrence terms in binary32 (the table then
-// holds binary32 values, exactly representable in the fixed-point grid).
+// Shared memory of one fold CTA: the running sums of its events and one
+// round of staged ELT entries.
+template <typename Real>
+struct FoldSmem {
+  Real x[kFoldEventsPerCta];
+  uint16_t st_off[kStage];
+  Real st_val[kStage];
+};
+
+// One CTA's fold of catalog events [b * kFoldEventsPerCta, ...).  FP32 = true:
+// combine and apply occurrence terms in binary32 (the table then holds
+// binary32 values, exactly representable in the fixed-point grid).  s_dyn:
+// 2 * n_elts + 1 ints of dynamic shared memory.
 template <bool FP32>
-__global__ void __launch_bounds__(kFoldThreads)
-fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
-            double occ_lim, int q, void *__restrict__ table, uint32_t *__restrict__ bitmap,
-            uint32_t bm_mul, double *__restrict__ f64_out, unsigned int *__restrict__ inexact) {
+__device__ __forceinline__ void fold_body(
+    FoldSmem<typename std::conditional<FP32, float, double>::type> &sm, int32_t *s_dyn, int b,
+    const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret, double occ_lim, int q,
+    void *__restrict__ table, uint32_t *__restrict__ bitmap, uint32_t bm_mul, double *__restrict__ f64_out,
+    unsigned int *__restrict__ inexact) {
   using Real = typename std::conditional<FP32, float, double>::type;
-  __shared__ Real x[kFoldEventsPerCta];
-  __shared__ uint16_t st_off[kStage];
-  __shared__ Real st_val[kStage];
-  // sized by the layer (n_elts + 1 and n_elts entries), so that a CTA of a
-  // typical layer needs little shared memory and the whole grid is resident
-  extern __shared__ int32_t s_dyn[];
+  Real *x = sm.x;
+  uint16_t *st_off = sm.st_off;
+  Real *st_val = sm.st_val;
   int32_t *seg = s_dyn;                // prefix sums of slice lengths
   int32_t *first = s_dyn + n_elts + 1;  // slice start inside ELT j
 
   const int tid = threadIdx.x;
-  const int b = blockIdx.x;
   const int32_t e0 = b * kFoldEventsPerCta;
 
   for (int i = tid; i < kFoldEventsPerCta; i += kFoldThreads) x[i] = Real(0);
@@ -148,6 +158,48 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
   }
 }
 
+
+template <bool FP32>
+__global__ void __launch_bounds__(kFoldThreads)
+fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret,
+            double occ_lim, int q, void *__restrict__ table, uint32_t *__restrict__ bitmap,
+            uint32_t bm_mul, double *__restrict__ f64_out, unsigned int *__restrict__ inexact) {
+  using Real = typename std::conditional<FP32, float, double>::type;
+  __shared__ FoldSmem<Real> sm;
+  // sized by the layer (n_elts + 1 and n_elts entries), so that a CTA of a
+  // typical layer needs little shared memory and the whole grid is resident
+  extern __shared__ int32_t s_dyn[];
+  fold_body<FP32>(sm, s_dyn, blockIdx.x, elts, n_elts, catalog, occ_ret, occ_lim, q, table, bitmap, bm_mul,
+                  f64_out, inexact);
+}
+
+// Many layers' folds in one launch (grid.y = layer): the CTAs of all the
+// layers are resident together, where one launch per layer leaves each
+// layer's short dependent chains to run on an otherwise idle GPU.
+__global__ void __launch_bounds__(kFoldThreads)
+fold_batch_kernel(const FoldJob *__restrict__ jobs, int32_t catalog) {
+  __shared__ __align__(16) unsigned char raw[sizeof(FoldSmem<double>)];
+  extern __shared__ int32_t s_dyn[];
+  const FoldJob j = jobs[blockIdx.y];
+  if (j.fp32)
+    fold_body<true>(*reinterpret_cast<FoldSmem<float> *>(raw), s_dyn, blockIdx.x, j.elts, j.n_elts, catalog,
+                    j.occ_ret, j.occ_lim, j.q, j.table, j.bitmap, j.bm_mul, nullptr, nullptr);
+  else
+    fold_body<false>(*reinterpret_cast<FoldSmem<double> *>(raw), s_dyn, blockIdx.x, j.elts, j.n_elts, catalog,
+                     j.occ_ret, j.occ_lim, j.q, j.table, j.bitmap, j.bm_mul, nullptr, nullptr);
+}
+
+// Before a batch of folds: every layer's bitmap cleared and its sentinel
+// entry (id = catalog) zeroed at the layer's entry width.
+__global__ void fold_clear_kernel(const FoldJob *__restrict__ jobs, int32_t catalog, int32_t words) {
+  const FoldJob j = jobs[blockIdx.y];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) j.bitmap[i] = 0u;
+  const int per = j.fp32 ? 1 : 2;  // 64-bit words of one entry
+  if (blockIdx.x == 0 && (int)threadIdx.x < per)
+    static_cast<unsigned long long *>(j.table)[(size_t)catalog * per + threadIdx.x] = 0ull;
+}
+
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,
                         double occ_lim, int q, void *table, uint32_t *bitmap,
                         BitmapLayout bm, bool fp32, double *f64_out, cudaStream_t s, unsigned int *inexact) {
@@ -160,6 +212,19 @@ cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, doub
   else
     fold_kernel<false><<<blocks, kFoldThreads, dyn, s>>>(d_elts, n_elts, catalog, occ_ret, occ_lim, q,
                                                           table, bitmap, bm.mul, f64_out, inexact);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_batch(const FoldJob *d_jobs, int n_jobs, int max_elts, int32_t catalog, int32_t words,
+                              cudaStream_t s) {
+  if (catalog <= 0 || n_jobs <= 0) return cudaSuccess;
+  const int sms = current_sm_count();
+  fold_clear_kernel<<<dim3((unsigned)std::max(1, sms / 4), (unsigned)n_jobs), 256, 0, s>>>(d_jobs, catalog, words);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int blocks = (catalog + kFoldEventsPerCta - 1) / kFoldEventsPerCta;
+  const size_t dyn = (2 * (size_t)max_elts + 1) * sizeof(int32_t);
+  fold_batch_kernel<<<dim3((unsigned)blocks, (unsigned)n_jobs), kFoldThreads, dyn, s>>>(d_jobs, catalog);
   return cudaGetLastError();
 }
 

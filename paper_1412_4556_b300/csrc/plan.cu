@@ -18,6 +18,7 @@
 #include "ara.h"
 #include "ara_ctx.h"
 #include "ara_internal.cuh"
+#include "fold_batch.h"
 
 using namespace ara;
 
@@ -40,6 +41,8 @@ struct ara_plan {
   unsigned int *d_err = nullptr;
   double *h_out = nullptr;           // pinned copy of d_out
   unsigned int *h_err = nullptr;     // pinned copy of d_err
+  FoldJob *d_jobs = nullptr;         // every layer's fold, launched as one batch
+  int max_elts = 0;
   std::vector<ara::LayerGroup> groups;  // the YLT passes (positions in layers)
   std::vector<int32_t> pass_info;    // kPassInfo per pass: entry bytes, layers, lanes per trial, unroll, prefetch,
                                      // threads per CTA, the layers' positions (-1 padded to 4)
@@ -62,6 +65,7 @@ void free_plan(ara_plan *p) {
   cudaFree(p->d_ws);
   cudaFree(p->d_out);
   cudaFree(p->d_err);
+  cudaFree(p->d_jobs);
   cudaFreeHost(p->h_out);
   cudaFreeHost(p->h_err);
   cudaGetLastError();
@@ -301,12 +305,27 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     p->pass_info.insert(p->pass_info.end(), {ps.eb, G, cfg.lanes_per_trial, cfg.unroll, cfg.prefetch, cfg.threads});
     for (int g = 0; g < 4; ++g) p->pass_info.push_back(g < G ? ps.idx[(size_t)g] : -1);
   }
+  // The folds of every layer as one batch (the layers' folds at creation
+  // fixed their exponents; the batch writes the same tables).
+  std::vector<FoldJob> jobs;
+  for (const LayerRec *L : Ls) {
+    jobs.push_back(FoldJob{L->d_desc, (int32_t)L->elts.size(), L->q, L->occ_ret, L->occ_lim, L->d_table, L->d_bitmap,
+                           L->bm.mul, L->precision == ARA_FP32_TABLE ? 1 : 0});
+    p->max_elts = std::max(p->max_elts, (int)L->elts.size());
+  }
+  if ((e = cudaMalloc(&p->d_jobs, jobs.size() * sizeof(FoldJob))) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_jobs, jobs.data(), jobs.size() * sizeof(FoldJob), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(c, ARA_E_NOMEM, "plan fold list: %s", cudaGetErrorString(e)));
+  }
   // Capture: folds, grouped YLT passes, batched selection, result copies.
   const bool timing = c->timing;
   c->timing = false;
   e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
   ara_status st = e == cudaSuccess ? ARA_OK : cuda_fail(c, e, "cudaStreamBeginCapture");
-  for (size_t i = 0; i < nl && st == ARA_OK; ++i) st = enqueue_fold(c, c->layers[(size_t)p->layers[i]], p->cap);
+  if (st == ARA_OK && (e = launch_fold_batch(p->d_jobs, n_layers, p->max_elts, c->catalog, bm.words, p->cap)) !=
+                          cudaSuccess)
+    st = cuda_fail(c, e, "fold kernels");
   if (st == ARA_OK)
     st = layers_ylt_on(c, p->layers.data(), n_layers, n_trials, p->d_ylt, p->cap, p->d_pair, p->d_pair_bm,
                        &p->groups);
