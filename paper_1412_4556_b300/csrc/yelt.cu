@@ -259,12 +259,18 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
           tot = add(tot, x[i]);
         }
       }
-      // entry i of this lane's chunk (with output: gathered again)
+      // entry i of this lane's chunk (with output: gathered again, from the
+      // interleaved table whose line this step has just brought into L2)
       auto entry = [&](int i) -> U128 {
-        if constexpr (OUT)
-          return entry_or_zero<EB>(table, id[i], (hits >> i) & 1u, pol_tab);
-        else
+        if constexpr (OUT) {
+          // the entry is the first 16 (8) bytes of the event's 32 (16) in the interleaved table
+          if constexpr (EB == 16)
+            return entry_or_zero<16>(comb, 2 * id[i], (hits >> i) & 1u, pol_tab);
+          else
+            return entry_or_zero<8>(comb, 2 * id[i], (hits >> i) & 1u, pol_tab);
+        } else {
           return x[i];
+        }
       };
       // inclusive scan of the lane totals across the trial's lanes
       U128 incl = tot;
