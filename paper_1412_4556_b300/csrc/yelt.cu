@@ -364,12 +364,28 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
       double a_fp = exact ? 0.0 : clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
 #pragma unroll
       for (int i = 0; i < IDS; ++i) {
-        P = add(P, entry(i));
+        const U128 e = entry(i);
+        P = add(P, e);
         double inc;
         if (exact) {
           const U128 a = clamp_fixed(P, L.af);
-          inc = from_fixed_int(sub128(a, a_fx), L.q);
+          const U128 d = sub128(a, a_fx);
           a_fx = a;
+          if constexpr (!OUT) {
+            // Only the largest increment is kept: one equal to its entry
+            // (the id lies inside the layer) joins the largest entry,
+            // converted once per trial; one of 0 cannot raise it; only a
+            // crossing id (d strictly between) is converted here.  Slots past
+            // the trial's end hold entry 0 and leave d = 0.
+            if (d.lo == e.lo && d.hi == e.hi) {
+              if (ge128(d, best_fx)) best_fx = d;
+            } else if ((d.lo | d.hi) != 0ull) {
+              const unsigned long long b = (unsigned long long)__double_as_longlong(from_fixed_int(d, L.q));
+              best = b > best ? b : best;
+            }
+            continue;
+          }
+          inc = from_fixed_int(d, L.q);
         } else {
           const double a = clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
           inc = __dsub_rn(a, a_fp);
