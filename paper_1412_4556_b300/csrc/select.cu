@@ -28,6 +28,13 @@ struct SelState {
   unsigned long long max_key;
   unsigned int done_pass;
   unsigned int done_sum;
+  // Early finish: once the bucket a threshold lies in holds a single key
+  // (state 1), the next pass records that key (found, per distinct prefix)
+  // and the threshold is known (state 2); when every return period is known
+  // the remaining passes return at once.
+  unsigned long long found[kMaxReturnPeriods];
+  unsigned int rstate[kMaxReturnPeriods];
+  unsigned int all_done;
   unsigned int hist[kMaxReturnPeriods][256];
 };
 
@@ -51,11 +58,14 @@ __global__ void select_init_kernel(SelState *states, KArgs ka, int n_rp) {
     st->cnt_gt[tid] = 0ull;
     st->acc_lo[tid] = 0ull;
     st->acc_hi[tid] = 0ull;
+    st->found[tid] = 0ull;
+    st->rstate[tid] = 0u;
   }
   if (tid == 0) {
     st->max_key = 0ull;
     st->done_pass = 0u;
     st->done_sum = 0u;
+    st->all_done = 0u;
   }
 }
 
@@ -67,15 +77,21 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
                    SelState *states, unsigned int *err) {
   const double *__restrict__ y = ylts + (size_t)blockIdx.y * (size_t)n;
   SelState *st = states + blockIdx.y;
+  if (pass > 0 && st->all_done) return;  // every threshold of this layer is known
   __shared__ unsigned int sh[kMaxReturnPeriods][256];
   __shared__ unsigned long long s_prefix[kMaxReturnPeriods];
   __shared__ unsigned long long s_pre[kMaxReturnPeriods];  // distinct prefixes, above the current digit
-  __shared__ int s_slot[kMaxReturnPeriods];                // return period -> its prefix's histogram
+  __shared__ int s_slot[kMaxReturnPeriods];                // return period -> its prefix's histogram (-1: known)
+  __shared__ unsigned int s_state[kMaxReturnPeriods];
   __shared__ int s_nslots;
+  __shared__ unsigned int s_find;  // slots whose bucket holds one key, to be recorded
   __shared__ bool s_last;
   const int tid = threadIdx.x;
   for (int i = tid; i < n_rp * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
-  if (tid < n_rp) s_prefix[tid] = st->prefix[tid];
+  if (tid < n_rp) {
+    s_prefix[tid] = st->prefix[tid];
+    s_state[tid] = st->rstate[tid];
+  }
   __syncthreads();
   const int shift = 56 - 8 * pass;
   // Return periods whose thresholds share the prefix chosen so far (all of
@@ -83,7 +99,12 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   // one shared-memory atomic: the distinct prefixes select disjoint keys.
   if (tid == 0) {
     int ns = 0;
+    unsigned int find = 0u;
     for (int r = 0; r < n_rp; ++r) {
+      if (s_state[r] == 2u) {
+        s_slot[r] = -1;
+        continue;
+      }
       const unsigned long long pr = pass == 0 ? 0ull : s_prefix[r] >> (shift + 8);
       int sl = -1;
       for (int q = 0; q < ns; ++q)
@@ -93,11 +114,14 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
         sl = ns++;
       }
       s_slot[r] = sl;
+      if (s_state[r] == 1u) find |= 1u << sl;
     }
     s_nslots = ns;
+    s_find = find;
   }
   __syncthreads();
   const int ns = s_nslots;
+  const unsigned int find = s_find;
   unsigned long long pre[4] = {0ull, 0ull, 0ull, 0ull};
   if constexpr (FAST) {
 #pragma unroll
@@ -123,7 +147,10 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
     } else {
       for (int q = 0; q < ns; ++q) sl = kp == s_pre[q] ? q : sl;
     }
-    if (sl >= 0) atomicAdd(&sh[sl][d], 1u);
+    if (sl >= 0) {
+      atomicAdd(&sh[sl][d], 1u);
+      if ((find >> sl) & 1u) st->found[sl] = key;  // the bucket's only key
+    }
   };
   // Four independent loads in flight per thread: one load at a time leaves
   // a pass over a many-layer batch (hundreds of MB) latency-bound.
@@ -146,7 +173,8 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   }
   __syncthreads();
   for (int i = tid; i < n_rp * 256; i += blockDim.x) {
-    const unsigned int c = sh[s_slot[i >> 8]][i & 255];
+    const int sl = s_slot[i >> 8];
+    const unsigned int c = sl >= 0 ? sh[sl][i & 255] : 0u;
     if (c) atomicAdd(&st->hist[0][0] + i, c);
   }
   __threadfence();
@@ -165,12 +193,18 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   const int lane = tid & 31, wid = tid >> 5;
   unsigned int *cnt = &sh[0][0];  // the block's histogram is merged: reuse its space
   for (int i = tid; i < n_rp * 256; i += blockDim.x) cnt[i] = __ldcg(&st->hist[0][0] + i);
-  if (tid < n_rp) s_krem[tid] = st->k_rem[tid];
+  if (tid < n_rp) {
+    s_krem[tid] = st->k_rem[tid];
+    if (s_state[tid] == 1u) {  // recorded during this pass: the threshold is that key
+      st->prefix[tid] = __ldcg(&st->found[s_slot[tid]]);
+      st->rstate[tid] = 2u;
+    }
+  }
   __syncthreads();
   const int half = tid >> 8, b = tid & 255;
   for (int r0 = 0; r0 < n_rp; r0 += 2) {
     const int r = r0 + half;
-    const bool act = r < n_rp;
+    const bool act = r < n_rp && s_state[r] == 0u;
     const long long k_rem = act ? s_krem[r] : 0;
     const long long h = act ? (long long)cnt[r * 256 + 255 - b] : 0;
     long long incl = h;
@@ -185,11 +219,17 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
     if (act && excl < k_rem && k_rem <= incl) {
       st->k_rem[r] = k_rem - excl;
       st->prefix[r] = s_prefix[r] | ((unsigned long long)(255 - b) << shift);
+      if (h == 1 && pass < 7) st->rstate[r] = 1u;  // a single key left in its bucket
     }
     __syncthreads();
   }
   for (int i = tid; i < n_rp * 256; i += blockDim.x) (&st->hist[0][0])[i] = 0u;
-  if (tid == 0) st->done_pass = 0u;
+  if (tid == 0) {
+    st->done_pass = 0u;
+    bool all = true;
+    for (int r = 0; r < n_rp; ++r) all = all && st->rstate[r] == 2u;
+    if (all) st->all_done = 1u;
+  }
 }
 
 __device__ __forceinline__ int select_q(unsigned long long max_key, int64_t n) {
