@@ -35,6 +35,10 @@ struct SelState {
   unsigned long long found[kMaxReturnPeriods];
   unsigned int rstate[kMaxReturnPeriods];
   unsigned int all_done;
+  // Keys equal to the largest (counted in the second pass): when at least k
+  // losses tie at the top (trials capped at AggL), the k-th largest is the
+  // largest, and ties never leave a bucket with a single key.
+  unsigned long long cnt_max;
   unsigned int hist[kMaxReturnPeriods][256];
 };
 
@@ -66,6 +70,7 @@ __global__ void select_init_kernel(SelState *states, KArgs ka, int n_rp) {
     st->done_pass = 0u;
     st->done_sum = 0u;
     st->all_done = 0u;
+    st->cnt_max = 0ull;
   }
 }
 
@@ -129,10 +134,13 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
   }
   unsigned long long local_max = 0ull;
   bool bad = false;
+  const unsigned long long max_key = pass == 1 ? st->max_key : ~0ull;
+  unsigned int n_max = 0u;  // pass 1: keys equal to the largest
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   auto take = [&](double v) {
     const unsigned long long key = (unsigned long long)__double_as_longlong(v);
     const unsigned int d = (unsigned int)(key >> shift) & 255u;
+    if (pass == 1) n_max += key == max_key ? 1u : 0u;
     if (pass == 0) {
       bad |= key >= 0x7FF0000000000000ull;  // negative, infinite or NaN
       local_max = key > local_max ? key : local_max;
@@ -171,6 +179,10 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
     if ((tid & 31) == 0 && local_max) atomicMax(&st->max_key, local_max);
     if (__any_sync(0xFFFFFFFFu, bad) && (tid & 31) == 0) atomicOr(err, 1u);
   }
+  if (pass == 1) {
+    const unsigned int w = __reduce_add_sync(0xFFFFFFFFu, n_max);
+    if ((tid & 31) == 0 && w) atomicAdd(&st->cnt_max, (unsigned long long)w);
+  }
   __syncthreads();
   for (int i = tid; i < n_rp * 256; i += blockDim.x) {
     const int sl = s_slot[i >> 8];
@@ -198,6 +210,10 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
     if (s_state[tid] == 1u) {  // recorded during this pass: the threshold is that key
       st->prefix[tid] = __ldcg(&st->found[s_slot[tid]]);
       st->rstate[tid] = 2u;
+    } else if (pass == 1 && s_state[tid] == 0u && __ldcg(&st->cnt_max) >= (unsigned long long)st->k[tid]) {
+      st->prefix[tid] = __ldcg(&st->max_key);  // at least k losses tie at the largest
+      st->rstate[tid] = 2u;
+      s_state[tid] = 2u;
     }
   }
   __syncthreads();
