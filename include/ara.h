@@ -369,11 +369,12 @@ ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const doub
  * FP64 or 4 FP32-table layers.  With autotune != 0, plan creation first
  * times the YLT kernel's launch shapes (lanes per trial -- the trials a warp
  * sums side by side --, id loads per lane, whether the id stream is
- * prefetched into L2, and 1024- or 768-thread CTAs) and, per entry width, the group size (FP64: 2 or 1
- * layers per pass; FP32 tables: 4, 2 or 1) by timing the whole set of passes,
- * on the plan's own layers and the first min(n_trials, 2^20) trials, and
- * keeps the fastest; the launch shapes also serve later ara_layers_ylt /
- * ara_layer_ylt calls on the context.
+ * prefetched into L2, and 1024- or 768-thread CTAs) on the first
+ * min(n_trials, 2^20) trials and, per entry width, the group size (FP64: 2
+ * or 1 layers per pass; FP32 tables: 4, 2 or 1) by timing the whole set of
+ * passes on the first min(n_trials, 2^18) trials, all on the plan's own
+ * layers, and keeps the fastest; the launch shapes also serve later
+ * ara_layers_ylt / ara_layer_ylt calls on the context.
  * The plan owns its output buffers.  A plan stops working (ARA_E_STATE from
  * ara_plan_run) when the YET is reloaded or one of its layers is released;
  * ara_destroy destroys the context's plans.
