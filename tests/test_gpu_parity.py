@@ -177,6 +177,36 @@ def test_pml_tvar_many_return_periods_wide_range(engine):
     np.testing.assert_allclose(tvar_g, tvar_o, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("rps", [[100.0], [100.0, 250.0, 500.0], [2.0, 7.0, 100.0, 999.0],
+                                 [1.0, 2.0, 5.0, 10.0, 100.0], [float(r) for r in range(1, 17)]])
+def test_pml_tvar_early_finish_and_ties(engine, rps):
+    """The radix selection's shortcuts against the oracle, batched over
+    layers that take different ones: distinct losses (a threshold's bucket
+    ends with one key and the remaining passes return at once), at least k
+    losses tied at the largest (the threshold is the largest after the
+    second pass), a k-th largest shared by three trials below the top (no
+    shortcut: every pass runs), all losses equal, and all zero."""
+    rng = np.random.default_rng(31)
+    n = 20_000
+    distinct = rng.lognormal(14.0, 1.2, n)
+    capped = np.minimum(rng.lognormal(16.0, 1.0, n), 2.5e7)          # thousands at the cap
+    tied = rng.lognormal(14.0, 1.2, n)
+    k = int(n // 100.0)
+    tau = np.sort(tied)[::-1][k - 1]
+    tied[np.argsort(-tied)[k - 3:k + 2]] = tau                     # the 100-year loss is shared
+    equal = np.full(n, 123456.789)
+    zero = np.zeros(n)
+    ys = np.stack([distinct, capped, tied, equal, zero])
+    pml_b, tvar_b = engine.pml_tvar_batch(ys, rps)
+    for i, y in enumerate(ys):
+        pml_o, tvar_o = oracle.pml_tvar(y, rps)
+        np.testing.assert_array_equal(pml_b[i], pml_o, err_msg=f"layer {i}")
+        np.testing.assert_allclose(tvar_b[i], tvar_o, rtol=1e-12, atol=0, err_msg=f"layer {i}")
+        pml_1, tvar_1 = engine.pml_tvar(y, rps)                      # one layer alone: same bits
+        np.testing.assert_array_equal(pml_1, pml_b[i])
+        np.testing.assert_array_equal(tvar_1.view(np.uint64), tvar_b[i].view(np.uint64))
+
+
 def test_result_independent_of_launch_shape(engine, monkeypatch):
     w = S.paper_scale(n_trials=3_000, catalog_size=300_000)
     (L,) = load_workload(engine, w)
