@@ -10,10 +10,14 @@
 // the values.  An MSD radix selection (8 passes of 8 bits) finds the exact
 // k_r-th largest key tau_r for every r at once: each pass histograms the keys
 // that share the prefix chosen so far, and the last CTA to finish a pass
-// picks the next digit ("last block done" counter, no waiting).  A final pass
-// sums the keys above tau_r exactly in 128-bit fixed point and adds
-// (k_r - count) copies of tau_r, so ties at the threshold are handled
-// exactly; one rounding to binary64 and one division give TVaR.
+// picks the next digit ("last block done" counter, no waiting).  A threshold
+// is known early when its bucket holds a single key (the next pass records
+// it) or when at least k_r keys tie at the largest (counted in the second
+// pass); once all of a YLT's thresholds are known its remaining passes
+// return at once.  A final pass sums the keys above tau_r exactly in 128-bit
+// fixed point and adds (k_r - count) copies of tau_r, so ties at the
+// threshold are handled exactly; one rounding to binary64 and one division
+// give TVaR.
 #include "ara_internal.cuh"
 
 namespace ara {
