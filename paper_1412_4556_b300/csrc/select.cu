@@ -43,6 +43,10 @@ struct SelState {
   // losses tie at the top (trials capped at AggL), the k-th largest is the
   // largest, and ties never leave a bucket with a single key.
   unsigned long long cnt_max;
+  // From the fourth pass on: the smallest and largest key matching each
+  // distinct prefix; equal, they say every candidate is the same loss (a
+  // tie below the top), which is then the threshold.
+  unsigned long long smin[kMaxReturnPeriods], smax[kMaxReturnPeriods];
   unsigned int hist[kMaxReturnPeriods][256];
 };
 
@@ -68,6 +72,8 @@ __global__ void select_init_kernel(SelState *states, KArgs ka, int n_rp) {
     st->acc_hi[tid] = 0ull;
     st->found[tid] = 0ull;
     st->rstate[tid] = 0u;
+    st->smin[tid] = ~0ull;
+    st->smax[tid] = 0ull;
   }
   if (tid == 0) {
     st->max_key = 0ull;
@@ -162,6 +168,10 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
     if (sl >= 0) {
       atomicAdd(&sh[sl][d], 1u);
       if ((find >> sl) & 1u) st->found[sl] = key;  // the bucket's only key
+      if (pass >= 3) {
+        atomicMin(&st->smin[sl], key);
+        atomicMax(&st->smax[sl], key);
+      }
     }
   };
   // Four independent loads in flight per thread: one load at a time leaves
@@ -218,6 +228,13 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
       st->prefix[tid] = __ldcg(&st->max_key);  // at least k losses tie at the largest
       st->rstate[tid] = 2u;
       s_state[tid] = 2u;
+    } else if (pass >= 3 && s_state[tid] == 0u) {
+      const unsigned long long lo = __ldcg(&st->smin[s_slot[tid]]), hi = __ldcg(&st->smax[s_slot[tid]]);
+      if (lo == hi) {  // every candidate is the same loss
+        st->prefix[tid] = lo;
+        st->rstate[tid] = 2u;
+        s_state[tid] = 2u;
+      }
     }
   }
   __syncthreads();
@@ -244,6 +261,10 @@ select_pass_kernel(const double *__restrict__ ylts, int64_t n, int n_rp, int pas
     __syncthreads();
   }
   for (int i = tid; i < n_rp * 256; i += blockDim.x) (&st->hist[0][0])[i] = 0u;
+  if (tid < kMaxReturnPeriods) {
+    st->smin[tid] = ~0ull;
+    st->smax[tid] = 0ull;
+  }
   if (tid == 0) {
     st->done_pass = 0u;
     bool all = true;
