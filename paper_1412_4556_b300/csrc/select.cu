@@ -12,8 +12,9 @@
 // that share the prefix chosen so far, and the last CTA to finish a pass
 // picks the next digit ("last block done" counter, no waiting).  A threshold
 // is known early when its bucket holds a single key (the next pass records
-// it) or when at least k_r keys tie at the largest (counted in the second
-// pass); once all of a YLT's thresholds are known its remaining passes
+// it), when at least k_r keys tie at the largest (counted in the second
+// pass), or when all its remaining candidates are one key (from the fourth
+// pass on); once all of a YLT's thresholds are known its remaining passes
 // return at once.  A final pass sums the keys above tau_r exactly in 128-bit
 // fixed point and adds (k_r - count) copies of tau_r, so ties at the
 // threshold are handled exactly; one rounding to binary64 and one division
