@@ -110,3 +110,68 @@ def test_tail_errors(engine):
     assert ei.value.name == "ARA_E_INVALID_ARG"
     p, tv = engine.pml_tvar_tail(t, 1000, [100.0])
     assert p[0] == y[-10] and tv[0] == pytest.approx(y[-10:].mean(), rel=1e-15)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_bench_shard_step_with_the_engine(world):
+    """bench.py's per-rank step with the real engine, its ranks run one after
+    the other on this GPU (one engine per rank; the all-gather is a device
+    copy, nothing waits on another rank): PML/TVaR of the union of the shards
+    equals the oracle's on the concatenated shard YLTs."""
+    import torch
+
+    import bench
+    from paper_1412_4556_b300 import Engine
+    rps = [100.0, 250.0, 500.0]
+    shards = [S.paper_scale(seed=bench.shard_seed(S.DEFAULT_SEED, r), n_trials=4_000, lam=200.0,
+                            catalog_size=200_000) for r in range(world)]
+    n = shards[0].yet.n_trials
+    k = bench.tail_size(n, world, rps)
+    dev = torch.device("cuda", 0)
+    tails = [None] * world
+    res = None
+    for rank in reversed(range(world)):  # rank 0 last: it gathers every tail
+        w = shards[rank]
+        with Engine(0) as eng:
+            eng.load_yet_from(w.yet)
+            first = eng.load_pool(w.pool)
+            handles = [first + j for j in w.layers[0].elts]
+            ylt_out = torch.empty(n, dtype=torch.float64, device=dev)
+            tail_out = torch.empty(k, dtype=torch.float64, device=dev)
+            gather_out = torch.empty(k * world, dtype=torch.float64, device=dev)
+
+            def all_gather(out, inp, rank=rank):
+                torch.cuda.synchronize()
+                tails[rank] = inp.clone()
+                if rank == 0:
+                    out.copy_(torch.cat(tails))
+                torch.cuda.synchronize()
+
+            r = bench.shard_step(eng, handles, w.layers[0], ylt_out, k, tail_out, gather_out, n, rank, world,
+                                 rps, all_gather)
+            torch.cuda.synchronize()
+            if rank == 0:
+                res = r
+            else:
+                assert r is None
+    pml, tvar = res
+    ylts, errs = [], []
+    for w in shards:
+        o, pre = oracle.layer_ylt(w.yet, w.pool, w.layers[0])
+        ylts.append(o)
+        errs.append(oracle.compare_fp64(_engine_ylt(w), o, pre)["max_abs_err"])
+    ref = np.concatenate(ylts)
+    pml_o, tvar_o = oracle.pml_tvar(ref, rps)
+    pt = oracle.compare_pml_tvar(pml, tvar, pml_o, tvar_o, rps, ref.size, max(errs))
+    assert pt["within_bound"], pt
+
+
+def _engine_ylt(w):
+    """The shard's YLT from a fresh engine (the step released its layer)."""
+    from paper_1412_4556_b300 import Engine
+    with Engine(0) as eng:
+        eng.load_yet_from(w.yet)
+        first = eng.load_pool(w.pool)
+        L = w.layers[0]
+        h = eng.define_layer([first + j for j in L.elts], L.occ_ret, L.occ_lim, L.agg_ret, L.agg_lim)
+        return eng.layer_ylt(h)
