@@ -225,7 +225,7 @@ YltStream ylt_stream(const ara_ctx *c, int G);
 
 ara_status fold_layer(ara_ctx *c, LayerRec &L, cudaStream_t s);
 // The device work of fold_layer for a layer whose buffers exist and whose
-// grid (q) is set: queue only memsets and the fold kernel (stream capture).
+// grid (q) is set: queue only memsets and the fold kernel.
 ara_status enqueue_fold(ara_ctx *c, const LayerRec &L, cudaStream_t s);
 void recycle_layer(ara_ctx *c, LayerRec &L);
 ara_status get_layer(ara_ctx *c, int32_t layer, LayerRec **out);
