@@ -713,6 +713,7 @@ def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -
     ms_p, ylt_p = timed(step_plain, steps)
     ms_p64 = timed(lambda: step_plain(ARA_FP64), steps)[0] if mixed else ms_p
     passes = plan.passes()
+    plan_launches = plan.kernel_launches()
     # nonzero events of every layer (for the passes' L1TEX floor)
     nz = np.stack([eng.event_table(h) != 0.0 for h in plan_layers])
     plan.close()
@@ -778,9 +779,7 @@ def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -
     if mixed:
         res["plain_fp64_per_layer_ms_per_step"] = ms_p64
         res["speedup_vs_plain_fp64"] = ms_p64 / ms_g
-    # 64 folds, one YLT launch per pass, the batched selection (init + 8
-    # passes + sum), and the interleave of each multi-layer pass
-    res["gpu_launches_per_step"] = G + len(passes) + 10 + sum(1 for _, g, *_ in passes if g > 1)
+    res["gpu_launches_per_step"] = plan_launches  # kernel nodes of the plan's graph
     return res
 
 

@@ -405,6 +405,11 @@ ARA_API ara_status ara_plan_run(ara_plan *plan, double *ylt_out, double *pml_out
 ARA_API ara_status ara_plan_passes(const ara_plan *plan, int32_t max_passes, int32_t *info,
                                    int32_t *n_passes);
 
+/* The number of kernel launches one ara_plan_run replays (the kernel nodes
+ * of the plan's graph: the folds, the YLT passes, any interleave of tables,
+ * the selection), in *n_kernels.  Errors: ARA_E_INVALID_ARG, ARA_E_CUDA. */
+ARA_API ara_status ara_plan_kernel_launches(const ara_plan *plan, int32_t *n_kernels);
+
 ARA_API void ara_plan_destroy(ara_plan *plan);
 
 /* ---------------------------------------------------------- pricing service */

@@ -298,6 +298,10 @@ class Plan:
     def passes(self):
         return _native.ara_plan_passes(self.engine.ctx, self.plan)
 
+    def kernel_launches(self) -> int:
+        """Kernel launches one run replays (the kernel nodes of the plan's graph)."""
+        return _native.ara_plan_kernel_launches(self.engine.ctx, self.plan)
+
     def close(self) -> None:
         if self.plan:
             _native.ara_plan_destroy(self.plan)

@@ -88,6 +88,7 @@ PROTOTYPES = {
     "ara_plan_create": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i32, C.POINTER(C.c_void_p)]),
     "ara_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "ara_plan_passes": (_i32, [_vp, _i32, _vp, C.POINTER(_i32)]),
+    "ara_plan_kernel_launches": (_i32, [_vp, C.POINTER(_i32)]),
     "ara_plan_destroy": (None, [_vp]),
     "ara_service_create": (_i32, [_vp, C.POINTER(ServiceConfig), C.POINTER(C.c_void_p)]),
     "ara_service_submit": (_i32, [_vp, C.POINTER(Request), C.POINTER(_i64)]),
@@ -266,6 +267,13 @@ def ara_plan_passes(ctx: int, plan: int):
         eb, g, lpt, u, pf, th = info[10 * i:10 * i + 6]
         out.append((eb, g, lpt, u, pf, th, tuple(info[10 * i + 6:10 * i + 6 + g])))
     return out
+
+
+def ara_plan_kernel_launches(ctx: int, plan: int) -> int:
+    """Kernel launches one replay of the plan makes."""
+    n = _i32(0)
+    _check(ctx, lib.ara_plan_kernel_launches(plan, C.byref(n)))
+    return n.value
 
 
 def ara_plan_destroy(plan: int) -> None:

@@ -547,7 +547,7 @@ ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g
 
 ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, int64_t n_trials,
                          double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap,
-                         const std::vector<LayerGroup> *groups) {
+                         const std::vector<LayerGroup> *groups, const std::vector<GroupTable> *tables) {
   std::vector<LayerRec *> Ls((size_t)n_layers);
   for (int32_t i = 0; i < n_layers; ++i) {
     ara_status st = get_layer(c, layers[i], &Ls[(size_t)i]);
@@ -564,7 +564,10 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
   // and FP32-table layers four to a pass (4 x 8 bytes): one 32-byte L2
   // sector per gather.
   const std::vector<LayerGroup> in_order = groups ? std::vector<LayerGroup>() : group_in_order(Ls, 2, 4);
+  size_t gi = 0;
   for (const LayerGroup &grp : groups ? *groups : in_order) {
+    const GroupTable pre = tables && gi < tables->size() ? (*tables)[gi] : GroupTable{nullptr, nullptr};
+    ++gi;
     const int eb = grp.eb;
     const int G = (int)grp.idx.size();
     if (!((eb == 16 && (G == 1 || G == 2)) || (eb == 8 && (G == 1 || G == 2 || G == 4))))
@@ -583,7 +586,10 @@ ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, in
     }
     const void *table = tabs.t[0];
     const uint32_t *bitmap = bms.b[0];
-    if (G > 1) {
+    if (G > 1 && pre.table) {
+      table = pre.table;
+      bitmap = pre.bitmap;
+    } else if (G > 1) {
       ARA_CUDA(c, launch_interleave(tabs, eb, G, (int64_t)entries, pair_table, bms, bm.words, pair_bitmap, s),
                "interleave layer tables");
       table = pair_table;

@@ -279,8 +279,16 @@ ara_status group_by_overlap(ara_ctx *c, const std::vector<LayerRec *> &Ls, int g
 // pair_table / pair_bitmap scratch of 2 * (catalog + 1) entries and of the
 // layers' bitmap size.  Layers must be folded for the loaded YET.  groups:
 // the passes to run (positions in layers), or NULL for group_in_order(2, 4).
+// tables: for each group of groups, an interleaved table and union bitmap
+// already written for it (by a plan's folds), used instead of interleaving
+// the layers' tables into pair_table (NULL entries: interleave as usual).
+struct GroupTable {
+  const void *table;
+  const uint32_t *bitmap;
+};
 ara_status layers_ylt_on(ara_ctx *c, const int32_t *layers, int32_t n_layers, int64_t n_trials,
                          double *dst, cudaStream_t s, ulonglong2 *pair_table, uint32_t *pair_bitmap,
-                         const std::vector<LayerGroup> *groups = nullptr);
+                         const std::vector<LayerGroup> *groups = nullptr,
+                         const std::vector<GroupTable> *tables = nullptr);
 
 }  // namespace ara

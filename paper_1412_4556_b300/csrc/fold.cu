@@ -63,7 +63,7 @@ __device__ __forceinline__ void fold_body(
     FoldSmem<typename std::conditional<FP32, float, double>::type> &sm, int32_t *s_dyn, int b,
     const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, double occ_ret, double occ_lim, int q,
     void *__restrict__ table, uint32_t *__restrict__ bitmap, uint32_t bm_mul, double *__restrict__ f64_out,
-    unsigned int *__restrict__ inexact) {
+    unsigned int *__restrict__ inexact, int stride) {
   using Real = typename std::conditional<FP32, float, double>::type;
   Real *x = sm.x;
   uint16_t *st_off = sm.st_off;
@@ -148,9 +148,9 @@ __device__ __forceinline__ void fold_body(
     if (table) {
       const U128 v = to_fixed(o, q);
       if constexpr (FP32)
-        static_cast<unsigned long long *>(table)[e] = v.lo;  // v.hi = 0 on this grid
+        static_cast<unsigned long long *>(table)[(size_t)e * stride] = v.lo;  // v.hi = 0 on this grid
       else
-        static_cast<ulonglong2 *>(table)[e] = make_ulonglong2(v.lo, v.hi);
+        static_cast<ulonglong2 *>(table)[(size_t)e * stride] = make_ulonglong2(v.lo, v.hi);
       if ((v.lo | v.hi) != 0ull) {
         atomicOr(bitmap + bitmap_word((uint32_t)e, bm_mul), 1u << (e & 31));
       }
@@ -170,7 +170,7 @@ fold_kernel(const EltDesc *__restrict__ elts, int n_elts, int32_t catalog, doubl
   // typical layer needs little shared memory and the whole grid is resident
   extern __shared__ int32_t s_dyn[];
   fold_body<FP32>(sm, s_dyn, blockIdx.x, elts, n_elts, catalog, occ_ret, occ_lim, q, table, bitmap, bm_mul,
-                  f64_out, inexact);
+                  f64_out, inexact, 1);
 }
 
 // Many layers' folds in one launch (grid.y = layer): the CTAs of all the
@@ -183,10 +183,10 @@ fold_batch_kernel(const FoldJob *__restrict__ jobs, int32_t catalog) {
   const FoldJob j = jobs[blockIdx.y];
   if (j.fp32)
     fold_body<true>(*reinterpret_cast<FoldSmem<float> *>(raw), s_dyn, blockIdx.x, j.elts, j.n_elts, catalog,
-                    j.occ_ret, j.occ_lim, j.q, j.table, j.bitmap, j.bm_mul, nullptr, nullptr);
+                    j.occ_ret, j.occ_lim, j.q, j.table, j.bitmap, j.bm_mul, nullptr, nullptr, j.stride);
   else
     fold_body<false>(*reinterpret_cast<FoldSmem<double> *>(raw), s_dyn, blockIdx.x, j.elts, j.n_elts, catalog,
-                     j.occ_ret, j.occ_lim, j.q, j.table, j.bitmap, j.bm_mul, nullptr, nullptr);
+                     j.occ_ret, j.occ_lim, j.q, j.table, j.bitmap, j.bm_mul, nullptr, nullptr, j.stride);
 }
 
 // Before a batch of folds: every layer's bitmap cleared and its sentinel
@@ -197,7 +197,7 @@ __global__ void fold_clear_kernel(const FoldJob *__restrict__ jobs, int32_t cata
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) j.bitmap[i] = 0u;
   const int per = j.fp32 ? 1 : 2;  // 64-bit words of one entry
   if (blockIdx.x == 0 && (int)threadIdx.x < per)
-    static_cast<unsigned long long *>(j.table)[(size_t)catalog * per + threadIdx.x] = 0ull;
+    static_cast<unsigned long long *>(j.table)[(size_t)catalog * j.stride * per + threadIdx.x] = 0ull;
 }
 
 cudaError_t launch_fold(const EltDesc *d_elts, int n_elts, int32_t catalog, double occ_ret,

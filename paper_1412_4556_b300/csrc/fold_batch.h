@@ -12,7 +12,10 @@ namespace ara {
 
 // One layer's fold in a batch: its ELT list, occurrence terms, fixed-point
 // exponent and output table/bitmap (as for launch_fold); fp32 selects the
-// binary32 combine of FP32-table layers.
+// binary32 combine of FP32-table layers.  stride > 1 writes the layer's
+// entries into an interleaved table of stride layers (table points at this
+// layer's first entry; event e's entry is table[e * stride]), and several
+// jobs may share one bitmap, which then receives the union of their bits.
 struct FoldJob {
   const EltDesc *elts;
   int32_t n_elts;
@@ -22,6 +25,7 @@ struct FoldJob {
   uint32_t *bitmap;
   uint32_t bm_mul;
   int32_t fp32;
+  int32_t stride;
 };
 
 // Clear the bitmaps (words 32-bit words each) and sentinel entries of n_jobs

@@ -43,6 +43,10 @@ struct ara_plan {
   unsigned int *h_err = nullptr;     // pinned copy of d_err
   FoldJob *d_jobs = nullptr;         // every layer's fold, launched as one batch
   int max_elts = 0;
+  // Per pass over several layers: its interleaved table and union bitmap,
+  // written by the folds directly (no interleave step in the graph).
+  std::vector<ara::GroupTable> gtables;
+  std::vector<void *> gbufs;
   std::vector<ara::LayerGroup> groups;  // the YLT passes (positions in layers)
   std::vector<int32_t> pass_info;    // kPassInfo per pass: entry bytes, layers, lanes per trial, unroll, prefetch,
                                      // threads per CTA, the layers' positions (-1 padded to 4)
@@ -66,6 +70,7 @@ void free_plan(ara_plan *p) {
   cudaFree(p->d_out);
   cudaFree(p->d_err);
   cudaFree(p->d_jobs);
+  for (void *b : p->gbufs) cudaFree(b);
   cudaFreeHost(p->h_out);
   cudaFreeHost(p->h_err);
   cudaGetLastError();
@@ -306,12 +311,52 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     for (int g = 0; g < 4; ++g) p->pass_info.push_back(g < G ? ps.idx[(size_t)g] : -1);
   }
   // The folds of every layer as one batch (the layers' folds at creation
-  // fixed their exponents; the batch writes the same tables).
+  // fixed their exponents).  A layer of a pass over several layers is folded
+  // straight into that pass's interleaved table and union bitmap, so the
+  // graph has no interleave step; the others write their own table.
   std::vector<FoldJob> jobs;
   for (const LayerRec *L : Ls) {
     jobs.push_back(FoldJob{L->d_desc, (int32_t)L->elts.size(), L->q, L->occ_ret, L->occ_lim, L->d_table, L->d_bitmap,
-                           L->bm.mul, L->precision == ARA_FP32_TABLE ? 1 : 0});
+                           L->bm.mul, L->precision == ARA_FP32_TABLE ? 1 : 0, 1});
     p->max_elts = std::max(p->max_elts, (int)L->elts.size());
+  }
+  {
+    bool ok = true;
+    std::vector<ara::GroupTable> gt;
+    for (const LayerGroup &ps : p->groups) {
+      const int G = (int)ps.idx.size();
+      if (G < 2 || !ok) {
+        gt.push_back(ara::GroupTable{nullptr, nullptr});
+        continue;
+      }
+      void *tab = nullptr, *gbm = nullptr;
+      if (cudaMalloc(&tab, ((size_t)c->catalog + 1) * (size_t)(ps.eb * G)) != cudaSuccess ||
+          cudaMalloc(&gbm, (size_t)bm.words * 4) != cudaSuccess) {
+        cudaGetLastError();
+        if (tab) cudaFree(tab);
+        ok = false;  // not enough memory: interleave in the graph instead
+        gt.push_back(ara::GroupTable{nullptr, nullptr});
+        continue;
+      }
+      p->gbufs.push_back(tab);
+      p->gbufs.push_back(gbm);
+      gt.push_back(ara::GroupTable{tab, static_cast<const uint32_t *>(gbm)});
+      for (int g = 0; g < G; ++g) {
+        FoldJob &j = jobs[(size_t)ps.idx[(size_t)g]];
+        j.table = static_cast<unsigned char *>(tab) + (size_t)g * (size_t)ps.eb;
+        j.bitmap = static_cast<uint32_t *>(gbm);
+        j.stride = G;
+      }
+    }
+    if (ok) {
+      p->gtables = gt;
+    } else {  // back to the layers' own tables and the interleave step
+      for (size_t i = 0; i < jobs.size(); ++i) {
+        jobs[i].table = Ls[i]->d_table;
+        jobs[i].bitmap = Ls[i]->d_bitmap;
+        jobs[i].stride = 1;
+      }
+    }
   }
   if ((e = cudaMalloc(&p->d_jobs, jobs.size() * sizeof(FoldJob))) != cudaSuccess ||
       (e = cudaMemcpy(p->d_jobs, jobs.data(), jobs.size() * sizeof(FoldJob), cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -328,7 +373,7 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     st = cuda_fail(c, e, "fold kernels");
   if (st == ARA_OK)
     st = layers_ylt_on(c, p->layers.data(), n_layers, n_trials, p->d_ylt, p->cap, p->d_pair, p->d_pair_bm,
-                       &p->groups);
+                       &p->groups, p->gtables.empty() ? nullptr : &p->gtables);
   if (st == ARA_OK && (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), p->cap)) != cudaSuccess)
     st = cuda_fail(c, e, "cudaMemsetAsync");
   if (st == ARA_OK && (e = launch_pml_tvar_batch(p->d_ylt, n_layers, n_trials, p->k, n_rp, p->d_ws, p->d_out,
@@ -391,6 +436,26 @@ ara_status ara_plan_passes(const ara_plan *p, int32_t max_passes, int32_t *info,
   if (info)
     for (int32_t i = 0; i < std::min(n, max_passes); ++i)
       for (int j = 0; j < kPassInfo; ++j) info[kPassInfo * i + j] = p->pass_info[(size_t)(kPassInfo * i + j)];
+  return ARA_OK;
+}
+
+ara_status ara_plan_kernel_launches(const ara_plan *p, int32_t *n_kernels) {
+  if (!p || !n_kernels) return fail_free(ARA_E_INVALID_ARG, "NULL argument");
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(p->graph, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e == cudaSuccess && n) e = cudaGraphGetNodes(p->graph, nodes.data(), &n);
+  int32_t k = 0;
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[i], &t);
+    if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail_free(ARA_E_CUDA, "plan graph nodes: %s", cudaGetErrorString(e));
+  }
+  *n_kernels = k;
   return ARA_OK;
 }
 

@@ -45,6 +45,9 @@ def test_plan_equals_direct_calls(engine, autotune):
             np.testing.assert_array_equal(pml, pml_d)
             np.testing.assert_array_equal(tvar, tvar_d)
         passes = plan.passes()
+        # one replay: the folds' clear and batch, one launch per pass (the
+        # folds write each multi-layer pass's table: no interleave), selection
+        assert plan.kernel_launches() == 2 + len(passes) + 10
     # every layer in exactly one pass, of its own entry width
     pos = sorted(i for *_, ps in passes for i in ps)
     assert pos == list(range(len(hs)))
