@@ -375,7 +375,11 @@ ARA_API ara_status ara_pml_tvar_noalloc(const double *ylt, int64_t n, const doub
  * passes on the first min(n_trials, 2^18) trials, all on the plan's own
  * layers, and keeps the fastest; the launch shapes also serve later
  * ara_layers_ylt / ara_layer_ylt calls on the context.
- * The plan owns its output buffers.  A plan stops working (ARA_E_STATE from
+ * The plan owns its output buffers and, for each pass over several layers,
+ * that pass's interleaved table ((catalog + 1) x entry bytes x layers) and
+ * union bitmap, into which its folds write directly (when these cannot be
+ * allocated the graph interleaves the layers' own tables instead).  A plan
+ * stops working (ARA_E_STATE from
  * ara_plan_run) when the YET is reloaded or one of its layers is released;
  * ara_destroy destroys the context's plans.
  */
