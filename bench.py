@@ -693,7 +693,7 @@ def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -
         return e0.elapsed_time(e1) / steps, k_ms / steps
 
     plan_layers = define()
-    plan = Plan(eng, plan_layers, w.return_periods, autotune=True)
+    plan = Plan(eng, plan_layers, w.return_periods, autotune=not args.no_autotune)
 
     def step_plan():
         # one graph launch: 64 ELT folds, the grouped YLT passes, PML/TVaR
@@ -757,8 +757,10 @@ def batched_result(args, w, mixed: bool, ceil=None, oracle_trials: int = 2048) -
         "metric": "layer-trial-events/s", "value": value, "unit": "layer-trial-events/s",
         "ms_per_step": ms_g, "steps": steps, "warmup": args.warmup,
         "dtype": "f32 tables, exact trial sums" if mixed else "f64",
-        "step": "ara_plan_run: one CUDA graph of 64 ELT folds + the grouped YLT passes + batched PML/TVaR "
-                "(launch shapes autotuned at plan creation)",
+        "step": "ara_plan_run: one CUDA graph of the 64 layers' ELT folds (one batched launch, into each "
+                "pass's interleaved table) + the grouped YLT passes + batched PML/TVaR "
+                + ("(default launch shapes and group sizes: --no-autotune)" if args.no_autotune
+                   else "(launch shapes and group sizes autotuned at plan creation)"),
         "yet_layout": yet_layout(compact_ms),
         "l2": "inputs larger than L2 (a 2-2.7 GB YET id stream per pass)",
         "ylt_kernels_ms_per_step": ylt_b,
@@ -1174,6 +1176,9 @@ def main():
     ap.add_argument("--rate", type=float, default=50.0, help="service: Poisson arrival rate per s")
     ap.add_argument("--slots", type=int, default=4, help="service: batches in flight")
     ap.add_argument("--max-batch", type=int, default=16, help="service: requests per batch")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched/mixed: plan without timing launch shapes and group sizes (for profilers, "
+                         "whose overhead would skew the timing)")
     ap.add_argument("--oracle-trials", type=int, default=0,
                     help="service: trials checked per sampled request (0: every trial)")
     ap.add_argument("--trials", type=int, default=1_000_000, help="trials per GPU")
