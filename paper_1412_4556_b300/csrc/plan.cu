@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "ara.h"
@@ -321,7 +322,10 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
     p->max_elts = std::max(p->max_elts, (int)L->elts.size());
   }
   {
-    bool ok = true;
+    // ARA_PLAN_INTERLEAVE=1 keeps the interleave step (the path taken when the
+    // pass tables cannot be allocated), for tests and measurements.
+    const char *force = std::getenv("ARA_PLAN_INTERLEAVE");
+    bool ok = !(force && std::atoi(force));
     std::vector<ara::GroupTable> gt;
     for (const LayerGroup &ps : p->groups) {
       const int G = (int)ps.idx.size();

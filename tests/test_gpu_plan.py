@@ -64,6 +64,27 @@ def test_plan_equals_direct_calls(engine, autotune):
             assert_fp64_parity(direct[i], o, pre, what=f"layer {i}")
 
 
+def test_plan_with_the_interleave_step(engine, monkeypatch):
+    """The path a plan takes when its passes' tables cannot be allocated: the
+    layers fold into their own tables and the graph interleaves them; same
+    bits as the direct calls."""
+    from paper_1412_4556_b300 import Plan
+    monkeypatch.setenv("ARA_PLAN_INTERLEAVE", "1")
+    w, hs, precs = setup(engine)
+    direct = engine.layers_ylt(hs)
+    pml_d, tvar_d = engine.pml_tvar_batch(direct, RPS)
+    with Plan(engine, hs, RPS, autotune=False) as plan:
+        y = np.empty_like(direct)
+        pml, tvar = plan.run(ylt_out=y)
+        passes = plan.passes()
+        multi = sum(1 for _, g, *_ in passes if g > 1)
+        assert multi > 0
+        assert plan.kernel_launches() == 2 + len(passes) + multi + 10
+    np.testing.assert_array_equal(y.view(np.uint64), direct.view(np.uint64))
+    np.testing.assert_array_equal(pml, pml_d)
+    np.testing.assert_array_equal(tvar, tvar_d)
+
+
 def test_plan_device_output_prefix_and_streams(engine):
     import torch
     from paper_1412_4556_b300 import Plan
