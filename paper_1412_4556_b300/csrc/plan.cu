@@ -362,6 +362,15 @@ ara_status ara_plan_create(ara_ctx *c, const int32_t *layers, int32_t n_layers, 
       }
     }
   }
+  // The batch's CTAs run layer after layer (blockIdx.y): the layers of one
+  // pass go next to each other, so the halves of each interleaved row are
+  // written while its L2 line is still there.
+  {
+    std::vector<FoldJob> ordered;
+    for (const LayerGroup &ps : p->groups)
+      for (const int32_t i : ps.idx) ordered.push_back(jobs[(size_t)i]);
+    if (ordered.size() == jobs.size()) jobs.swap(ordered);
+  }
   if ((e = cudaMalloc(&p->d_jobs, jobs.size() * sizeof(FoldJob))) != cudaSuccess ||
       (e = cudaMemcpy(p->d_jobs, jobs.data(), jobs.size() * sizeof(FoldJob), cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaGetLastError();
