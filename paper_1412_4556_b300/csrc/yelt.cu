@@ -385,7 +385,14 @@ yelt_kernel(const int64_t *__restrict__ coff, const int4 *__restrict__ chunks,
             }
             continue;
           }
-          inc = from_fixed_int(d, L.q);
+          // with output: an id inside the layer is its own binary64 value,
+          // one that changes nothing is 0; only a crossing id is converted
+          if ((d.lo | d.hi) == 0ull)
+            inc = 0.0;
+          else if (use64 && d.lo == e.lo && d.hi == e.hi)
+            inc = __longlong_as_double((long long)f[i]);
+          else
+            inc = from_fixed_int(d, L.q);
         } else {
           const double a = clamp_fp64(P, L.q, L.agg_ret, L.agg_lim);
           inc = __dsub_rn(a, a_fp);
